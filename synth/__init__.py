@@ -1,0 +1,190 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds random-number generation and input construction only; it
+contains none of the method's arithmetic (no Hamiltonian action, no ansatz, no
+energy).  Both the CPU oracle and the CUDA path consume exactly the arrays it
+returns, so the two sides see identical bytes.
+
+Generators (published definitions, restated):
+  * splitmix64 (S. Vigna) seeds the state of
+  * xoshiro256** (D. Blackman and S. Vigna, 2018).
+  * uniform u = (r >> 11) * 2**-53 in [0, 1).
+  * standard normals by the Box-Muller transform, consumed in pairs: the
+    second value of a pair is cached and returned by the next draw.
+
+Integral recipe (synthetic stand-in for the FMO fragment integrals of the
+paper, Section 2.2, which are not available):
+  (i)   h_pq for p < q in row-major order ~ N(0, 1), mirrored to q > p; the
+        diagonal is replaced by linspace(-2, -0.5, n_orb) ascending, so the
+        lowest orbitals are the occupied ones of the reference determinant.
+  (ii)  Cholesky-like vectors L^k_pq for k = 0..n_chol-1 and p <= q row-major
+        ~ N(0, 1) / sqrt(n_chol), mirrored.
+  (iii) (pq|rs) = sum_k L^k_pq L^k_rs: chemist-notation integrals with the
+        8-fold permutational symmetry of real orbitals, positive semidefinite
+        as a (pq),(rs) matrix.
+  e_core = 0.
+Amplitude vectors theta use a separate generator stream.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+MASK64 = (1 << 64) - 1
+
+
+def _rotl(x: int, k: int) -> int:
+    return ((x << k) | (x >> (64 - k))) & MASK64
+
+
+class SplitMix64:
+    """splitmix64 (Vigna): a 64-bit counter with an avalanche output mix."""
+
+    def __init__(self, seed: int):
+        self.state = seed & MASK64
+
+    def next(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & MASK64
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & MASK64
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & MASK64
+        return z ^ (z >> 31)
+
+
+class Xoshiro256StarStar:
+    """xoshiro256** (Blackman and Vigna), state filled from splitmix64(seed)."""
+
+    def __init__(self, seed: int):
+        sm = SplitMix64(seed)
+        self.s = [sm.next() for _ in range(4)]
+        self._spare = None
+
+    def next(self) -> int:
+        s = self.s
+        result = (_rotl((s[1] * 5) & MASK64, 7) * 9) & MASK64
+        t = (s[1] << 17) & MASK64
+        s[2] ^= s[0]
+        s[3] ^= s[1]
+        s[1] ^= s[2]
+        s[0] ^= s[3]
+        s[2] ^= t
+        s[3] = _rotl(s[3], 45)
+        return result
+
+    def uniform(self) -> float:
+        """Uniform double in [0, 1) from the top 53 bits."""
+        return (self.next() >> 11) * (2.0 ** -53)
+
+    def normal(self) -> float:
+        """Standard normal by Box-Muller; pairs are consumed, spare cached."""
+        if self._spare is not None:
+            v, self._spare = self._spare, None
+            return v
+        # u1 in (0, 1] so that log(u1) is finite.
+        u1 = ((self.next() >> 11) + 1) * (2.0 ** -53)
+        u2 = (self.next() >> 11) * (2.0 ** -53)
+        r = math.sqrt(-2.0 * math.log(u1))
+        z0 = r * math.cos(2.0 * math.pi * u2)
+        z1 = r * math.sin(2.0 * math.pi * u2)
+        self._spare = z1
+        return z0
+
+
+def make_integrals(n_orb: int, n_chol: int, seed: int):
+    """Synthetic one- and two-electron integrals (recipe in the module doc).
+
+    Returns (h, eri, e_core): h is (n_orb, n_orb) float64 symmetric,
+    eri is (n_orb,)*4 float64 chemist-notation (pq|rs), e_core = 0.0.
+    """
+    rng = Xoshiro256StarStar(seed)
+    h = np.zeros((n_orb, n_orb), dtype=np.float64)
+    for p in range(n_orb):
+        for q in range(p + 1, n_orb):
+            v = rng.normal()
+            h[p, q] = v
+            h[q, p] = v
+    diag = np.linspace(-2.0, -0.5, n_orb) if n_orb > 1 else np.array([-2.0])
+    for p in range(n_orb):
+        h[p, p] = diag[p]
+    L = np.zeros((n_chol, n_orb, n_orb), dtype=np.float64)
+    scale = 1.0 / math.sqrt(n_chol)
+    for k in range(n_chol):
+        for p in range(n_orb):
+            for q in range(p, n_orb):
+                v = rng.normal() * scale
+                L[k, p, q] = v
+                L[k, q, p] = v
+    Lm = L.reshape(n_chol, n_orb * n_orb)
+    eri = (Lm.T @ Lm).reshape(n_orb, n_orb, n_orb, n_orb)
+    # Enforce exact 8-fold symmetry against matmul rounding order.
+    eri = 0.5 * (eri + eri.transpose(2, 3, 0, 1))
+    eri = 0.5 * (eri + eri.transpose(1, 0, 2, 3))
+    eri = 0.5 * (eri + eri.transpose(0, 1, 3, 2))
+    return np.ascontiguousarray(h), np.ascontiguousarray(eri), 0.0
+
+
+def theta_uniform(K: int, lo: float, hi: float, seed: int) -> np.ndarray:
+    rng = Xoshiro256StarStar(seed)
+    return np.array([lo + (hi - lo) * rng.uniform() for _ in range(K)],
+                    dtype=np.float64)
+
+
+def theta_normal(K: int, std: float, seed: int) -> np.ndarray:
+    rng = Xoshiro256StarStar(seed)
+    return np.array([std * rng.normal() for _ in range(K)], dtype=np.float64)
+
+
+def random_state(n_qubits: int, seed: int, sector=None) -> np.ndarray:
+    """Random normalised complex vector (test input), optionally supported
+    only on the basis states accepted by ``sector`` (a callable x -> bool)."""
+    rng = Xoshiro256StarStar(seed)
+    N = 1 << n_qubits
+    v = np.zeros(N, dtype=np.complex128)
+    for x in range(N):
+        if sector is None or sector(x):
+            re = rng.normal()
+            im = rng.normal()
+            v[x] = complex(re, im)
+    nrm = np.linalg.norm(v)
+    return v / nrm if nrm > 0 else v
+
+
+# Workloads with the shapes of the paper's fragments (monomers 8-12 qubits,
+# dimers 16-18 qubits) plus a 26-qubit scale-up.  n_qubits = 2 * n_orb under
+# the Jordan-Wigner mapping; closed shell n_alpha = n_beta = n_elec / 2.
+WORKLOADS = {
+    "8q": dict(n_orb=4, n_elec=4, n_chol=6, seed=0),
+    "12q": dict(n_orb=6, n_elec=6, n_chol=10, seed=1),
+    "18q": dict(n_orb=9, n_elec=10, n_chol=16, seed=2),
+    "26q": dict(n_orb=13, n_elec=12, n_chol=20, seed=4),
+}
+
+
+def workload(name: str):
+    w = WORKLOADS[name]
+    h, eri, e_core = make_integrals(w["n_orb"], w["n_chol"], w["seed"])
+    return dict(w, h=h, eri=eri, e_core=e_core,
+                n_alpha=w["n_elec"] // 2, n_beta=w["n_elec"] // 2)
+
+
+def stream_requests(n_req: int, seed: int = 7):
+    """Fragment request mix of a two-body FMO job: 60% monomers with
+    n_orb in {4,5,6} (8/10/12 qubits; 4/4/6 electrons) and 40% dimers with
+    n_orb in {8,9} (16/18 qubits; 8/10 electrons).  Fragment r draws its
+    integrals from seed 10000 + r with n_chol = n_orb + 1.  Inter-arrival
+    gaps are unit-rate exponentials (scale them by 1/rate)."""
+    rng = Xoshiro256StarStar(seed)
+    out = []
+    t = 0.0
+    for r in range(n_req):
+        t += -math.log(1.0 - rng.uniform())
+        if rng.uniform() < 0.6:
+            n_orb = (4, 5, 6)[min(2, int(3 * rng.uniform()))]
+            n_elec = {4: 4, 5: 4, 6: 6}[n_orb]
+        else:
+            n_orb = (8, 9)[min(1, int(2 * rng.uniform()))]
+            n_elec = {8: 8, 9: 10}[n_orb]
+        out.append(dict(r=r, t_unit=t, n_orb=n_orb, n_elec=n_elec,
+                        n_chol=n_orb + 1, seed=10000 + r))
+    return out
