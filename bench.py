@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Benchmark: Trotterised UCCSD energy + adjoint-gradient evaluations per
+second on GB300 (sm_103a), one JSON line on stdout.
+
+Workload (one step): the 18-qubit dimer-scale fragment (10 electrons, 9
+spatial orbitals, synthetic integrals seed 2 with 16 Cholesky vectors,
+K = 560 spin-conserving singles+doubles, first-order Trotter, M = 1) with a
+batch of 64 amplitude vectors theta ~ N(0, 0.05) (seeds 1002+b): one energy
+and full gradient per vector, FP32 state with FP64 reductions.  The
+26-qubit scale-up (12 electrons, K = 2478, seed 4) is timed as well and
+reported under "scaleup".
+
+--impl reference times the CPU oracle (FP64, OpenMP on the host cores) on
+a bounded sample of the same workload.
+
+Under torchrun each rank evaluates its own batch of 64 (weak scaling; the
+evaluations are independent, there is no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "UCCSD energy+grad evals/s (18q dimer fragment, batch 64)"
+UNIT = "evals/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-scaleup", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# oracle arm
+# ---------------------------------------------------------------------------
+def oracle_rate(w, thetas, n_eval):
+    import oracle
+    ex = oracle.excitations(w["n_orb"], w["n_alpha"], w["n_beta"])
+    t = time.perf_counter()
+    for b in range(n_eval):
+        oracle.energy_grad(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
+                           ex, thetas[b % len(thetas)], sector=True)
+    dt = time.perf_counter() - t
+    return n_eval / dt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = synth.workload("18q")
+    K = 560
+    thetas = [synth.theta_normal(K, 0.05, 1002 + b) for b in range(args.batch)]
+    per_step = 4
+    for _ in range(args.warmup):
+        oracle_rate(w, thetas, 1)
+    t = time.perf_counter()
+    for s in range(args.steps):
+        oracle_rate(w, thetas[(s * per_step) % args.batch:], per_step)
+    dt = time.perf_counter() - t
+    value = args.steps * per_step / dt
+    sample = f"{per_step} of the 64 theta vectors per step (sector-restricted FP64 oracle)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": "18q/10e UCCSD K=560, batch 64 theta"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def algorithmic(ctx_info, fam, B, n, amp_bytes, plan_fracs):
+    """Algorithmic bytes per launch of the pass kernels: one read and one
+    write of every amplitude of every slot (the compulsory traffic of a
+    shared-memory pass)."""
+    N = 1 << n
+    return 2.0 * amp_bytes * N * B
+
+
+def run_ours(args):
+    import torch
+    import paper_2402_17993_gb300 as uc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = uc.FP32_STATE if args.precision == "fp32" else uc.FP64
+    amp_bytes = 8 if prec == uc.FP32_STATE else 16
+    w = synth.workload("18q")
+    B = args.batch
+    ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
+                          precision=prec, device=local, batch=B)
+    K = ctx.K
+    th_host = np.stack([synth.theta_normal(K, 0.05, 1002 + b + 1000 * rank) for b in range(B)])
+    theta = torch.tensor(th_host, device=dev, dtype=torch.float64)
+    E = torch.empty(B, device=dev, dtype=torch.float64)
+    G = torch.empty(B, K, device=dev, dtype=torch.float64)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        ctx.energy_grad_device(theta, E, G, stream)
+    barrier()
+    ctx.set_profiling(True)
+    launches0 = ctx.info()["launches"]
+    clocks = Clocks(local)
+    clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    barrier()
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)  # evict L2 between timed steps (not timed)
+        evs[s][0].record(stream)
+        ctx.energy_grad_device(theta, E, G, stream)
+        evs[s][1].record(stream)
+    barrier()
+    ck = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    launches = ctx.info()["launches"] - launches0
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * B * args.steps / (total_ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    th_pin = torch.tensor(th_host, dtype=torch.float64).pin_memory()
+    E_pin = torch.empty(B, dtype=torch.float64).pin_memory()
+    G_pin = torch.empty(B, K, dtype=torch.float64).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.energy_grad_ptr(B, th_pin.data_ptr(), E_pin.data_ptr(), G_pin.data_ptr(), False, stream)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": B * K * 8, "d2h_bytes_per_step": B * 8 + B * K * 8}
+
+    info = ctx.info()
+    pk, pk_kind = peaks()
+    fams = ["forward", "happly", "adjoint"]
+    dom = max(fams, key=lambda f: prof["ms"][f])
+    per_launch_ms = prof["ms"][dom] / max(1, prof["launches"][dom])
+    alg_bytes = algorithmic(info, dom, B, info["n_qubits"], amp_bytes, None)
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_kind": pk_kind,
+                "family_ms_per_step": {f: prof["ms"][f] / max(1, prof["calls"]) for f in prof["ms"]},
+                "family_launches_per_step": {f: prof["launches"][f] / max(1, prof["calls"])
+                                             for f in prof["launches"]}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == uc.FP32_STATE else "f64", "data": "synthetic",
+        "config": {"workload": "18q/10e UCCSD K=560 (seed 2, 16 Cholesky), batch 64 theta "
+                               "~N(0,0.05), energy+adjoint gradient, M=1 first-order Trotter",
+                   "state": "complex64 + FP64 reductions" if prec else "complex128",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "fwd_runs": info["n_fwd_runs"], "adj_runs": info["n_adj_runs"],
+                   "groups": info["n_groups"], "terms": info["n_terms"]},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        thetas = [th_host[b] for b in range(B)]
+        rate, dt, cores = oracle_rate(w, thetas, 12)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"12 of the 64 theta vectors ({dt:.1f} s, sector-restricted "
+                                          "FP64 oracle, OpenMP)"}
+    if rank == 0 and not args.no_scaleup:
+        line["scaleup"] = scaleup_26q(uc, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def scaleup_26q(uc, device):
+    import torch
+    w = synth.workload("26q")
+    out = {}
+    for name, prec in (("fp32", uc.FP32_STATE), ("fp64", uc.FP64)):
+        ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"],
+                              w["n_beta"], precision=prec, device=device)
+        th = torch.tensor(synth.theta_normal(ctx.K, 0.02, 1004), device="cuda",
+                          dtype=torch.float64).unsqueeze(0)
+        E = torch.empty(1, device="cuda", dtype=torch.float64)
+        G = torch.empty(1, ctx.K, device="cuda", dtype=torch.float64)
+        ctx.energy_grad_device(th, E, G)
+        torch.cuda.synchronize()
+        ctx.set_profiling(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps = 2
+        a.record()
+        for _ in range(steps):
+            ctx.energy_grad_device(th, E, G)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        prof = ctx.profile()
+        inf = ctx.info()
+        out[name] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "E": float(E[0].item()),
+                     "family_ms": {f: prof["ms"][f] / max(1, prof["calls"]) for f in prof["ms"]},
+                     "fwd_runs": inf["n_fwd_runs"], "adj_runs": inf["n_adj_runs"]}
+        del ctx
+        torch.cuda.empty_cache()
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * uccsd.h -- C ABI of the GB300 (sm_103a) VQE-UCCSD state-vector library.
+ *
+ * The library evaluates the energy and gradient of the Trotterised unitary
+ * coupled-cluster singles and doubles ansatz used for the correlation step
+ * of the FMO scheme in Sugisaki, Nakano and Mochizuki, "Size-consistency and
+ * orbital-invariance issues revealed by VQE-UCCSD calculations with the FMO
+ * scheme" (arXiv:2402.17993):
+ *
+ *   H      = sum_pq h_pq a+_p a_q + 1/2 sum_pqrs g_pqrs a+_p a+_q a_s a_r   (Eq. 2)
+ *   |Psi>  = exp(T - T+) |Psi_HF>                                           (Eq. 3)
+ *   T      = sum t_i^a a+_a a_i + 1/2 sum t_ij^ab a+_a a+_b a_j a_i        (Eq. 4)
+ *   exp(T - T+) ~ [ prod_k exp(theta_k G_k / M) ]^M   (first order, Eq. 5)
+ *   second order: [ prod_{1..K} exp(theta G/2M) prod_{K..1} exp(theta G/2M) ]^M (Eq. 6)
+ *   E      = <Psi|H|Psi>   (Section 2.3; evaluated exactly, no shot noise)
+ *
+ * Conventions (this library's readings of the paper, stated once here):
+ *   - Jordan-Wigner mapping; spin orbital P = 2p + s (s = 0 alpha, 1 beta) is
+ *     qubit P, and bit P of a basis index is its occupation.
+ *   - g_pqrs of Eq. 2 = <pq|rs> = (pr|qs) from chemist-notation spatial
+ *     integrals eri[p][q][r][s] = (pq|rs), with spin deltas.
+ *   - |Psi_HF> occupies the n_alpha lowest alpha and n_beta lowest beta
+ *     spin orbitals.
+ *   - One amplitude per excitation row (i, j, a, b) over spin orbitals;
+ *     singles use j = b = -1.  Generator G = tau - tau+ with
+ *     tau = a+_a a_i (single) or a+_a a+_b a_j a_i (double).
+ *   - The excitation list is the circuit order: row 0 acts first on |HF>.
+ *   - The gradient is dE/dtheta_k of the same Trotterised energy, from one
+ *     adjoint (reverse) sweep.
+ *
+ * Ownership: the caller owns every array passed in; the library copies what
+ * it keeps before returning.  A context owns all device memory it allocates
+ * and frees it in uccsd_destroy.  Device outputs are written on `stream`
+ * (a cudaStream_t passed as void*; NULL = legacy default stream) and are
+ * ready when that stream reaches the point of the call.  Host outputs are
+ * valid when the call returns (the call synchronises `stream`).
+ *
+ * Errors: every call returns a uccsd_status; nothing is thrown across the
+ * ABI and nothing exits.  uccsd_last_error() describes the last failure of a
+ * context.  A CUDA error marks the context as failed; later compute calls
+ * return UCCSD_ERR_STATE.
+ *
+ * Threading: a context is not thread-safe; use one context per host thread
+ * and stream.  Distinct contexts are independent.
+ */
+#ifndef UCCSD_GB300_H
+#define UCCSD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct uccsd_ctx uccsd_ctx;
+
+typedef enum {
+    UCCSD_OK = 0,
+    UCCSD_ERR_ARG = 1,     /* invalid argument (value, range, symmetry, finiteness) */
+    UCCSD_ERR_OOM = 2,     /* device allocation failed */
+    UCCSD_ERR_CUDA = 3,    /* a CUDA runtime call or kernel failed */
+    UCCSD_ERR_STATE = 4,   /* call order violated or context failed earlier */
+    UCCSD_ERR_TIMEOUT = 5, /* a bounded device wait gave up */
+    UCCSD_ERR_BUDGET = 6   /* requested footprint exceeds the context's HBM budget */
+} uccsd_status;
+
+typedef enum {
+    UCCSD_FP64 = 0,       /* complex128 state, FP64 arithmetic throughout */
+    UCCSD_FP32_STATE = 1  /* complex64 state and rotations; FP64 energy/gradient reductions */
+} uccsd_prec;
+
+typedef struct {
+    int n_qubits;         /* 2 * n_orb */
+    int n_orb, n_alpha, n_beta;
+    int K;                /* excitations (amplitudes) */
+    int n_ops;            /* factors in the Trotter schedule (K * M or 2 * K * M) */
+    int n_groups;         /* X-mask groups of the Jordan-Wigner Hamiltonian */
+    int n_terms;          /* Pauli terms of the Jordan-Wigner Hamiltonian */
+    int n_fwd_runs;       /* shared-memory passes of the forward sweep */
+    int n_adj_runs;       /* shared-memory passes of the adjoint sweep */
+    int batch;            /* state slots reserved */
+    int precision;        /* uccsd_prec */
+    size_t device_bytes;  /* device memory held by the context */
+    uint64_t launches;    /* kernels launched by this context so far */
+} uccsd_info_t;
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes = 0 means no
+ * budget; otherwise allocations that would exceed it fail with
+ * UCCSD_ERR_BUDGET before touching the device.  *out = NULL on failure. */
+uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec,
+                          size_t hbm_budget_bytes);
+
+/* Free all device memory of the context.  NULL is accepted. */
+void uccsd_destroy(uccsd_ctx *ctx);
+
+/* Context-owned message of the last failure; valid until the next call on
+ * the context.  Never NULL. */
+const char *uccsd_last_error(const uccsd_ctx *ctx);
+
+/* Static name of a status code. */
+const char *uccsd_status_string(uccsd_status st);
+
+/* Hamiltonian of Eq. 2 (Section 2.2) from spatial integrals.
+ *   h    n_orb*n_orb row-major, symmetric to 1e-12 (host pointer)
+ *   eri  n_orb^4 row-major chemist (pq|rs) with 8-fold symmetry to 1e-12
+ *   e_core constant energy added to H.
+ * 1 <= n_orb <= 15.  The Jordan-Wigner compile (X-mask/Z-mask grouping)
+ * runs on the host; its tables are copied to the device.  Non-finite or
+ * asymmetric input -> UCCSD_ERR_ARG.  Invalidates excitations and state. */
+uccsd_status uccsd_set_hamiltonian(uccsd_ctx *ctx, int n_orb, const double *h,
+                                   const double *eri, double e_core);
+
+/* Reference determinant |Psi_HF> (Eq. 3): n_alpha, n_beta electrons in the
+ * lowest spin orbitals of each spin.  Needs the Hamiltonian first. */
+uccsd_status uccsd_set_reference(uccsd_ctx *ctx, int n_alpha, int n_beta);
+
+/* Stateless builder of the spin-conserving UCCSD list of Eq. 4: singles
+ * (i, -1, a, -1) with i occupied, a virtual, same spin; then doubles
+ * (i, j, a, b), i < j occupied, a < b virtual, spin multiset conserved;
+ * each block in lexicographic order.  Writes min(count, cap) rows of 4
+ * int32 to `out` (host; may be NULL when cap = 0) and the full count to
+ * *n_out. */
+uccsd_status uccsd_build_uccsd_list(int n_orb, int n_alpha, int n_beta,
+                                    int32_t *out, int cap, int *n_out);
+
+/* Ordered excitation list (host, K rows of (i, j, a, b); j = b = -1 for
+ * singles) and the Trotter schedule of Eq. 5 (trotter_order = 1) or Eq. 6
+ * (trotter_order = 2) with n_slices = M >= 1.  Every row must map occupied
+ * to virtual orbitals of |Psi_HF> and conserve spin.  Needs the reference. */
+uccsd_status uccsd_set_excitations(uccsd_ctx *ctx, int K, const int32_t *ijab,
+                                   int trotter_order, int n_slices);
+
+/* Reserve B >= 1 state slots for the batched call (default 1). */
+uccsd_status uccsd_set_batch(uccsd_ctx *ctx, int B);
+
+/* Energy of slot 0 for amplitudes theta[K].  theta_on_device != 0: theta
+ * and E are device pointers (E: one double), written on `stream`;
+ * otherwise host pointers and the call synchronises. */
+uccsd_status uccsd_energy(uccsd_ctx *ctx, const double *theta, int theta_on_device,
+                          double *E, void *stream);
+
+/* Energy and the gradient dE/dtheta[K] (adjoint sweep) of slot 0.
+ * grad has the residency of theta. */
+uccsd_status uccsd_energy_grad(uccsd_ctx *ctx, const double *theta, int theta_on_device,
+                               double *E, double *grad, void *stream);
+
+/* B independent evaluations of the same fragment: theta is B*K row-major,
+ * E is B, grad is B*K (or NULL for energies only).  1 <= B <= reserved
+ * batch.  Same residency rules as uccsd_energy_grad. */
+uccsd_status uccsd_energy_grad_batch(uccsd_ctx *ctx, int B, const double *theta,
+                                     int theta_on_device, double *E, double *grad,
+                                     void *stream);
+
+/* Copy the state vector of slot `slot` after the last uccsd_energy or
+ * energies-only batch call to host memory as 2*2^n interleaved (re, im)
+ * doubles.  len must be >= 2*2^n.  Synchronises the context's last stream.
+ * After a gradient call the slot holds the swept-back state instead. */
+uccsd_status uccsd_get_state(uccsd_ctx *ctx, int slot, double *out_re_im, size_t len);
+
+/* Sizes and counters of the context. */
+uccsd_status uccsd_info(const uccsd_ctx *ctx, uccsd_info_t *info);
+
+/* Kernel families of the evaluation, for uccsd_get_profile. */
+enum {
+    UCCSD_K_CS = 0,       /* cos/sin of the schedule factors */
+    UCCSD_K_FORWARD = 1,  /* forward sweep passes (Eq. 5 / Eq. 6) */
+    UCCSD_K_HAPPLY = 2,   /* H psi and energy partials (Eq. 2, Section 2.3) */
+    UCCSD_K_ADJOINT = 3,  /* adjoint sweep passes (gradient) */
+    UCCSD_K_REDUCE = 4,   /* final energy/gradient reductions */
+    UCCSD_K_FAMILIES = 5
+};
+
+typedef struct {
+    double ms[UCCSD_K_FAMILIES];        /* accumulated device time per family */
+    uint64_t launches[UCCSD_K_FAMILIES];
+    uint64_t calls;                     /* evaluations profiled */
+} uccsd_profile_t;
+
+/* Profiling (off by default): with on != 0 every evaluation records CUDA
+ * events around each kernel family on the evaluation stream and
+ * synchronises at its end to accumulate the device times; on = 0 stops it.
+ * Either call resets the accumulators. */
+uccsd_status uccsd_set_profiling(uccsd_ctx *ctx, int on);
+uccsd_status uccsd_get_profile(const uccsd_ctx *ctx, uccsd_profile_t *out);
+
+/* Host-only: Jordan-Wigner compile statistics of the Hamiltonian of Eq. 2
+ * without creating a context (no device use).  Any output may be NULL. */
+uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *eri,
+                                     double e_core, int *n_groups, int *n_terms);
+
+/* Host-only: the compiled Jordan-Wigner Pauli terms of Eq. 2 in the
+ * X^x Z^z form: H = sum_t coef[t] X^{xmask[t]} Z^{zmask[t]}, where
+ * X^x Z^z |y> = (-1)^{popcount(y & z)} |y ^ x>.  Writes min(count, cap)
+ * terms and *n_out = count.  Any array may be NULL when cap = 0. */
+uccsd_status uccsd_pauli_terms(int n_orb, const double *h, const double *eri, double e_core,
+                               uint32_t *xmask, uint32_t *zmask, double *coef, int cap,
+                               int *n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* UCCSD_GB300_H */

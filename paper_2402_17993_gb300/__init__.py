@@ -1,0 +1,304 @@
+"""GB300 (sm_103a) VQE-UCCSD state-vector library: Python binding.
+
+Thin ctypes marshalling over the C ABI declared in ``include/uccsd.h``
+(Trotterised UCCSD energy and adjoint gradient of arXiv:2402.17993,
+Eqs. 2-6).  Every step of the computation runs in the CUDA library; this
+module only moves arguments.  PyTorch is used for device tensors and
+streams.  If the compiled library is missing, importing a function that
+needs it raises immediately: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libuccsd_gb300.so")
+
+FP64 = 0
+FP32_STATE = 1
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "device out of memory", 3: "CUDA error",
+          4: "invalid call order or failed context", 5: "device wait timed out",
+          6: "HBM budget exceeded"}
+
+# Symbols of include/uccsd.h (checked by the CPU test suite).
+EXPORTS = [
+    "uccsd_create", "uccsd_destroy", "uccsd_last_error", "uccsd_status_string",
+    "uccsd_set_hamiltonian", "uccsd_set_reference", "uccsd_build_uccsd_list",
+    "uccsd_set_excitations", "uccsd_set_batch", "uccsd_energy", "uccsd_energy_grad",
+    "uccsd_energy_grad_batch", "uccsd_get_state", "uccsd_info", "uccsd_hamiltonian_stats",
+    "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile",
+]
+
+FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
+
+
+class UCCSDError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("n_orb", ctypes.c_int), ("n_alpha", ctypes.c_int),
+                ("n_beta", ctypes.c_int), ("K", ctypes.c_int), ("n_ops", ctypes.c_int),
+                ("n_groups", ctypes.c_int), ("n_terms", ctypes.c_int),
+                ("n_fwd_runs", ctypes.c_int), ("n_adj_runs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("precision", ctypes.c_int),
+                ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_uint64 * 5),
+                ("calls", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"UCCSD CUDA library not built ({LIB_PATH}); "
+                               "run `python -m paper_2402_17993_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        L.uccsd_create.argtypes = [ctypes.POINTER(vp), ip, ip, ctypes.c_size_t]
+        L.uccsd_destroy.argtypes = [vp]
+        L.uccsd_destroy.restype = None
+        L.uccsd_last_error.argtypes = [vp]
+        L.uccsd_last_error.restype = ctypes.c_char_p
+        L.uccsd_status_string.argtypes = [ip]
+        L.uccsd_status_string.restype = ctypes.c_char_p
+        L.uccsd_set_hamiltonian.argtypes = [vp, ip, f64p, f64p, ctypes.c_double]
+        L.uccsd_set_reference.argtypes = [vp, ip, ip]
+        L.uccsd_build_uccsd_list.argtypes = [ip, ip, ip, i32p, ip, ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_set_excitations.argtypes = [vp, ip, i32p, ip, ip]
+        L.uccsd_set_batch.argtypes = [vp, ip]
+        L.uccsd_energy.argtypes = [vp, dp, ip, dp, vp]
+        L.uccsd_energy_grad.argtypes = [vp, dp, ip, dp, dp, vp]
+        L.uccsd_energy_grad_batch.argtypes = [vp, ip, dp, ip, dp, dp, vp]
+        L.uccsd_get_state.argtypes = [vp, ip, f64p, ctypes.c_size_t]
+        L.uccsd_info.argtypes = [vp, ctypes.POINTER(Info)]
+        L.uccsd_hamiltonian_stats.argtypes = [ip, f64p, f64p, ctypes.c_double,
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_set_profiling.argtypes = [vp, ip]
+        L.uccsd_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
+        L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
+                                        ctypes.POINTER(ctypes.c_int)]
+        _lib = L
+    return _lib
+
+
+def _f64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# Host-only entry points
+# ---------------------------------------------------------------------------
+def build_uccsd_list(n_orb: int, n_alpha: int, n_beta: int) -> np.ndarray:
+    L = lib()
+    n = ctypes.c_int(0)
+    st = L.uccsd_build_uccsd_list(n_orb, n_alpha, n_beta, None, 0, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "build_uccsd_list")
+    out = np.zeros((n.value, 4), dtype=np.int32)
+    st = L.uccsd_build_uccsd_list(n_orb, n_alpha, n_beta, _i32p(out), n.value, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "build_uccsd_list")
+    return out
+
+
+def hamiltonian_stats(n_orb, h, eri, e_core=0.0):
+    g, t = ctypes.c_int(0), ctypes.c_int(0)
+    h, eri = _c64(h), _c64(eri)
+    st = lib().uccsd_hamiltonian_stats(n_orb, _f64p(h), _f64p(eri), float(e_core),
+                                       ctypes.byref(g), ctypes.byref(t))
+    if st:
+        raise UCCSDError(st, "hamiltonian_stats")
+    return g.value, t.value
+
+
+def pauli_terms(n_orb, h, eri, e_core=0.0):
+    """Compiled Jordan-Wigner terms: (xmask, zmask, coef) with
+    H = sum coef X^xmask Z^zmask."""
+    L = lib()
+    h, eri = _c64(h), _c64(eri)
+    n = ctypes.c_int(0)
+    st = L.uccsd_pauli_terms(n_orb, _f64p(h), _f64p(eri), float(e_core), None, None, None, 0,
+                             ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "pauli_terms")
+    x = np.zeros(n.value, dtype=np.uint32)
+    z = np.zeros(n.value, dtype=np.uint32)
+    c = np.zeros(n.value, dtype=np.float64)
+    st = L.uccsd_pauli_terms(n_orb, _f64p(h), _f64p(eri), float(e_core),
+                             x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                             z.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), _f64p(c), n.value,
+                             ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "pauli_terms")
+    return x, z, c
+
+
+# ---------------------------------------------------------------------------
+# Context
+# ---------------------------------------------------------------------------
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One fragment (Hamiltonian + reference + excitation list) on one GPU."""
+
+    def __init__(self, device: int = 0, precision: int = FP64, hbm_budget_bytes: int = 0):
+        self._L = lib()
+        self._c = ctypes.c_void_p(None)
+        st = self._L.uccsd_create(ctypes.byref(self._c), device, precision, hbm_budget_bytes)
+        if st:
+            raise UCCSDError(st, "uccsd_create")
+        self.device = device
+        self.precision = precision
+        self.K = 0
+        self.n_qubits = 0
+
+    def _check(self, st, what):
+        if st:
+            msg = self._L.uccsd_last_error(self._c).decode()
+            raise UCCSDError(st, f"{what}: {msg}")
+
+    def close(self):
+        if self._c:
+            self._L.uccsd_destroy(self._c)
+            self._c = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_hamiltonian(self, n_orb, h, eri, e_core=0.0):
+        h, eri = _c64(h), _c64(eri)
+        self._check(self._L.uccsd_set_hamiltonian(self._c, n_orb, _f64p(h), _f64p(eri),
+                                                  float(e_core)), "set_hamiltonian")
+        self.n_qubits = 2 * n_orb
+        return self
+
+    def set_reference(self, n_alpha, n_beta):
+        self._check(self._L.uccsd_set_reference(self._c, n_alpha, n_beta), "set_reference")
+        return self
+
+    def set_excitations(self, ijab, trotter_order=1, n_slices=1):
+        ijab = np.ascontiguousarray(ijab, dtype=np.int32).reshape(-1, 4)
+        self._check(self._L.uccsd_set_excitations(self._c, ijab.shape[0], _i32p(ijab),
+                                                  trotter_order, n_slices), "set_excitations")
+        self.K = ijab.shape[0]
+        return self
+
+    def set_batch(self, B):
+        self._check(self._L.uccsd_set_batch(self._c, B), "set_batch")
+        return self
+
+    # -- host-buffer calls (synchronising) --
+    def energy(self, theta, stream=None):
+        th = _c64(theta).reshape(self.K)
+        E = np.zeros(1)
+        self._check(self._L.uccsd_energy(self._c, th.ctypes.data, 0, E.ctypes.data,
+                                         _stream_ptr(stream)), "energy")
+        return float(E[0])
+
+    def energy_grad(self, theta, stream=None):
+        th = _c64(theta).reshape(self.K)
+        E = np.zeros(1)
+        g = np.zeros(max(self.K, 1))
+        self._check(self._L.uccsd_energy_grad(self._c, th.ctypes.data, 0, E.ctypes.data,
+                                              g.ctypes.data, _stream_ptr(stream)), "energy_grad")
+        return float(E[0]), g[:self.K].copy()
+
+    def energy_grad_batch(self, theta, grad=True, stream=None):
+        th = _c64(theta).reshape(-1, self.K)
+        B = th.shape[0]
+        E = np.zeros(B)
+        g = np.zeros((B, max(self.K, 1)))
+        self._check(self._L.uccsd_energy_grad_batch(self._c, B, th.ctypes.data, 0, E.ctypes.data,
+                                                    g.ctypes.data if grad else None,
+                                                    _stream_ptr(stream)), "energy_grad_batch")
+        return E, (g[:, :self.K].copy() if grad else None)
+
+    # -- device-tensor calls (asynchronous on the stream) --
+    def energy_grad_device(self, theta, E, grad, stream=None):
+        """theta: CUDA float64 tensor (B, K) or (K,); E: (B,); grad: (B, K) or None."""
+        B = 1 if theta.dim() == 1 else theta.shape[0]
+        assert theta.is_cuda and theta.dtype.is_floating_point and theta.is_contiguous()
+        gp = None if grad is None else grad.data_ptr()
+        self._check(self._L.uccsd_energy_grad_batch(self._c, B, theta.data_ptr(), 1, E.data_ptr(),
+                                                    gp, _stream_ptr(stream)),
+                    "energy_grad_batch(device)")
+
+    def state(self, slot=0):
+        N = 1 << self.n_qubits
+        out = np.zeros(2 * N)
+        self._check(self._L.uccsd_get_state(self._c, slot, _f64p(out), out.size), "get_state")
+        return out.view(np.complex128)
+
+    def set_profiling(self, on=True):
+        self._check(self._L.uccsd_set_profiling(self._c, 1 if on else 0), "set_profiling")
+
+    def profile(self):
+        p = Profile()
+        self._check(self._L.uccsd_get_profile(self._c, ctypes.byref(p)), "get_profile")
+        return {"ms": dict(zip(FAMILIES, list(p.ms))),
+                "launches": dict(zip(FAMILIES, list(p.launches))), "calls": p.calls}
+
+    def energy_grad_ptr(self, B, theta_ptr, E_ptr, grad_ptr, on_device, stream=None):
+        """Raw-pointer call (host pinned or device buffers)."""
+        self._check(self._L.uccsd_energy_grad_batch(self._c, B, theta_ptr, 1 if on_device else 0,
+                                                    E_ptr, grad_ptr, _stream_ptr(stream)),
+                    "energy_grad_batch(ptr)")
+
+    def info(self):
+        inf = Info()
+        self._check(self._L.uccsd_info(self._c, ctypes.byref(inf)), "info")
+        return inf.as_dict()
+
+
+def make_context(n_orb, h, eri, e_core, n_alpha, n_beta, ijab=None, precision=FP64, device=0,
+                 batch=1, trotter_order=1, n_slices=1, hbm_budget_bytes=0):
+    ctx = Context(device, precision, hbm_budget_bytes)
+    ctx.set_hamiltonian(n_orb, h, eri, e_core).set_reference(n_alpha, n_beta)
+    if ijab is None:
+        ijab = build_uccsd_list(n_orb, n_alpha, n_beta)
+    ctx.set_excitations(ijab, trotter_order, n_slices)
+    if batch != 1:
+        ctx.set_batch(batch)
+    return ctx
+
+
+from .autograd import UCCSDEnergy, uccsd_energy  # noqa: E402,F401

@@ -1,0 +1,718 @@
+// C ABI of the UCCSD library (declared in include/uccsd.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/uccsd.h"
+#include "jw.hpp"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+using namespace uccsd;
+
+namespace {
+
+// Tile bits of the kernels per precision (shared memory per CTA):
+//   forward  FP32 13 (64 KiB), FP64 12 (64 KiB)
+//   adjoint  FP32 12 (2 x 32 KiB), FP64 11 (2 x 32 KiB)
+//   H-apply  12 (32 / 64 KiB)
+constexpr int kFwdL[2] = {12, 13};
+constexpr int kAdjL[2] = {11, 12};
+constexpr int kHL = 12;
+constexpr int kCmin = 3;
+
+template <typename R>
+struct HamTables {
+    std::vector<GroupT<R>> groups;
+    std::vector<int32_t> seg_begin;
+    std::vector<uint32_t> seg_d;
+    std::vector<R> spec;
+};
+
+template <typename R>
+HamTables<R> make_tables(const CompiledH &H, int LH) {
+    HamTables<R> T;
+    std::vector<std::pair<uint32_t, int>> order;  // (sort key, group index)
+    for (size_t g = 0; g < H.groups.size(); ++g) {
+        uint32_t d = H.groups[g].xmask >> LH;
+        order.push_back({d == 0 ? 0xFFFFFFFFu : d, int(g)});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<uint32_t, int> &a, const std::pair<uint32_t, int> &b) {
+                         return a.first < b.first;
+                     });
+    uint32_t cur = 0;
+    bool open = false;
+    for (auto &kv : order) {
+        const GroupT<double> &s = H.groups[kv.second];
+        if (!open || kv.first != cur) {
+            T.seg_begin.push_back(int(T.groups.size()));
+            T.seg_d.push_back(kv.first == 0xFFFFFFFFu ? 0u : kv.first);
+            cur = kv.first;
+            open = true;
+        }
+        GroupT<R> g{};
+        g.xmask = s.xmask;
+        g.jmask = s.jmask;
+        g.nb = s.nb;
+        g.spec = s.spec;
+        g.active = s.active;
+        for (int k = 0; k < 4; ++k) g.pos[k] = s.pos[k];
+        for (int p = 0; p < 16; ++p) g.lut[p] = R(s.lut[p]);
+        T.groups.push_back(g);
+    }
+    // the own-tile (d = 0) segment is always last, possibly empty
+    if (T.seg_d.empty() || cur != 0xFFFFFFFFu) {
+        T.seg_begin.push_back(int(T.groups.size()));
+        T.seg_d.push_back(0u);
+    }
+    T.seg_begin.push_back(int(T.groups.size()));
+    for (double v : H.spec) T.spec.push_back(R(v));
+    if (T.spec.empty()) T.spec.push_back(R(0));
+    return T;
+}
+
+}  // namespace
+
+struct uccsd_ctx {
+    int device = 0;
+    int prec = 0;  // 0 FP64, 1 FP32 state
+    size_t budget = 0;
+    size_t bytes = 0;
+    std::string err;
+    bool failed = false;
+    uint64_t launches = 0;
+    cudaStream_t last_stream = nullptr;
+
+    // problem
+    int n_orb = 0, n = 0;
+    bool have_h = false, have_ref = false, have_exc = false;
+    int n_alpha = 0, n_beta = 0;
+    uint32_t hf = 0;
+    CompiledH H;
+    int K = 0, order = 1, M = 1;
+    std::vector<int32_t> ijab, op_k;
+    std::vector<double> op_scale;
+    SweepPlan fwd, adj;
+    int LH = kHL;
+    int B = 1;          // reserved slots
+    bool state_valid = false;
+
+    // device memory: name -> (ptr, bytes)
+    std::map<std::string, std::pair<void *, size_t>> mem;
+
+    // Hamiltonian views
+    DevHam<float> hf32;
+    DevHam<double> hf64;
+
+    // diagonal in fixed point; energy shift (the reference determinant's
+    // diagonal energy) applied to H on the device and added back in FP64
+    std::vector<long long> diag_qa, diag_qb;
+    double diag_unit = 0.0;
+    double shift = 0.0;
+
+    // profiling
+    bool profiling = false;
+    uccsd_profile_t prof{};
+    std::vector<cudaEvent_t> events;
+};
+
+namespace {
+
+uccsd_status fail(uccsd_ctx *c, uccsd_status st, const std::string &msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+uccsd_status cuda_fail(uccsd_ctx *c, cudaError_t e, const char *what) {
+    c->failed = true;
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return UCCSD_ERR_CUDA;
+}
+
+void release(uccsd_ctx *c, const std::string &name) {
+    auto it = c->mem.find(name);
+    if (it == c->mem.end()) return;
+    cudaFree(it->second.first);
+    c->bytes -= it->second.second;
+    c->mem.erase(it);
+}
+
+// (Re)allocate a named device buffer; contents are undefined.
+uccsd_status dalloc(uccsd_ctx *c, const std::string &name, size_t bytes, void **out) {
+    auto it = c->mem.find(name);
+    if (it != c->mem.end() && it->second.second == bytes) {
+        *out = it->second.first;
+        return UCCSD_OK;
+    }
+    release(c, name);
+    bytes = std::max<size_t>(bytes, 16);
+    if (c->budget && c->bytes + bytes > c->budget)
+        return fail(c, UCCSD_ERR_BUDGET, "device footprint of '" + name + "' exceeds the HBM budget");
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, UCCSD_ERR_OOM, "cudaMalloc of '" + name + "' failed: " + cudaGetErrorString(e));
+    }
+    c->mem[name] = {p, bytes};
+    c->bytes += bytes;
+    *out = p;
+    return UCCSD_OK;
+}
+
+void *dptr(uccsd_ctx *c, const std::string &name) {
+    auto it = c->mem.find(name);
+    return it == c->mem.end() ? nullptr : it->second.first;
+}
+
+template <typename T>
+uccsd_status upload(uccsd_ctx *c, const std::string &name, const std::vector<T> &v, T **out) {
+    void *p = nullptr;
+    uccsd_status st = dalloc(c, name, sizeof(T) * std::max<size_t>(v.size(), 1), &p);
+    if (st) return st;
+    if (!v.empty()) {
+        cudaError_t e = cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "upload");
+    }
+    *out = static_cast<T *>(p);
+    return UCCSD_OK;
+}
+
+// Fixed-point form of the diagonal: unit 2^-k with k chosen so that every
+// partial sum of |c0| + sum |a| + sum |b| (times 2 for the shift) fits in
+// 62 bits.  Quantisation error <= 2^-(k+1) per term.
+void make_fixed_point(uccsd_ctx *c) {
+    const CompiledH &H = c->H;
+    double bound = std::fabs(H.c0);
+    for (double v : H.diag_a) bound += std::fabs(v);
+    for (double v : H.diag_b) bound += std::fabs(v);
+    bound = 2.0 * bound + 1.0;
+    int k = 61 - int(std::ceil(std::log2(bound)));
+    k = std::max(0, std::min(k, 60));
+    double scale = std::ldexp(1.0, k);
+    c->diag_unit = std::ldexp(1.0, -k);
+    c->diag_qa.resize(H.diag_a.size());
+    c->diag_qb.resize(H.diag_b.size());
+    for (size_t i = 0; i < H.diag_a.size(); ++i) c->diag_qa[i] = std::llround(H.diag_a[i] * scale);
+    for (size_t i = 0; i < H.diag_b.size(); ++i) c->diag_qb[i] = std::llround(H.diag_b[i] * scale);
+}
+
+// Diagonal constant after the shift, in fixed point.
+long long shifted_q0(const uccsd_ctx *c) {
+    return std::llround((c->H.c0 - c->shift) / c->diag_unit);
+}
+
+template <typename R>
+uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
+    HamTables<R> T = make_tables<R>(c->H, c->LH);
+    std::string t(tag);
+    GroupT<R> *g;
+    int32_t *sb;
+    uint32_t *sd;
+    R *sp;
+    long long *qa, *qb;
+    uccsd_status st;
+    if ((st = upload(c, t + "groups", T.groups, &g))) return st;
+    if ((st = upload(c, t + "seg_begin", T.seg_begin, &sb))) return st;
+    if ((st = upload(c, t + "seg_d", T.seg_d, &sd))) return st;
+    if ((st = upload(c, t + "spec", T.spec, &sp))) return st;
+    if ((st = upload(c, "diag_qa", c->diag_qa, &qa))) return st;
+    if ((st = upload(c, "diag_qb", c->diag_qb, &qb))) return st;
+    dh->groups = g;
+    dh->seg_begin = sb;
+    dh->seg_d = sd;
+    dh->n_seg = int(T.seg_d.size());
+    dh->spec = sp;
+    dh->diag_qa = qa;
+    dh->diag_qb = qb;
+    dh->diag_q0 = shifted_q0(c);
+    dh->diag_unit = c->diag_unit;
+    dh->has_diag = c->H.has_diag ? 1 : 0;
+    dh->n = c->n;
+    return UCCSD_OK;
+}
+
+size_t state_bytes(const uccsd_ctx *c) { return size_t(1) << c->n; }
+size_t amp_bytes(const uccsd_ctx *c) { return c->prec ? 8 : 16; }
+int n_tiles_h(const uccsd_ctx *c) { return 1 << (c->n - c->LH); }
+int n_tiles_a(const uccsd_ctx *c) { return c->adj.runs.empty() ? 1 : 1 << (c->n - c->adj.L); }
+
+// Per-slot buffers sized for c->B slots.
+uccsd_status alloc_slots(uccsd_ctx *c) {
+    if (!c->have_exc) return UCCSD_OK;
+    void *p;
+    uccsd_status st;
+    const size_t B = c->B;
+    const size_t n_ops = std::max<size_t>(c->op_k.size(), 1);
+    if ((st = dalloc(c, "psi", B * state_bytes(c) * amp_bytes(c), &p))) return st;
+    if ((st = dalloc(c, "sig", B * state_bytes(c) * amp_bytes(c), &p))) return st;
+    if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
+    if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
+    if ((st = dalloc(c, "E", B * sizeof(double), &p))) return st;
+    if ((st = dalloc(c, "grad", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
+    if ((st = dalloc(c, "Epart", 2 * B * n_tiles_h(c) * sizeof(double), &p))) return st;
+    if ((st = dalloc(c, "gpart", B * n_ops * n_tiles_a(c) * sizeof(double), &p))) return st;
+    return UCCSD_OK;
+}
+
+bool finite_all(const double *v, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+uccsd_status check_hamiltonian_input(uccsd_ctx *c, int n_orb, const double *h, const double *eri,
+                                     double e_core) {
+    if (n_orb < 1 || n_orb > 15) return fail(c, UCCSD_ERR_ARG, "n_orb must be in [1, 15]");
+    if (!h || !eri) return fail(c, UCCSD_ERR_ARG, "null integral pointer");
+    const size_t no = n_orb;
+    if (!finite_all(h, no * no) || !finite_all(eri, no * no * no * no) || !std::isfinite(e_core))
+        return fail(c, UCCSD_ERR_ARG, "non-finite integral");
+    for (size_t p = 0; p < no; ++p)
+        for (size_t q = 0; q < no; ++q)
+            if (std::fabs(h[p * no + q] - h[q * no + p]) > 1e-12)
+                return fail(c, UCCSD_ERR_ARG, "h is not symmetric");
+    auto E = [&](size_t p, size_t q, size_t r, size_t s) { return eri[((p * no + q) * no + r) * no + s]; };
+    for (size_t p = 0; p < no; ++p)
+        for (size_t q = 0; q < no; ++q)
+            for (size_t r = 0; r < no; ++r)
+                for (size_t s = 0; s < no; ++s) {
+                    double v = E(p, q, r, s);
+                    if (std::fabs(v - E(q, p, r, s)) > 1e-12 || std::fabs(v - E(p, q, s, r)) > 1e-12 ||
+                        std::fabs(v - E(r, s, p, q)) > 1e-12)
+                        return fail(c, UCCSD_ERR_ARG, "eri lacks the 8-fold permutational symmetry");
+                }
+    return UCCSD_OK;
+}
+
+// Event marker between kernel families (profiling only).
+struct Marks {
+    uccsd_ctx *c;
+    cudaStream_t s;
+    std::vector<std::pair<int, int>> spans;  // (family, event index of its start)
+    int next = 0;
+    void begin(int fam) {
+        if (!c->profiling) return;
+        if (next >= int(c->events.size())) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->events.push_back(e);
+        }
+        cudaEventRecord(c->events[next], s);
+        spans.push_back({fam, next});
+        ++next;
+    }
+    void finish() {
+        if (!c->profiling) return;
+        begin(-1);
+        cudaEventSynchronize(c->events[next - 1]);
+        for (size_t i = 0; i + 1 < spans.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, c->events[spans[i].second], c->events[spans[i + 1].second]);
+            c->prof.ms[spans[i].first] += ms;
+        }
+        c->prof.calls++;
+    }
+};
+
+template <typename R>
+uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, double *E, double *grad,
+                      cudaStream_t stream) {
+    const size_t N = state_bytes(c);
+    LaunchCfg cfg;
+    cfg.n = c->n;
+    cfg.N = N;
+    cfg.B = B;
+    cfg.n_ops = int(c->op_k.size());
+    cfg.stream = stream;
+    const int K = c->K;
+    cudaError_t e;
+    double *d_theta = static_cast<double *>(dptr(c, "theta"));
+    const double *th = theta;
+    if (!on_dev) {
+        e = cudaMemcpyAsync(d_theta, theta, sizeof(double) * B * K, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "theta upload");
+        th = d_theta;
+    }
+    void *psi = dptr(c, "psi"), *sig = dptr(c, "sig"), *cs = dptr(c, "cs");
+    double *Epart = static_cast<double *>(dptr(c, "Epart"));
+    double *gpart = static_cast<double *>(dptr(c, "gpart"));
+    const int32_t *d_op_k = static_cast<const int32_t *>(dptr(c, "op_k"));
+    const double *d_op_scale = static_cast<const double *>(dptr(c, "op_scale"));
+    Marks mk{c, stream};
+    if (cfg.n_ops > 0) {
+        mk.begin(UCCSD_K_CS);
+        if ((e = launch_cs<R>(cfg, th, K, d_op_k, d_op_scale, cs)) != cudaSuccess)
+            return cuda_fail(c, e, "cs kernel");
+        ++c->launches;
+        c->prof.launches[UCCSD_K_CS]++;
+    }
+    const OpDev *fops = static_cast<const OpDev *>(dptr(c, "fwd_ops"));
+    mk.begin(UCCSD_K_FORWARD);
+    for (size_t r = 0; r < c->fwd.runs.size(); ++r) {
+        if ((e = launch_forward_run<R>(cfg, psi, c->fwd.runs[r], fops, cs, r == 0 ? 1 : 0, c->hf)) !=
+            cudaSuccess)
+            return cuda_fail(c, e, "forward kernel");
+        ++c->launches;
+        c->prof.launches[UCCSD_K_FORWARD]++;
+    }
+    const DevHam<R> &H = *reinterpret_cast<const DevHam<R> *>(sizeof(R) == 4 ? (const void *)&c->hf32
+                                                                             : (const void *)&c->hf64);
+    mk.begin(UCCSD_K_HAPPLY);
+    if ((e = launch_happly<R>(cfg, psi, sig, c->LH, H, Epart, grad ? 1 : 0)) != cudaSuccess)
+        return cuda_fail(c, e, "H-apply kernel");
+    ++c->launches;
+    c->prof.launches[UCCSD_K_HAPPLY]++;
+    if (grad) {
+        const OpDev *aops = static_cast<const OpDev *>(dptr(c, "adj_ops"));
+        mk.begin(UCCSD_K_ADJOINT);
+        for (int r = int(c->adj.runs.size()) - 1; r >= 0; --r) {
+            if ((e = launch_adjoint_run<R>(cfg, psi, sig, c->adj.runs[r], aops, cs, gpart,
+                                           n_tiles_a(c))) != cudaSuccess)
+                return cuda_fail(c, e, "adjoint kernel");
+            ++c->launches;
+            c->prof.launches[UCCSD_K_ADJOINT]++;
+        }
+    }
+    mk.begin(UCCSD_K_REDUCE);
+    double *dE = on_dev ? E : static_cast<double *>(dptr(c, "E"));
+    double *dG = grad ? (on_dev ? grad : static_cast<double *>(dptr(c, "grad"))) : nullptr;
+    if ((e = launch_reduce(cfg, Epart, n_tiles_h(c), gpart, n_tiles_a(c), K,
+                           static_cast<const int32_t *>(dptr(c, "k_ptr")),
+                           static_cast<const int32_t *>(dptr(c, "k_ops")), d_op_scale, c->shift,
+                           c->prec ? 1 : 0, dE, dG)) !=
+        cudaSuccess)
+        return cuda_fail(c, e, "reduce kernel");
+    ++c->launches;
+    c->prof.launches[UCCSD_K_REDUCE]++;
+    mk.finish();
+    c->state_valid = (grad == nullptr);
+    c->last_stream = stream;
+    if (!on_dev) {
+        e = cudaMemcpyAsync(E, dE, sizeof(double) * B, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && grad)
+            e = cudaMemcpyAsync(grad, dG, sizeof(double) * B * K, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "result download");
+    }
+    return UCCSD_OK;
+}
+
+uccsd_status eval(uccsd_ctx *c, int B, const double *theta, int on_dev, double *E, double *grad,
+                  void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
+    if (B < 1 || B > c->B) return fail(c, UCCSD_ERR_ARG, "batch size outside the reserved slots");
+    if ((!theta && c->K > 0) || !E) return fail(c, UCCSD_ERR_ARG, "null theta or E");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (c->prec) return run_eval<float>(c, B, theta, on_dev, E, grad, s);
+    return run_eval<double>(c, B, theta, on_dev, E, grad, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec, size_t hbm_budget_bytes) {
+    if (!out) return UCCSD_ERR_ARG;
+    *out = nullptr;
+    if (prec != UCCSD_FP64 && prec != UCCSD_FP32_STATE) return UCCSD_ERR_ARG;
+    int nd = 0;
+    if (cudaGetDeviceCount(&nd) != cudaSuccess || device < 0 || device >= nd) {
+        cudaGetLastError();
+        return UCCSD_ERR_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return UCCSD_ERR_CUDA;
+    if (configure_kernels() != cudaSuccess) return UCCSD_ERR_CUDA;
+    uccsd_ctx *c = new uccsd_ctx();
+    c->device = device;
+    c->prec = int(prec);
+    c->budget = hbm_budget_bytes;
+    *out = c;
+    return UCCSD_OK;
+}
+
+void uccsd_destroy(uccsd_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (auto &kv : c->mem) cudaFree(kv.second.first);
+    delete c;
+}
+
+const char *uccsd_last_error(const uccsd_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+const char *uccsd_status_string(uccsd_status st) {
+    switch (st) {
+        case UCCSD_OK: return "ok";
+        case UCCSD_ERR_ARG: return "invalid argument";
+        case UCCSD_ERR_OOM: return "device out of memory";
+        case UCCSD_ERR_CUDA: return "CUDA error";
+        case UCCSD_ERR_STATE: return "invalid call order or failed context";
+        case UCCSD_ERR_TIMEOUT: return "device wait timed out";
+        case UCCSD_ERR_BUDGET: return "HBM budget exceeded";
+    }
+    return "unknown status";
+}
+
+uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, const double *eri,
+                                   double e_core) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    uccsd_status st = check_hamiltonian_input(c, n_orb, h, eri, e_core);
+    if (st) return st;
+    CompiledH H;
+    std::string err;
+    if (!compile_hamiltonian(n_orb, h, eri, e_core, &H, &err)) return fail(c, UCCSD_ERR_ARG, err);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    c->n_orb = n_orb;
+    c->n = 2 * n_orb;
+    c->H = std::move(H);
+    c->LH = std::min(kHL, c->n);
+    c->have_h = c->have_ref = c->have_exc = false;
+    c->state_valid = false;
+    c->shift = 0.0;
+    make_fixed_point(c);
+    if ((st = upload_ham<float>(c, &c->hf32, "h32_"))) return st;
+    if ((st = upload_ham<double>(c, &c->hf64, "h64_"))) return st;
+    c->have_h = true;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_set_reference(uccsd_ctx *c, int n_alpha, int n_beta) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (!c->have_h) return fail(c, UCCSD_ERR_STATE, "set_hamiltonian must come first");
+    if (n_alpha < 0 || n_beta < 0 || n_alpha > c->n_orb || n_beta > c->n_orb)
+        return fail(c, UCCSD_ERR_ARG, "electron counts out of range");
+    c->n_alpha = n_alpha;
+    c->n_beta = n_beta;
+    c->hf = uint32_t(hf_bits(n_alpha, n_beta));
+    // shift = <HF|H|HF> from the diagonal quadratic form (FP64)
+    double sft = c->H.c0;
+    for (int q = 0; q < c->n; ++q) {
+        if (!((c->hf >> q) & 1u)) continue;
+        sft += c->H.diag_a[q];
+        for (int r = q + 1; r < c->n; ++r)
+            if ((c->hf >> r) & 1u) sft += c->H.diag_b[size_t(q) * c->n + r];
+    }
+    c->shift = c->H.has_diag ? sft : c->H.c0;
+    c->hf32.diag_q0 = shifted_q0(c);
+    c->hf64.diag_q0 = shifted_q0(c);
+    c->have_ref = true;
+    c->have_exc = false;
+    c->state_valid = false;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_build_uccsd_list(int n_orb, int n_alpha, int n_beta, int32_t *out, int cap,
+                                    int *n_out) {
+    if (n_orb < 1 || n_orb > 15 || n_alpha < 0 || n_beta < 0 || n_alpha > n_orb || n_beta > n_orb ||
+        cap < 0 || !n_out || (cap > 0 && !out))
+        return UCCSD_ERR_ARG;
+    std::vector<int32_t> v = build_uccsd_list(n_orb, n_alpha, n_beta);
+    int count = int(v.size() / 4);
+    int w = std::min(count, cap);
+    if (w > 0) std::memcpy(out, v.data(), sizeof(int32_t) * 4 * w);
+    *n_out = count;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int trotter_order,
+                                   int n_slices) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->have_ref) return fail(c, UCCSD_ERR_STATE, "set_reference must come first");
+    if (K < 0 || (K > 0 && !ijab)) return fail(c, UCCSD_ERR_ARG, "bad excitation list");
+    if (trotter_order != 1 && trotter_order != 2) return fail(c, UCCSD_ERR_ARG, "trotter_order must be 1 or 2");
+    if (n_slices < 1 || n_slices > 64) return fail(c, UCCSD_ERR_ARG, "n_slices must be in [1, 64]");
+    const int n = c->n;
+    std::vector<CompiledExc> exc(K);
+    for (int k = 0; k < K; ++k) {
+        const int32_t *r = ijab + 4 * k;
+        bool single = r[1] < 0;
+        auto occ = [&](int q) { return q >= 0 && q < n && ((c->hf >> q) & 1u); };
+        auto vir = [&](int q) { return q >= 0 && q < n && !((c->hf >> q) & 1u); };
+        bool ok;
+        if (single) {
+            ok = r[3] < 0 && occ(r[0]) && vir(r[2]) && ((r[0] & 1) == (r[2] & 1));
+        } else {
+            ok = occ(r[0]) && occ(r[1]) && vir(r[2]) && vir(r[3]) && r[0] != r[1] && r[2] != r[3] &&
+                 ((r[0] & 1) + (r[1] & 1) == (r[2] & 1) + (r[3] & 1));
+        }
+        if (!ok) return fail(c, UCCSD_ERR_ARG, "excitation row " + std::to_string(k) +
+                                                   " is not a spin-conserving occupied->virtual excitation");
+        std::string err;
+        if (!compile_excitation(n, r, &exc[k], &err)) return fail(c, UCCSD_ERR_ARG, err);
+    }
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    c->K = K;
+    c->order = trotter_order;
+    c->M = n_slices;
+    c->ijab.assign(ijab, ijab + 4 * size_t(K));
+    build_schedule(K, trotter_order, n_slices, &c->op_k, &c->op_scale);
+    const int pi = c->prec ? 1 : 0;
+    c->fwd = plan_sweep(n, kFwdL[pi], kCmin, exc, c->op_k);
+    if (c->fwd.runs.empty()) {
+        // no factors: one pass still prepares |HF>
+        RunDev r{};
+        int L = std::min(kFwdL[pi], n);
+        r.tmask = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
+        r.rmask = ((n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u)) & ~r.tmask;
+        r.L = L;
+        r.c = L;
+        r.op_begin = r.op_end = 0;
+        c->fwd.runs.push_back(r);
+        c->fwd.L = L;
+    }
+    c->adj = plan_sweep(n, kAdjL[pi], kCmin, exc, c->op_k);
+    // per-amplitude CSR of schedule factors (for the gradient sum)
+    std::vector<int32_t> k_ptr(K + 1, 0), k_ops;
+    for (size_t o = 0; o < c->op_k.size(); ++o) k_ptr[c->op_k[o] + 1]++;
+    for (int k = 0; k < K; ++k) k_ptr[k + 1] += k_ptr[k];
+    k_ops.resize(c->op_k.size());
+    std::vector<int32_t> fill(k_ptr.begin(), k_ptr.end() - 1);
+    for (size_t o = 0; o < c->op_k.size(); ++o) k_ops[fill[c->op_k[o]]++] = int32_t(o);
+    uccsd_status st;
+    OpDev *p1;
+    int32_t *p2;
+    double *p3;
+    if ((st = upload(c, "fwd_ops", c->fwd.ops, &p1))) return st;
+    if ((st = upload(c, "adj_ops", c->adj.ops, &p1))) return st;
+    if ((st = upload(c, "op_k", c->op_k, &p2))) return st;
+    if ((st = upload(c, "op_scale", c->op_scale, &p3))) return st;
+    if ((st = upload(c, "k_ptr", k_ptr, &p2))) return st;
+    if ((st = upload(c, "k_ops", k_ops, &p2))) return st;
+    c->have_exc = true;
+    c->state_valid = false;
+    return alloc_slots(c);
+}
+
+uccsd_status uccsd_set_batch(uccsd_ctx *c, int B) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (B < 1 || B > 4096) return fail(c, UCCSD_ERR_ARG, "batch must be in [1, 4096]");
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    int old = c->B;
+    c->B = B;
+    uccsd_status st = alloc_slots(c);
+    if (st) {
+        c->B = old;
+        alloc_slots(c);
+    }
+    c->state_valid = false;
+    return st;
+}
+
+uccsd_status uccsd_energy(uccsd_ctx *c, const double *theta, int on_dev, double *E, void *stream) {
+    return eval(c, 1, theta, on_dev, E, nullptr, stream);
+}
+
+uccsd_status uccsd_energy_grad(uccsd_ctx *c, const double *theta, int on_dev, double *E, double *grad,
+                               void *stream) {
+    if (c && c->K > 0 && !grad) return fail(c, UCCSD_ERR_ARG, "null grad");
+    double dummy = 0.0;
+    return eval(c, 1, theta, on_dev, E, grad ? grad : (on_dev ? nullptr : &dummy), stream);
+}
+
+uccsd_status uccsd_energy_grad_batch(uccsd_ctx *c, int B, const double *theta, int on_dev, double *E,
+                                     double *grad, void *stream) {
+    return eval(c, B, theta, on_dev, E, grad, stream);
+}
+
+uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "no state yet");
+    if (slot < 0 || slot >= c->B) return fail(c, UCCSD_ERR_ARG, "slot out of range");
+    const size_t N = state_bytes(c);
+    if (!out || len < 2 * N) return fail(c, UCCSD_ERR_ARG, "output buffer too small");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
+    const char *src = static_cast<const char *>(dptr(c, "psi")) + size_t(slot) * N * amp_bytes(c);
+    if (c->prec) {
+        std::vector<float> tmp(2 * N);
+        e = cudaMemcpy(tmp.data(), src, N * 8, cudaMemcpyDeviceToHost);
+        for (size_t i = 0; i < 2 * N; ++i) out[i] = tmp[i];
+    } else {
+        e = cudaMemcpy(out, src, N * 16, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "state download");
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_info(const uccsd_ctx *c, uccsd_info_t *info) {
+    if (!c || !info) return UCCSD_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_qubits = c->n;
+    info->n_orb = c->n_orb;
+    info->n_alpha = c->n_alpha;
+    info->n_beta = c->n_beta;
+    info->K = c->K;
+    info->n_ops = int(c->op_k.size());
+    info->n_groups = int(c->H.groups.size()) + (c->H.has_diag ? 1 : 0);
+    info->n_terms = c->H.n_terms;
+    info->n_fwd_runs = int(c->fwd.runs.size());
+    info->n_adj_runs = int(c->adj.runs.size());
+    info->batch = c->B;
+    info->precision = c->prec;
+    info->device_bytes = c->bytes;
+    info->launches = c->launches;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_set_profiling(uccsd_ctx *c, int on) {
+    if (!c) return UCCSD_ERR_ARG;
+    c->profiling = on != 0;
+    std::memset(&c->prof, 0, sizeof(c->prof));
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_get_profile(const uccsd_ctx *c, uccsd_profile_t *out) {
+    if (!c || !out) return UCCSD_ERR_ARG;
+    *out = c->prof;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *eri, double e_core,
+                                     int *n_groups, int *n_terms) {
+    uccsd_status st = check_hamiltonian_input(nullptr, n_orb, h, eri, e_core);
+    if (st) return st;
+    CompiledH H;
+    std::string err;
+    if (!compile_hamiltonian(n_orb, h, eri, e_core, &H, &err)) return UCCSD_ERR_ARG;
+    if (n_groups) *n_groups = int(H.groups.size()) + (H.has_diag ? 1 : 0);
+    if (n_terms) *n_terms = H.n_terms;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_pauli_terms(int n_orb, const double *h, const double *eri, double e_core,
+                               uint32_t *xmask, uint32_t *zmask, double *coef, int cap, int *n_out) {
+    if (cap < 0 || !n_out || (cap > 0 && (!xmask || !zmask || !coef))) return UCCSD_ERR_ARG;
+    uccsd_status st = check_hamiltonian_input(nullptr, n_orb, h, eri, e_core);
+    if (st) return st;
+    CompiledH H;
+    std::string err;
+    if (!compile_hamiltonian(n_orb, h, eri, e_core, &H, &err)) return UCCSD_ERR_ARG;
+    int w = std::min(cap, H.n_terms);
+    for (int t = 0; t < w; ++t) {
+        xmask[t] = H.terms[t].x;
+        zmask[t] = H.terms[t].z;
+        coef[t] = H.terms[t].c;
+    }
+    *n_out = H.n_terms;
+    return UCCSD_OK;
+}
+
+}  // extern "C"

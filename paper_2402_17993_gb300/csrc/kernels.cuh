@@ -1,0 +1,76 @@
+// Launch wrappers of the UCCSD CUDA kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.hpp"
+
+namespace uccsd {
+
+// Device copy of the compiled Hamiltonian for one precision R.
+template <typename R>
+struct DevHam {
+    const GroupT<R> *groups = nullptr;  // sorted by segment, diagonal segment last
+    const int32_t *seg_begin = nullptr; // n_seg + 1
+    const uint32_t *seg_d = nullptr;    // high-part XOR of each segment
+    int n_seg = 0;
+    const R *spec = nullptr;            // spectator rows [row][4]
+    // Diagonal group as an occupation quadratic form in 64-bit fixed point
+    // (one unit = diag_unit Ha), summed exactly:
+    //   d(x) - shift = q0 + sum_{q in occ(x)} qa[q] + sum_{q<r in occ(x)} qb[q*n + r]
+    const long long *diag_qa = nullptr; // n
+    const long long *diag_qb = nullptr; // n*n (q < r)
+    long long diag_q0 = 0;
+    double diag_unit = 0.0;
+    int has_diag = 0;
+    int n = 0;                          // qubits (row length of diag_qb)
+};
+
+struct LaunchCfg {
+    int n = 0;           // qubits
+    size_t N = 0;        // 2^n
+    int B = 1;           // slots in this call
+    int n_ops = 0;
+    cudaStream_t stream = nullptr;
+};
+
+// cs[b][o] = (cos, sin)(theta[b][op_k[o]] * op_scale[o]) computed in FP64,
+// stored in R.
+template <typename R>
+cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const int32_t *op_k,
+                      const double *op_scale, void *cs);
+
+template <typename R>
+cudaError_t launch_forward_run(const LaunchCfg &cfg, void *psi, const RunDev &run,
+                               const OpDev *ops, const void *cs, int init_hf, uint32_t hf);
+
+template <typename R>
+cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
+                          const DevHam<R> &H, double *Epart, int store_sigma);
+
+template <typename R>
+cudaError_t launch_adjoint_run(const LaunchCfg &cfg, void *phi, void *lam, const RunDev &run,
+                               const OpDev *ops, const void *cs, double *gpart, int n_tiles);
+
+// E[b] from the per-tile partials (e', n) of sum Re(conj psi (H - shift) psi)
+// and sum |psi|^2: E = shift * n + e' (rayleigh = 0) or shift + e'/n
+// (rayleigh = 1); the gradient is divided by n when rayleigh = 1.
+cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles_h,
+                          const double *gpart, int n_tiles_a, int K, const int32_t *k_ptr,
+                          const int32_t *k_ops, const double *op_scale, double shift,
+                          int rayleigh, double *E, double *grad);
+
+// Shared memory needed by each kernel for tile bits L.
+template <typename R>
+size_t forward_smem(int L, int c);
+template <typename R>
+size_t adjoint_smem(int L, int c);
+template <typename R>
+size_t happly_smem(int LH);
+
+// One-time kernel attribute set-up (dynamic shared memory opt-in).
+cudaError_t configure_kernels();
+
+}  // namespace uccsd
