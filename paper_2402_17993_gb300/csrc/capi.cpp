@@ -109,6 +109,7 @@ struct uccsd_ctx {
     // Hamiltonian views
     DevHam<float> hf32;
     DevHam<double> hf64;
+    HSector hsec;
 
     // diagonal in fixed point; energy shift (the reference determinant's
     // diagonal energy) applied to H on the device and added back in FP64
@@ -238,6 +239,36 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     return UCCSD_OK;
 }
 
+// Local indices of the H-apply tile (low LH bits, alpha = even bits)
+// grouped by (alpha count, beta count), ascending inside each group.
+uccsd_status upload_sector_lists(uccsd_ctx *c) {
+    const int LH = c->LH, half = LH / 2;
+    const int nk = (half + 1) * (half + 1);
+    std::vector<std::vector<uint16_t>> lists(nk);
+    for (uint32_t l = 0; l < (1u << LH); ++l) {
+        int a = __builtin_popcount(l & 0x55555555u), b = __builtin_popcount(l & 0xAAAAAAAAu);
+        lists[a * (half + 1) + b].push_back(uint16_t(l));
+    }
+    std::vector<uint16_t> perm;
+    std::vector<int32_t> offs;
+    int mx = 0;
+    for (auto &v : lists) {
+        offs.push_back(int32_t(perm.size()));
+        perm.insert(perm.end(), v.begin(), v.end());
+        mx = std::max(mx, int(v.size()));
+    }
+    offs.push_back(int32_t(perm.size()));
+    uint16_t *pp;
+    int32_t *po;
+    uccsd_status st;
+    if ((st = upload(c, "sector_perm", perm, &pp))) return st;
+    if ((st = upload(c, "sector_offs", offs, &po))) return st;
+    c->hsec.perm = pp;
+    c->hsec.offs = po;
+    c->hsec.max_list = mx;
+    return UCCSD_OK;
+}
+
 size_t state_bytes(const uccsd_ctx *c) { return size_t(1) << c->n; }
 size_t amp_bytes(const uccsd_ctx *c) { return c->prec ? 8 : 16; }
 int n_tiles_h(const uccsd_ctx *c) { return 1 << (c->n - c->LH); }
@@ -252,6 +283,9 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     const size_t n_ops = std::max<size_t>(c->op_k.size(), 1);
     if ((st = dalloc(c, "psi", B * state_bytes(c) * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "sig", B * state_bytes(c) * amp_bytes(c), &p))) return st;
+    // sigma is written only inside the electron sector; the rest stays zero
+    cudaError_t e = cudaMemset(p, 0, B * state_bytes(c) * amp_bytes(c));
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset");
     if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
     if ((st = dalloc(c, "E", B * sizeof(double), &p))) return st;
@@ -365,7 +399,7 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     const DevHam<R> &H = *reinterpret_cast<const DevHam<R> *>(sizeof(R) == 4 ? (const void *)&c->hf32
                                                                              : (const void *)&c->hf64);
     mk.begin(UCCSD_K_HAPPLY);
-    if ((e = launch_happly<R>(cfg, psi, sig, c->LH, H, Epart, grad ? 1 : 0)) != cudaSuccess)
+    if ((e = launch_happly<R>(cfg, psi, sig, c->LH, H, c->hsec, Epart, grad ? 1 : 0)) != cudaSuccess)
         return cuda_fail(c, e, "H-apply kernel");
     ++c->launches;
     c->prof.launches[UCCSD_K_HAPPLY]++;
@@ -483,6 +517,7 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, con
     c->state_valid = false;
     c->shift = 0.0;
     make_fixed_point(c);
+    if ((st = upload_sector_lists(c))) return st;
     if ((st = upload_ham<float>(c, &c->hf32, "h32_"))) return st;
     if ((st = upload_ham<double>(c, &c->hf64, "h64_"))) return st;
     c->have_h = true;
@@ -508,6 +543,8 @@ uccsd_status uccsd_set_reference(uccsd_ctx *c, int n_alpha, int n_beta) {
     c->shift = c->H.has_diag ? sft : c->H.c0;
     c->hf32.diag_q0 = shifted_q0(c);
     c->hf64.diag_q0 = shifted_q0(c);
+    c->hsec.n_alpha = n_alpha;
+    c->hsec.n_beta = n_beta;
     c->have_ref = true;
     c->have_exc = false;
     c->state_valid = false;

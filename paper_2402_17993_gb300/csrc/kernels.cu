@@ -15,6 +15,7 @@ namespace uccsd {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kHThreads = 128;  // H-apply: up to 4 sector entries per thread (<= 512 per tile)
 
 template <typename R>
 struct Vec2;
@@ -181,56 +182,98 @@ __global__ void __launch_bounds__(kThreads) forward_run_kernel(V2<R> *__restrict
 }
 
 // ---------------------------------------------------------------------------
-// Hamiltonian action and energy (Section 2.3): sigma = H psi over X-mask
-// groups, tile = the low LH bits.  For each segment of groups sharing the
-// high part d of their X-mask the source tile (h ^ d) is staged in shared
-// memory; the diagonal segment (d = 0) runs last so the own tile is
-// resident for the energy partial sum_x Re(conj(psi_x) sigma_x) in FP64.
+// Hamiltonian action and energy (Section 2.3): sigma = (H - shift) psi over
+// X-mask groups, tile = the low LH bits of the amplitude index.
+//
+// H conserves N_alpha and N_beta, and psi vanishes outside the
+// (n_alpha, n_beta) sector, so only sector amplitudes are read or
+// produced: inside a tile whose high bits hold (a_h, b_h) electrons the
+// sector entries are the local indices with (n_alpha - a_h, n_beta - b_h)
+// electrons in the tile bits, listed contiguously in `perm` (offsets
+// `offs[a * (LH/2 + 1) + b]`).  For each segment of groups sharing the high
+// part d of their X-mask, the sector entries of the source tile (h ^ d) are
+// gathered into shared memory; a group contributes to output x only for a
+// number-conserving flip pattern, which keeps x ^ xmask inside the sector.
+// The own-tile segment (d = 0) runs last so psi_x is resident for the FP64
+// partials sum Re(conj(psi_x) sigma_x) and sum |psi_x|^2.  Entries of sigma
+// outside the sector are never written (they stay zero).
 // ---------------------------------------------------------------------------
+struct SectorLists {
+    const uint16_t *perm;  // 2^LH local indices grouped by (alpha, beta) count
+    const int32_t *offs;   // (LH/2 + 1)^2 + 1 offsets
+    int n_alpha, n_beta;
+};
+
+__device__ __forceinline__ void sector_range(const SectorLists &sl, int LH, uint32_t hi, int *beg,
+                                             int *end) {
+    const int half = LH >> 1;
+    const int a = sl.n_alpha - __popc(hi & 0x55555555u);
+    const int bb = sl.n_beta - __popc(hi & 0xAAAAAAAAu);
+    if (a < 0 || a > half || bb < 0 || bb > half) {
+        *beg = *end = 0;
+        return;
+    }
+    const int k = a * (half + 1) + bb;
+    *beg = sl.offs[k];
+    *end = sl.offs[k + 1];
+}
+
 template <typename R, int APT>
-__global__ void __launch_bounds__(kThreads) happly_kernel(const V2<R> *__restrict__ psi,
-                                                          V2<R> *__restrict__ sig, size_t N,
-                                                          int LH, DevHam<R> H,
-                                                          double *__restrict__ Epart,
-                                                          int store_sigma) {
+__global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restrict__ psi,
+                                                           V2<R> *__restrict__ sig, size_t N,
+                                                           int LH, DevHam<R> H, SectorLists sl,
+                                                           double *__restrict__ Epart,
+                                                           int store_sigma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
     __shared__ double red[32];
     const int b = blockIdx.y;
     const uint32_t h = blockIdx.x;
     const V2<R> *src = psi + (size_t)b * N;
-    const uint32_t tsize = 1u << LH;
-    const uint32_t lowmask = tsize - 1u;
-    V2<R> acc[APT];
+    const uint32_t lowmask = (1u << LH) - 1u;
+    int o_beg, o_end;
+    sector_range(sl, LH, h, &o_beg, &o_end);
+    const int cnt = o_end - o_beg;
+    double e = 0.0, nrm = 0.0;
+    if (cnt > 0) {
+        uint32_t xl[APT];
+        V2<R> acc[APT];
 #pragma unroll
-    for (int i = 0; i < APT; ++i) {
-        acc[i].x = (R)0;
-        acc[i].y = (R)0;
-    }
-    for (int s = 0; s < H.n_seg; ++s) {
-        const uint32_t hs = h ^ H.seg_d[s];
-        const uint32_t base = hs << LH;
-        __syncthreads();
-        for (uint32_t l = threadIdx.x; l < tsize; l += blockDim.x) tile[l] = src[base + l];
-        __syncthreads();
-        const int g_end = H.seg_begin[s + 1];
-        for (int g = H.seg_begin[s]; g < g_end; ++g) {
-            const GroupT<R> *G = H.groups + g;
-            const uint32_t xm = G->xmask;
-            const uint32_t jm = G->jmask;
-            const int nb = G->nb;
-            const int spec = G->spec;
-            const uint32_t active = G->active;
-            const int p0 = G->pos[0], p1 = G->pos[1], p2 = G->pos[2], p3 = G->pos[3];
+        for (int i = 0; i < APT; ++i) {
+            const int j = threadIdx.x + i * blockDim.x;
+            xl[i] = j < cnt ? sl.perm[o_beg + j] : 0xFFFFFFFFu;
+            acc[i].x = (R)0;
+            acc[i].y = (R)0;
+        }
+        for (int s = 0; s < H.n_seg; ++s) {
+            const uint32_t hs = h ^ H.seg_d[s];
+            int s_beg, s_end;
+            sector_range(sl, LH, hs, &s_beg, &s_end);
+            if (s_beg == s_end && s != H.n_seg - 1) continue;  // source tile is all zero
+            const uint32_t base = hs << LH;
+            __syncthreads();
+            for (int j = s_beg + threadIdx.x; j < s_end; j += blockDim.x) {
+                const uint32_t l = sl.perm[j];
+                tile[l] = src[base + l];
+            }
+            __syncthreads();
+            const int g_end = H.seg_begin[s + 1];
+            for (int g = H.seg_begin[s]; g < g_end; ++g) {
+                const GroupT<R> *G = H.groups + g;
+                const uint32_t xm = G->xmask;
+                const uint32_t jm = G->jmask;
+                const int nb = G->nb;
+                const int spec = G->spec;
+                const uint32_t active = G->active;
+                const int p0 = G->pos[0], p1 = G->pos[1], p2 = G->pos[2], p3 = G->pos[3];
 #pragma unroll
-            for (int i = 0; i < APT; ++i) {
-                const uint32_t xl = threadIdx.x + i * blockDim.x;
-                if (xl >= tsize) continue;
-                const uint32_t yl = xl ^ (xm & lowmask);
-                const uint32_t y = base | yl;
-                int pat = ((y >> p0) & 1u) | (((y >> p1) & 1u) << 1);
-                if (nb == 4) pat |= (((y >> p2) & 1u) << 2) | (((y >> p3) & 1u) << 3);
-                if ((active >> pat) & 1u) {
+                for (int i = 0; i < APT; ++i) {
+                    if (xl[i] == 0xFFFFFFFFu) continue;
+                    const uint32_t yl = xl[i] ^ (xm & lowmask);
+                    const uint32_t y = base | yl;
+                    int pat = ((y >> p0) & 1u) | (((y >> p1) & 1u) << 1);
+                    if (nb == 4) pat |= (((y >> p2) & 1u) << 2) | (((y >> p3) & 1u) << 3);
+                    if (!((active >> pat) & 1u)) continue;
                     R v = G->lut[pat];
                     if (spec >= 0) {
                         uint32_t occ = y & ~xm;
@@ -247,44 +290,35 @@ __global__ void __launch_bounds__(kThreads) happly_kernel(const V2<R> *__restric
                 }
             }
         }
-    }
-    // After the last segment (d = 0) the own tile is resident.
-    const uint32_t own = h << LH;
-    if (H.has_diag) {
+        // After the last segment (d = 0) the own tile is resident.
+        const uint32_t own = h << LH;
         const int n = H.n;
 #pragma unroll
         for (int i = 0; i < APT; ++i) {
-            const uint32_t xl = threadIdx.x + i * blockDim.x;
-            if (xl >= tsize) continue;
-            const uint32_t x = own | xl;
-            long long q = H.diag_q0;
-            uint32_t o1 = x;
-            while (o1) {
-                const int a = __ffs(o1) - 1;
-                o1 &= o1 - 1u;
-                q += H.diag_qa[a];
-                uint32_t o2 = o1;
-                while (o2) {
-                    const int r = __ffs(o2) - 1;
-                    o2 &= o2 - 1u;
-                    q += H.diag_qb[a * n + r];
+            if (xl[i] == 0xFFFFFFFFu) continue;
+            const V2<R> p = tile[xl[i]];
+            if (H.has_diag) {
+                long long q = H.diag_q0;
+                uint32_t o1 = own | xl[i];
+                while (o1) {
+                    const int a = __ffs(o1) - 1;
+                    o1 &= o1 - 1u;
+                    q += H.diag_qa[a];
+                    uint32_t o2 = o1;
+                    while (o2) {
+                        const int r = __ffs(o2) - 1;
+                        o2 &= o2 - 1u;
+                        q += H.diag_qb[a * n + r];
+                    }
                 }
+                const R v = (R)q * (R)H.diag_unit;
+                acc[i].x += v * p.x;
+                acc[i].y += v * p.y;
             }
-            const R v = (R)q * (R)H.diag_unit;
-            const V2<R> p = tile[xl];
-            acc[i].x += v * p.x;
-            acc[i].y += v * p.y;
+            e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
+            nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+            if (store_sigma) sig[(size_t)b * N + (own | xl[i])] = acc[i];
         }
-    }
-    double e = 0.0, nrm = 0.0;
-#pragma unroll
-    for (int i = 0; i < APT; ++i) {
-        const uint32_t xl = threadIdx.x + i * blockDim.x;
-        if (xl >= tsize) continue;
-        const V2<R> p = tile[xl];
-        e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
-        nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-        if (store_sigma) sig[(size_t)b * N + (own | xl)] = acc[i];
     }
     e = block_sum(e, red);
     nrm = block_sum(nrm, red);
@@ -468,22 +502,14 @@ cudaError_t launch_forward_run(const LaunchCfg &cfg, void *psi, const RunDev &ru
 
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
-                          const DevHam<R> &H, double *Epart, int store_sigma) {
+                          const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma) {
     dim3 grid(1u << (cfg.n - LH), cfg.B);
-    const int tsize = 1 << LH;
-    const int threads = std::min(kThreads, std::max(32, tsize));
-    const int apt = std::max(1, tsize / threads);
     const size_t smem = happly_smem<R>(LH);
-    const V2<R> *p = static_cast<const V2<R> *>(psi);
-    V2<R> *s = static_cast<V2<R> *>(sig);
-    switch (apt) {
-        case 1: happly_kernel<R, 1><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, LH, H, Epart, store_sigma); break;
-        case 2: happly_kernel<R, 2><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, LH, H, Epart, store_sigma); break;
-        case 4: happly_kernel<R, 4><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, LH, H, Epart, store_sigma); break;
-        case 8: happly_kernel<R, 8><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, LH, H, Epart, store_sigma); break;
-        case 16: happly_kernel<R, 16><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, LH, H, Epart, store_sigma); break;
-        default: return cudaErrorInvalidValue;
-    }
+    SectorLists sl{hs.perm, hs.offs, hs.n_alpha, hs.n_beta};
+    if (hs.max_list > 4 * kHThreads) return cudaErrorInvalidValue;
+    happly_kernel<R, 4><<<grid, kHThreads, smem, cfg.stream>>>(
+        static_cast<const V2<R> *>(psi), static_cast<V2<R> *>(sig), cfg.N, LH, H, sl, Epart,
+        store_sigma);
     return cudaGetLastError();
 }
 
@@ -520,16 +546,8 @@ cudaError_t configure_kernels() {
     UCCSD_SET(forward_run_kernel<double>);
     UCCSD_SET(adjoint_run_kernel<float>);
     UCCSD_SET(adjoint_run_kernel<double>);
-    UCCSD_SET((happly_kernel<float, 1>));
-    UCCSD_SET((happly_kernel<float, 2>));
     UCCSD_SET((happly_kernel<float, 4>));
-    UCCSD_SET((happly_kernel<float, 8>));
-    UCCSD_SET((happly_kernel<float, 16>));
-    UCCSD_SET((happly_kernel<double, 1>));
-    UCCSD_SET((happly_kernel<double, 2>));
     UCCSD_SET((happly_kernel<double, 4>));
-    UCCSD_SET((happly_kernel<double, 8>));
-    UCCSD_SET((happly_kernel<double, 16>));
 #undef UCCSD_SET
     return cudaSuccess;
 }
@@ -543,7 +561,7 @@ cudaError_t configure_kernels() {
     template cudaError_t launch_forward_run<R>(const LaunchCfg &, void *, const RunDev &,      \
                                                const OpDev *, const void *, int, uint32_t);    \
     template cudaError_t launch_happly<R>(const LaunchCfg &, const void *, void *, int,        \
-                                          const DevHam<R> &, double *, int);                   \
+                                          const DevHam<R> &, const HSector &, double *, int);  \
     template cudaError_t launch_adjoint_run<R>(const LaunchCfg &, void *, void *,              \
                                                const RunDev &, const OpDev *, const void *,    \
                                                double *, int);

@@ -28,6 +28,15 @@ struct DevHam {
     int n = 0;                          // qubits (row length of diag_qb)
 };
 
+// Sector index lists of the H-apply tile (low LH bits): local indices
+// grouped by (alpha count, beta count), offsets per (a, b) pair.
+struct HSector {
+    const uint16_t *perm = nullptr;  // 2^LH
+    const int32_t *offs = nullptr;   // (LH/2 + 1)^2 + 1
+    int n_alpha = 0, n_beta = 0;
+    int max_list = 0;                // largest (a, b) list
+};
+
 struct LaunchCfg {
     int n = 0;           // qubits
     size_t N = 0;        // 2^n
@@ -48,7 +57,7 @@ cudaError_t launch_forward_run(const LaunchCfg &cfg, void *psi, const RunDev &ru
 
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
-                          const DevHam<R> &H, double *Epart, int store_sigma);
+                          const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma);
 
 template <typename R>
 cudaError_t launch_adjoint_run(const LaunchCfg &cfg, void *phi, void *lam, const RunDev &run,
