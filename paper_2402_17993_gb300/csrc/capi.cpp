@@ -12,19 +12,12 @@
 #include "jw.hpp"
 #include "kernels.cuh"
 #include "plan.hpp"
+#include "ctx.hpp"
 
 using namespace uccsd;
 
 namespace {
 
-// Tile bits of the kernels per precision (shared memory per CTA):
-//   forward  FP32 13 (64 KiB), FP64 12 (64 KiB)
-//   adjoint  FP32 12 (2 x 32 KiB), FP64 11 (2 x 32 KiB)
-//   H-apply  12 (32 / 64 KiB)
-constexpr int kFwdL[2] = {12, 13};
-constexpr int kAdjL[2] = {11, 12};
-constexpr int kHL = 12;
-constexpr int kCmin = 3;
 
 template <typename R>
 struct HamTables {
@@ -78,50 +71,6 @@ HamTables<R> make_tables(const CompiledH &H, int LH) {
 }
 
 }  // namespace
-
-struct uccsd_ctx {
-    int device = 0;
-    int prec = 0;  // 0 FP64, 1 FP32 state
-    size_t budget = 0;
-    size_t bytes = 0;
-    std::string err;
-    bool failed = false;
-    uint64_t launches = 0;
-    cudaStream_t last_stream = nullptr;
-
-    // problem
-    int n_orb = 0, n = 0;
-    bool have_h = false, have_ref = false, have_exc = false;
-    int n_alpha = 0, n_beta = 0;
-    uint32_t hf = 0;
-    CompiledH H;
-    int K = 0, order = 1, M = 1;
-    std::vector<int32_t> ijab, op_k;
-    std::vector<double> op_scale;
-    SweepPlan fwd, adj;
-    int LH = kHL;
-    int B = 1;          // reserved slots
-    bool state_valid = false;
-
-    // device memory: name -> (ptr, bytes)
-    std::map<std::string, std::pair<void *, size_t>> mem;
-
-    // Hamiltonian views
-    DevHam<float> hf32;
-    DevHam<double> hf64;
-    HSector hsec;
-
-    // diagonal in fixed point; energy shift (the reference determinant's
-    // diagonal energy) applied to H on the device and added back in FP64
-    std::vector<long long> diag_qa, diag_qb;
-    double diag_unit = 0.0;
-    double shift = 0.0;
-
-    // profiling
-    bool profiling = false;
-    uccsd_profile_t prof{};
-    std::vector<cudaEvent_t> events;
-};
 
 namespace {
 
