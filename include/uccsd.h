@@ -184,6 +184,37 @@ typedef struct {
 uccsd_status uccsd_set_profiling(uccsd_ctx *ctx, int on);
 uccsd_status uccsd_get_profile(const uccsd_ctx *ctx, uccsd_profile_t *out);
 
+/* Energy of a state vector that the caller already holds on the device,
+ * computed without allocating any device memory.  The paper has no
+ * counterpart; it exists for callers that cannot call cudaMalloc when they
+ * need an energy: code running while a stream is captured into a CUDA
+ * graph (an allocation would invalidate the capture), serving or real-time
+ * loops held to a memory budget reserved up front, and programs whose
+ * device allocator belongs to another framework.
+ *
+ *   ctx    context with set_hamiltonian and set_reference done (its tables
+ *          were uploaded then; set_excitations is not needed)
+ *   psi    device pointer to 2^n amplitudes in the context's precision
+ *          (complex128 for UCCSD_FP64, complex64 for UCCSD_FP32_STATE),
+ *          interleaved (re, im); only entries with n_alpha alpha and n_beta
+ *          beta electrons are read (the others must be zero)
+ *   E      device pointer to one double, written on `stream`:
+ *          <psi|H|psi> (UCCSD_FP64) or <psi|H|psi>/<psi|psi> (FP32 state),
+ *          the same quantity the context's evaluations report
+ *
+ * Scratch: a fixed device array of 2 * UCCSD_NOALLOC_MAX_TILES doubles
+ * (256 KiB) inside the library, held by every GPU that loads the library
+ * until the process exits.  States above 26 qubits need more partials and
+ * are rejected with UCCSD_ERR_ARG.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls in the process share the array and
+ * it keeps the last call's partials; each call overwrites what it reads, so
+ * nothing has to be cleared, but calls that overlap on the GPU (different
+ * streams or contexts without ordering between them) race on it. */
+#define UCCSD_NOALLOC_MAX_TILES 16384
+uccsd_status uccsd_expectation_noalloc(uccsd_ctx *ctx, const void *psi, double *E,
+                                       void *stream);
+
 /* Host-only: Jordan-Wigner compile statistics of the Hamiltonian of Eq. 2
  * without creating a context (no device use).  Any output may be NULL. */
 uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *eri,

@@ -30,7 +30,7 @@ EXPORTS = [
     "uccsd_set_hamiltonian", "uccsd_set_reference", "uccsd_build_uccsd_list",
     "uccsd_set_excitations", "uccsd_set_batch", "uccsd_energy", "uccsd_energy_grad",
     "uccsd_energy_grad_batch", "uccsd_get_state", "uccsd_info", "uccsd_hamiltonian_stats",
-    "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile",
+    "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile", "uccsd_expectation_noalloc",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -94,6 +94,7 @@ def lib():
         L.uccsd_hamiltonian_stats.argtypes = [ip, f64p, f64p, ctypes.c_double,
                                               ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_expectation_noalloc.argtypes = [vp, vp, vp, vp]
         L.uccsd_set_profiling.argtypes = [vp, ip]
         L.uccsd_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
