@@ -292,6 +292,8 @@ def run_ours(args):
 def scaleup_26q(uc, device):
     import torch
     w = synth.workload("26q")
+    gold_path = os.path.join(ROOT, "tests", "golden", "golden_26q.json")
+    gold = json.load(open(gold_path)) if os.path.exists(gold_path) else None
     out = {}
     for name, prec in (("fp32", uc.FP32_STATE), ("fp64", uc.FP64)):
         ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"],
@@ -313,7 +315,12 @@ def scaleup_26q(uc, device):
         ms = a.elapsed_time(b) / steps
         prof = ctx.profile()
         inf = ctx.info()
-        out[name] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "E": float(E[0].item()),
+        err = {}
+        if gold is not None:
+            err = {"abs_dE_vs_oracle": abs(float(E[0].item()) - gold["E"]),
+                   "max_abs_dgrad_vs_oracle": float(np.max(np.abs(G[0].cpu().numpy()
+                                                                  - np.array(gold["grad"]))))}
+        out[name] = {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "E": float(E[0].item()), **err,
                      "family_ms": {f: prof["ms"][f] / max(1, prof["calls"]) for f in prof["ms"]},
                      "fwd_runs": inf["n_fwd_runs"], "adj_runs": inf["n_adj_runs"]}
         del ctx

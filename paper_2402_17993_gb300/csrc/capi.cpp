@@ -221,7 +221,7 @@ uccsd_status upload_sector_lists(uccsd_ctx *c) {
 size_t state_bytes(const uccsd_ctx *c) { return size_t(1) << c->n; }
 size_t amp_bytes(const uccsd_ctx *c) { return c->prec ? 8 : 16; }
 int n_tiles_h(const uccsd_ctx *c) { return 1 << (c->n - c->LH); }
-int n_tiles_a(const uccsd_ctx *c) { return c->adj.runs.empty() ? 1 : 1 << (c->n - c->adj.L); }
+int n_tiles_a(const uccsd_ctx *c) { return c->adj.max_tiles; }
 
 // Per-slot buffers sized for c->B slots.
 uccsd_status alloc_slots(uccsd_ctx *c) {
@@ -231,6 +231,9 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     const size_t B = c->B;
     const size_t n_ops = std::max<size_t>(c->op_k.size(), 1);
     if ((st = dalloc(c, "psi", B * state_bytes(c) * amp_bytes(c), &p))) return st;
+    // the sweeps touch only electron-sector amplitudes; the rest stays zero
+    cudaError_t e0 = cudaMemset(p, 0, B * state_bytes(c) * amp_bytes(c));
+    if (e0 != cudaSuccess) return cuda_fail(c, e0, "memset");
     if ((st = dalloc(c, "sig", B * state_bytes(c) * amp_bytes(c), &p))) return st;
     // sigma is written only inside the electron sector; the rest stays zero
     cudaError_t e = cudaMemset(p, 0, B * state_bytes(c) * amp_bytes(c));
@@ -336,12 +339,17 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
         ++c->launches;
         c->prof.launches[UCCSD_K_CS]++;
     }
-    const OpDev *fops = static_cast<const OpDev *>(dptr(c, "fwd_ops"));
+    const COpDev *fops = static_cast<const COpDev *>(dptr(c, "fwd_ops"));
     mk.begin(UCCSD_K_FORWARD);
     for (size_t r = 0; r < c->fwd.runs.size(); ++r) {
-        if ((e = launch_forward_run<R>(cfg, psi, c->fwd.runs[r], fops, cs, r == 0 ? 1 : 0, c->hf)) !=
-            cudaSuccess)
+        if ((e = launch_forward_sweep<R>(cfg, psi, c->fwd.runs[r], fops, cs, c->fwd_args,
+                                         r == 0 ? 1 : 0, c->hf)) != cudaSuccess)
             return cuda_fail(c, e, "forward kernel");
+        ++c->launches;
+        c->prof.launches[UCCSD_K_FORWARD]++;
+    }
+    if (c->fwd.runs.empty()) {
+        if ((e = launch_set_hf<R>(cfg, psi, c->hf)) != cudaSuccess) return cuda_fail(c, e, "hf kernel");
         ++c->launches;
         c->prof.launches[UCCSD_K_FORWARD]++;
     }
@@ -353,11 +361,11 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     ++c->launches;
     c->prof.launches[UCCSD_K_HAPPLY]++;
     if (grad) {
-        const OpDev *aops = static_cast<const OpDev *>(dptr(c, "adj_ops"));
+        const COpDev *aops = static_cast<const COpDev *>(dptr(c, "adj_ops"));
         mk.begin(UCCSD_K_ADJOINT);
         for (int r = int(c->adj.runs.size()) - 1; r >= 0; --r) {
-            if ((e = launch_adjoint_run<R>(cfg, psi, sig, c->adj.runs[r], aops, cs, gpart,
-                                           n_tiles_a(c))) != cudaSuccess)
+            if ((e = launch_adjoint_sweep<R>(cfg, psi, sig, c->adj.runs[r], aops, cs, c->adj_args,
+                                             gpart, n_tiles_a(c))) != cudaSuccess)
                 return cuda_fail(c, e, "adjoint kernel");
             ++c->launches;
             c->prof.launches[UCCSD_K_ADJOINT]++;
@@ -366,7 +374,8 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     mk.begin(UCCSD_K_REDUCE);
     double *dE = on_dev ? E : static_cast<double *>(dptr(c, "E"));
     double *dG = grad ? (on_dev ? grad : static_cast<double *>(dptr(c, "grad"))) : nullptr;
-    if ((e = launch_reduce(cfg, Epart, n_tiles_h(c), gpart, n_tiles_a(c), K,
+    if ((e = launch_reduce(cfg, Epart, n_tiles_h(c), gpart, n_tiles_a(c),
+                           static_cast<const int32_t *>(dptr(c, "op_tiles")), K,
                            static_cast<const int32_t *>(dptr(c, "k_ptr")),
                            static_cast<const int32_t *>(dptr(c, "k_ops")), d_op_scale, c->shift,
                            c->prec ? 1 : 0, dE, dG)) !=
@@ -416,6 +425,7 @@ uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec, size_t h
     }
     if (cudaSetDevice(device) != cudaSuccess) return UCCSD_ERR_CUDA;
     if (configure_kernels() != cudaSuccess) return UCCSD_ERR_CUDA;
+    if (configure_sweep_kernels(kSweepBudget) != cudaSuccess) return UCCSD_ERR_CUDA;
     uccsd_ctx *c = new uccsd_ctx();
     c->device = device;
     c->prec = int(prec);
@@ -547,21 +557,13 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->M = n_slices;
     c->ijab.assign(ijab, ijab + 4 * size_t(K));
     build_schedule(K, trotter_order, n_slices, &c->op_k, &c->op_scale);
-    const int pi = c->prec ? 1 : 0;
-    c->fwd = plan_sweep(n, kFwdL[pi], kCmin, exc, c->op_k);
-    if (c->fwd.runs.empty()) {
-        // no factors: one pass still prepares |HF>
-        RunDev r{};
-        int L = std::min(kFwdL[pi], n);
-        r.tmask = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
-        r.rmask = ((n >= 32) ? 0xFFFFFFFFu : ((1u << n) - 1u)) & ~r.tmask;
-        r.L = L;
-        r.c = L;
-        r.op_begin = r.op_end = 0;
-        c->fwd.runs.push_back(r);
-        c->fwd.L = L;
-    }
-    c->adj = plan_sweep(n, kAdjL[pi], kCmin, exc, c->op_k);
+    const size_t A = c->prec ? 8 : 16;
+    c->fwd = plan_sweep(n, c->n_alpha, c->n_beta, A, 1, kSweepBudget, exc, c->op_k);
+    c->adj = plan_sweep(n, c->n_alpha, c->n_beta, A, 2, kSweepBudget, exc, c->op_k);
+    for (const SweepPlan *pl : {&c->fwd, &c->adj})
+        for (const CRunDev &r : pl->runs)
+            if ((size_t)r.max_entries * A * (pl == &c->adj ? 2 : 1) > kSweepBudget)
+                return fail(c, UCCSD_ERR_ARG, "an excitation does not fit one shared-memory tile");
     // per-amplitude CSR of schedule factors (for the gradient sum)
     std::vector<int32_t> k_ptr(K + 1, 0), k_ops;
     for (size_t o = 0; o < c->op_k.size(); ++o) k_ptr[c->op_k[o] + 1]++;
@@ -570,15 +572,38 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     std::vector<int32_t> fill(k_ptr.begin(), k_ptr.end() - 1);
     for (size_t o = 0; o < c->op_k.size(); ++o) k_ops[fill[c->op_k[o]]++] = int32_t(o);
     uccsd_status st;
-    OpDev *p1;
+    COpDev *p1;
     int32_t *p2;
     double *p3;
+    uint32_t *p4;
+    uint16_t *p5;
     if ((st = upload(c, "fwd_ops", c->fwd.ops, &p1))) return st;
     if ((st = upload(c, "adj_ops", c->adj.ops, &p1))) return st;
     if ((st = upload(c, "op_k", c->op_k, &p2))) return st;
     if ((st = upload(c, "op_scale", c->op_scale, &p3))) return st;
     if ((st = upload(c, "k_ptr", k_ptr, &p2))) return st;
     if ((st = upload(c, "k_ops", k_ops, &p2))) return st;
+    if ((st = upload(c, "op_tiles", c->adj.op_tiles, &p2))) return st;
+    // combinatorial rank tables (shared by both sweeps)
+    std::vector<uint16_t> combos, ranks;
+    std::vector<int32_t> coffs;
+    build_comb_tables(&combos, &ranks, &coffs);
+    SweepArgs base{};
+    if ((st = upload(c, "combos", combos, &p5))) return st;
+    base.combos = p5;
+    if ((st = upload(c, "ranks", ranks, &p5))) return st;
+    base.ranks = p5;
+    if ((st = upload(c, "comb_offs", coffs, &p2))) return st;
+    base.comb_offs = p2;
+    for (int q = 0; q < n; q += 2) base.amask |= 1u << q;
+    base.n_alpha = c->n_alpha;
+    base.n_beta = c->n_beta;
+    c->fwd_args = base;
+    c->adj_args = base;
+    if ((st = upload(c, "fwd_spread", c->fwd.spread, &p4))) return st;
+    c->fwd_args.spread = p4;
+    if ((st = upload(c, "adj_spread", c->adj.spread, &p4))) return st;
+    c->adj_args.spread = p4;
     c->have_exc = true;
     c->state_valid = false;
     return alloc_slots(c);

@@ -23,32 +23,39 @@ struct GroupT {
     R lut[16];
 };
 
-// One factor exp(angle * G) of the Trotter schedule, in the local bit space
-// of the shared-memory tile of the run that applies it.  For a basis state
-// x with the occupied-side pattern (occ bits set, the other flip bits
-// clear) and partner x' = x ^ flip:
-//   G|x>  = s(x)|x'>,   G|x'> = -s(x)|x>,
-//   s(x)  = s0 * (-1)^{popc(x_local & par_l) + popc(x_rest & par_rest)}.
-struct OpDev {
-    uint32_t flip_l;    // flipped bits (tile-local positions)
-    uint32_t occ_l;     // bits that are occupied on the x side (local)
-    uint32_t par_l;     // Jordan-Wigner parity mask inside the tile (local)
-    uint32_t par_rest;  // Jordan-Wigner parity mask outside the tile (global bits)
-    int32_t nb;         // 2 (single) or 4 (double)
-    int32_t pos[4];     // flipped local bit positions, ascending
-    int32_t s0;         // +1 or -1
-    int32_t op;         // index of this factor in the schedule
+// A shared-memory pass over compact sector tiles.  The factors
+// [op_begin, op_end) of the schedule flip only bits inside the tile bit set
+// `tmask`, so every tile (fixed values of the other bits) evolves on its
+// own.  A tile keeps only its electron-sector entries: with (a, b) the
+// alpha/beta electrons the sector leaves for the tile bits, the entries
+// form a dense [C(La, a)] x [C(Lb, b)] array indexed by the ranks of the
+// tile's alpha and beta bit strings among the strings of the same
+// popcount.  Amplitudes outside the sector are zero and never touched.
+struct CRunDev {
+    uint32_t tmask;      // tile bits (global positions)
+    uint32_t rmask;      // the other bits
+    int32_t La, Lb;      // alpha / beta bits of the tile
+    int32_t op_begin, op_end;
+    int32_t spread_off;  // run's spread table: 2^La alpha then 2^Lb beta entries
+    int32_t n_tiles;     // 2^(n - La - Lb)
+    int32_t max_entries; // largest compact tile over the run's CTAs
 };
 
-// A shared-memory pass: the factors [op_begin, op_end) of the schedule all
-// flip only bits inside the tile bit set `tmask` (L bits, containing the
-// low bits 0..c-1), so every tile of 2^L amplitudes evolves on its own.
-struct RunDev {
-    uint32_t tmask;     // tile bits (global positions)
-    uint32_t rmask;     // the other bits
-    int32_t L;          // popcount(tmask)
-    int32_t c;          // contiguous low bits in tmask
-    int32_t op_begin, op_end;  // range in the run's op table
+// One factor exp(angle * G) of the schedule in the string spaces of its
+// run's tile (bit k of an alpha string = the k-th alpha bit of the tile).
+// The occupied side of a pair has the bits oa/ob set and the other flip
+// bits clear; the partner flips fa/fb.  JW sign of the pair:
+//   s0 * (-1)^{popc(sa & pa) + popc(sb & pb) + popc(rest & par_rest)}.
+struct COpDev {
+    uint32_t fa, fb;      // flipped bits
+    uint32_t oa, ob;      // occupied-side bits
+    uint32_t pa, pb;      // Jordan-Wigner parity bits inside the tile
+    uint32_t par_rest;    // Jordan-Wigner parity bits outside the tile (global)
+    int32_t nfa, nfb;     // popcounts of fa, fb
+    int32_t noa, nob;     // popcounts of oa, ob
+    int32_t posa[4], posb[4];  // flip positions, ascending
+    int32_t s0;           // +1 or -1
+    int32_t op;           // index of this factor in the schedule
 };
 
 }  // namespace uccsd

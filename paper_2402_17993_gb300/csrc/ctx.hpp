@@ -12,14 +12,11 @@
 #include "plan.hpp"
 
 namespace uccsd {
-// Tile bits of the kernels per precision (shared memory per CTA):
-//   forward  FP32 13 (64 KiB), FP64 12 (64 KiB)
-//   adjoint  FP32 12 (2 x 32 KiB), FP64 11 (2 x 32 KiB)
-//   H-apply  12 (32 / 64 KiB)
-inline constexpr int kFwdL[2] = {12, 13};
-inline constexpr int kAdjL[2] = {11, 12};
+// Tile bits of the H-apply (low bits of the amplitude index).
 inline constexpr int kHL = 12;
-inline constexpr int kCmin = 3;
+// Shared memory budget of one compact sweep tile (forward: one vector,
+// adjoint: phi and lambda), bytes.
+inline constexpr size_t kSweepBudget = 200 * 1024;
 }  // namespace uccsd
 
 struct uccsd_ctx {
@@ -42,6 +39,7 @@ struct uccsd_ctx {
     std::vector<int32_t> ijab, op_k;
     std::vector<double> op_scale;
     uccsd::SweepPlan fwd, adj;
+    uccsd::SweepArgs fwd_args, adj_args;
     int LH = uccsd::kHL;
     int B = 1;          // reserved slots
     bool state_valid = false;

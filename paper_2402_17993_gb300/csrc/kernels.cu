@@ -30,34 +30,31 @@ struct Vec2<double> {
 template <typename R>
 using V2 = typename Vec2<R>::T;
 
-// Deposit the low bits of v into the positions of mask (software pdep).
-__device__ __forceinline__ uint32_t deposit(uint32_t v, uint32_t mask) {
-    uint32_t r = 0;
-    while (mask) {
-        uint32_t low = mask & (0u - mask);
-        if (v & 1u) r |= low;
-        v >>= 1;
-        mask ^= low;
-    }
-    return r;
-}
-
-// Insert a zero bit at each of the ascending positions pos[0..nb).
-__device__ __forceinline__ uint32_t insert_zeros(uint32_t j, const int32_t *pos, int nb) {
-#pragma unroll 4
-    for (int k = 0; k < nb; ++k) {
-        int p = pos[k];
-        uint32_t lowm = (1u << p) - 1u;
-        j = ((j & ~lowm) << 1) | (j & lowm);
-    }
-    return j;
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
+}
+
+// acc += v * p.  FP32 accumulators carry a Kahan compensation term so that
+// the sum of thousands of group contributions per amplitude keeps FP32
+// relative accuracy (FP64 accumulators add plainly).
+template <typename R>
+__device__ __forceinline__ void accumulate(V2<R> &acc, V2<R> &comp, R v, V2<R> p) {
+    if constexpr (sizeof(R) == 4) {
+        const R yx = v * p.x - comp.x;
+        const R tx = acc.x + yx;
+        comp.x = (tx - acc.x) - yx;
+        acc.x = tx;
+        const R yy = v * p.y - comp.y;
+        const R ty = acc.y + yy;
+        comp.y = (ty - acc.y) - yy;
+        acc.y = ty;
+    } else {
+        acc.x += v * p.x;
+        acc.y += v * p.y;
+    }
 }
 
 // Fixed-order block sum (deterministic); result valid in thread 0.
@@ -92,93 +89,6 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
     v.x = (R)c;
     v.y = (R)s;
     cs[(size_t)b * n_ops + o] = v;
-}
-
-// ---------------------------------------------------------------------------
-// Tile load/store helpers.  Tile-local index l maps to the global index
-// hi[l >> c] | (l & (2^c - 1)) | rest, where hi[] deposits the upper tile
-// bits; the low c tile bits are global bits 0..c-1 (contiguous runs).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void build_hi_table(uint32_t *hi, const RunDev &run) {
-    const uint32_t cmask = (1u << run.c) - 1u;
-    const uint32_t upper = run.tmask & ~cmask;
-    const int nhi = 1 << (run.L - run.c);
-    for (int j = threadIdx.x; j < nhi; j += blockDim.x) hi[j] = deposit((uint32_t)j, upper);
-}
-
-// ---------------------------------------------------------------------------
-// Forward sweep (Eq. 5): one shared-memory pass applies the factors of a
-// run to every tile.  Pair (x, x ^ flip) with x on the occupied side:
-//   psi_x  <- c psi_x  - s sn psi_x'
-//   psi_x' <- c psi_x' + s sn psi_x
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kThreads) forward_run_kernel(V2<R> *__restrict__ psi, size_t N,
-                                                               RunDev run,
-                                                               const OpDev *__restrict__ ops,
-                                                               const V2<R> *__restrict__ cs,
-                                                               int n_ops, int init_hf,
-                                                               uint32_t hf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
-    uint32_t *hi = reinterpret_cast<uint32_t *>(tile + (1u << run.L));
-    const int b = blockIdx.y;
-    V2<R> *st = psi + (size_t)b * N;
-    const uint32_t rest = deposit(blockIdx.x, run.rmask);
-    const uint32_t tsize = 1u << run.L;
-    const uint32_t cmask = (1u << run.c) - 1u;
-    build_hi_table(hi, run);
-    __syncthreads();
-    if (init_hf) {
-        V2<R> z;
-        z.x = (R)0;
-        z.y = (R)0;
-        for (uint32_t l = threadIdx.x; l < tsize; l += blockDim.x) tile[l] = z;
-        __syncthreads();
-        if (threadIdx.x == 0 && (hf & run.rmask) == rest) {
-            // local index of hf: gather its tile bits
-            uint32_t l = 0;
-            int k = 0;
-            for (uint32_t m = run.tmask; m; m &= m - 1) {
-                int bit = __ffs(m) - 1;
-                l |= ((hf >> bit) & 1u) << k++;
-            }
-            V2<R> one;
-            one.x = (R)1;
-            one.y = (R)0;
-            tile[l] = one;
-        }
-    } else {
-        for (uint32_t l = threadIdx.x; l < tsize; l += blockDim.x)
-            tile[l] = st[hi[l >> run.c] | (l & cmask) | rest];
-    }
-    __syncthreads();
-    for (int o = run.op_begin; o < run.op_end; ++o) {
-        const OpDev &op = ops[o];
-        const V2<R> csv = cs[(size_t)b * n_ops + op.op];
-        const R ct = csv.x;
-        const R st0 = op.s0 > 0 ? csv.y : -csv.y;
-        const uint32_t rpar = __popc(rest & op.par_rest) & 1u;
-        const uint32_t npairs = tsize >> op.nb;
-        int32_t pos[4] = {op.pos[0], op.pos[1], op.pos[2], op.pos[3]};
-        for (uint32_t j = threadIdx.x; j < npairs; j += blockDim.x) {
-            const uint32_t x = insert_zeros(j, pos, op.nb) | op.occ_l;
-            const uint32_t xp = x ^ op.flip_l;
-            const uint32_t par = (__popc(x & op.par_l) + rpar) & 1u;
-            const R ss = par ? -st0 : st0;
-            const V2<R> a = tile[x], bb = tile[xp];
-            V2<R> na, nb;
-            na.x = ct * a.x - ss * bb.x;
-            na.y = ct * a.y - ss * bb.y;
-            nb.x = ct * bb.x + ss * a.x;
-            nb.y = ct * bb.y + ss * a.y;
-            tile[x] = na;
-            tile[xp] = nb;
-        }
-        __syncthreads();
-    }
-    for (uint32_t l = threadIdx.x; l < tsize; l += blockDim.x)
-        st[hi[l >> run.c] | (l & cmask) | rest] = tile[l];
 }
 
 // ---------------------------------------------------------------------------
@@ -237,13 +147,15 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
     double e = 0.0, nrm = 0.0;
     if (cnt > 0) {
         uint32_t xl[APT];
-        V2<R> acc[APT];
+        V2<R> acc[APT], comp[APT];
 #pragma unroll
         for (int i = 0; i < APT; ++i) {
             const int j = threadIdx.x + i * blockDim.x;
             xl[i] = j < cnt ? sl.perm[o_beg + j] : 0xFFFFFFFFu;
             acc[i].x = (R)0;
             acc[i].y = (R)0;
+            comp[i].x = (R)0;
+            comp[i].y = (R)0;
         }
         for (int s = 0; s < H.n_seg; ++s) {
             const uint32_t hs = h ^ H.seg_d[s];
@@ -284,9 +196,7 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
                         }
                     }
                     if (__popc(y & jm) & 1u) v = -v;
-                    const V2<R> p = tile[yl];
-                    acc[i].x += v * p.x;
-                    acc[i].y += v * p.y;
+                    accumulate<R>(acc[i], comp[i], v, tile[yl]);
                 }
             }
         }
@@ -312,8 +222,7 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
                     }
                 }
                 const R v = (R)q * (R)H.diag_unit;
-                acc[i].x += v * p.x;
-                acc[i].y += v * p.y;
+                accumulate<R>(acc[i], comp[i], v, p);
             }
             e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
             nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
@@ -329,100 +238,15 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
 }
 
 // ---------------------------------------------------------------------------
-// Adjoint sweep: for the factors of a run in reverse order,
-//   g_o = 2 Re <lambda|G phi>   (partial over this tile, FP64)
-//   phi <- U(-angle) phi,  lambda <- U(-angle) lambda
-// Per-op warp partials go through a two-slot shared-memory ring and are
-// summed in a fixed order, then written to gpart[b][op][tile].
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void __launch_bounds__(kThreads) adjoint_run_kernel(
-    V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, RunDev run,
-    const OpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops,
-    double *__restrict__ gpart, int n_tiles) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t tsize = 1u << run.L;
-    V2<R> *tp = reinterpret_cast<V2<R> *>(smem_raw);
-    V2<R> *tl = tp + tsize;
-    uint32_t *hi = reinterpret_cast<uint32_t *>(tl + tsize);
-    __shared__ double wring[2][32];
-    const int b = blockIdx.y;
-    V2<R> *sp = phi + (size_t)b * N;
-    V2<R> *sl = lam + (size_t)b * N;
-    const uint32_t rest = deposit(blockIdx.x, run.rmask);
-    const uint32_t cmask = (1u << run.c) - 1u;
-    const int nw = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    build_hi_table(hi, run);
-    __syncthreads();
-    for (uint32_t l = threadIdx.x; l < tsize; l += blockDim.x) {
-        const uint32_t gx = hi[l >> run.c] | (l & cmask) | rest;
-        tp[l] = sp[gx];
-        tl[l] = sl[gx];
-    }
-    __syncthreads();
-    int it = 0;
-    for (int o = run.op_end - 1; o >= run.op_begin; --o, ++it) {
-        const OpDev &op = ops[o];
-        const V2<R> csv = cs[(size_t)b * n_ops + op.op];
-        const R ct = csv.x;
-        const R st0 = op.s0 > 0 ? csv.y : -csv.y;
-        const uint32_t rpar = __popc(rest & op.par_rest) & 1u;
-        const uint32_t npairs = tsize >> op.nb;
-        int32_t pos[4] = {op.pos[0], op.pos[1], op.pos[2], op.pos[3]};
-        R part = (R)0;
-        for (uint32_t j = threadIdx.x; j < npairs; j += blockDim.x) {
-            const uint32_t x = insert_zeros(j, pos, op.nb) | op.occ_l;
-            const uint32_t xp = x ^ op.flip_l;
-            const bool neg = ((__popc(x & op.par_l) + rpar) & 1u) != 0u;
-            const V2<R> fa = tp[x], fb = tp[xp];
-            const V2<R> la = tl[x], lb = tl[xp];
-            // (G phi)_x = -s phi_x', (G phi)_x' = s phi_x
-            const R d = (lb.x * fa.x + lb.y * fa.y) - (la.x * fb.x + la.y * fb.y);
-            part += neg ? -d : d;
-            const R ss = neg ? -st0 : st0;
-            V2<R> v;
-            v.x = ct * fa.x + ss * fb.x;
-            v.y = ct * fa.y + ss * fb.y;
-            tp[x] = v;
-            v.x = ct * fb.x - ss * fa.x;
-            v.y = ct * fb.y - ss * fa.y;
-            tp[xp] = v;
-            v.x = ct * la.x + ss * lb.x;
-            v.y = ct * la.y + ss * lb.y;
-            tl[x] = v;
-            v.x = ct * lb.x - ss * la.x;
-            v.y = ct * lb.y - ss * la.y;
-            tl[xp] = v;
-        }
-        // s0 enters the derivative once
-        double dp = (double)part * (double)op.s0;
-        dp = warp_sum(dp);
-        const int buf = it & 1;
-        if (lane == 0) wring[buf][warp] = dp;
-        __syncthreads();
-        // Warp 0 folds the previous-but-now-complete slot: this op's slot.
-        if (warp == 0) {
-            double s = (lane < nw) ? wring[buf][lane] : 0.0;
-            s = warp_sum(s);
-            if (lane == 0) gpart[((size_t)b * n_ops + op.op) * n_tiles + blockIdx.x] = s;
-        }
-    }
-    for (uint32_t l = threadIdx.x; l < tsize; l += blockDim.x) {
-        const uint32_t gx = hi[l >> run.c] | (l & cmask) | rest;
-        sp[gx] = tp[l];
-        sl[gx] = tl[l];
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Final deterministic reductions: E[b] = sum over H tiles; grad[b][k] =
 // sum over the schedule factors o of k of 2 * scale_o * sum over tiles.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restrict__ Epart,
                                                           int n_tiles_h,
                                                           const double *__restrict__ gpart,
-                                                          int n_tiles_a, int n_ops, int K,
+                                                          int tile_stride,
+                                                          const int32_t *__restrict__ op_tiles,
+                                                          int n_ops, int K,
                                                           const int32_t *__restrict__ k_ptr,
                                                           const int32_t *__restrict__ k_ops,
                                                           const double *__restrict__ op_scale,
@@ -452,9 +276,10 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
         double gk = 0.0;
         for (int u = k_ptr[k]; u < k_ptr[k + 1]; ++u) {
             const int o = k_ops[u];
-            const double *p = gpart + ((size_t)b * n_ops + o) * n_tiles_a;
+            const double *p = gpart + ((size_t)b * n_ops + o) * tile_stride;
+            const int nt = op_tiles[o];
             double s = 0.0;
-            for (int t = lane; t < n_tiles_a; t += 32) s += p[t];
+            for (int t = lane; t < nt; t += 32) s += p[t];
             s = warp_sum(s);
             gk += 2.0 * op_scale[o] * s;
         }
@@ -468,14 +293,6 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
 // Launch wrappers
 // ---------------------------------------------------------------------------
 template <typename R>
-size_t forward_smem(int L, int c) {
-    return (sizeof(V2<R>) << L) + (sizeof(uint32_t) << (L - c));
-}
-template <typename R>
-size_t adjoint_smem(int L, int c) {
-    return (2 * sizeof(V2<R>) << L) + (sizeof(uint32_t) << (L - c));
-}
-template <typename R>
 size_t happly_smem(int LH) {
     return sizeof(V2<R>) << LH;
 }
@@ -486,17 +303,6 @@ cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const in
     dim3 grid((cfg.n_ops + kThreads - 1) / kThreads, cfg.B);
     cs_kernel<R><<<grid, kThreads, 0, cfg.stream>>>(theta, K, op_k, op_scale, cfg.n_ops,
                                                      static_cast<V2<R> *>(cs));
-    return cudaGetLastError();
-}
-
-template <typename R>
-cudaError_t launch_forward_run(const LaunchCfg &cfg, void *psi, const RunDev &run,
-                               const OpDev *ops, const void *cs, int init_hf, uint32_t hf) {
-    dim3 grid(1u << (cfg.n - run.L), cfg.B);
-    int threads = std::min<int>(kThreads, std::max(32, 1 << run.L));
-    forward_run_kernel<R><<<grid, threads, forward_smem<R>(run.L, run.c), cfg.stream>>>(
-        static_cast<V2<R> *>(psi), cfg.N, run, ops, static_cast<const V2<R> *>(cs), cfg.n_ops,
-        init_hf, hf);
     return cudaGetLastError();
 }
 
@@ -513,24 +319,15 @@ cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int 
     return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_adjoint_run(const LaunchCfg &cfg, void *phi, void *lam, const RunDev &run,
-                               const OpDev *ops, const void *cs, double *gpart, int n_tiles) {
-    dim3 grid(1u << (cfg.n - run.L), cfg.B);
-    int threads = std::min<int>(kThreads, std::max(32, 1 << run.L));
-    adjoint_run_kernel<R><<<grid, threads, adjoint_smem<R>(run.L, run.c), cfg.stream>>>(
-        static_cast<V2<R> *>(phi), static_cast<V2<R> *>(lam), cfg.N, run, ops,
-        static_cast<const V2<R> *>(cs), cfg.n_ops, gpart, n_tiles);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles_h,
-                          const double *gpart, int n_tiles_a, int K, const int32_t *k_ptr,
+                          const double *gpart, int tile_stride, const int32_t *op_tiles,
+                          int K, const int32_t *k_ptr,
                           const int32_t *k_ops, const double *op_scale, double shift,
                           int rayleigh, double *E, double *grad) {
     int gx = grad ? std::max(1, std::min(64, (K + 7) / 8)) : 1;
     dim3 grid(gx, cfg.B);
-    reduce_kernel<<<grid, kThreads, 0, cfg.stream>>>(Epart, n_tiles_h, gpart, n_tiles_a, cfg.n_ops,
+    reduce_kernel<<<grid, kThreads, 0, cfg.stream>>>(Epart, n_tiles_h, gpart, tile_stride, op_tiles,
+                                                     cfg.n_ops,
                                                      K, k_ptr, k_ops, op_scale, shift, rayleigh, E,
                                                      grad);
     return cudaGetLastError();
@@ -542,10 +339,6 @@ cudaError_t configure_kernels() {
 #define UCCSD_SET(fn)                                                                  \
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big);   \
     if (e != cudaSuccess) return e;
-    UCCSD_SET(forward_run_kernel<float>);
-    UCCSD_SET(forward_run_kernel<double>);
-    UCCSD_SET(adjoint_run_kernel<float>);
-    UCCSD_SET(adjoint_run_kernel<double>);
     UCCSD_SET((happly_kernel<float, 4>));
     UCCSD_SET((happly_kernel<double, 4>));
 #undef UCCSD_SET
@@ -553,18 +346,11 @@ cudaError_t configure_kernels() {
 }
 
 #define UCCSD_INST(R)                                                                          \
-    template size_t forward_smem<R>(int, int);                                                 \
-    template size_t adjoint_smem<R>(int, int);                                                 \
     template size_t happly_smem<R>(int);                                                       \
     template cudaError_t launch_cs<R>(const LaunchCfg &, const double *, int, const int32_t *, \
                                       const double *, void *);                                 \
-    template cudaError_t launch_forward_run<R>(const LaunchCfg &, void *, const RunDev &,      \
-                                               const OpDev *, const void *, int, uint32_t);    \
     template cudaError_t launch_happly<R>(const LaunchCfg &, const void *, void *, int,        \
-                                          const DevHam<R> &, const HSector &, double *, int);  \
-    template cudaError_t launch_adjoint_run<R>(const LaunchCfg &, void *, void *,              \
-                                               const RunDev &, const OpDev *, const void *,    \
-                                               double *, int);
+                                          const DevHam<R> &, const HSector &, double *, int);
 UCCSD_INST(float)
 UCCSD_INST(double)
 #undef UCCSD_INST

@@ -51,31 +51,49 @@ template <typename R>
 cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const int32_t *op_k,
                       const double *op_scale, void *cs);
 
+// Tables shared by the compact-tile sweeps (see plan.hpp).
+struct SweepArgs {
+    const uint16_t *combos = nullptr;    // strings sorted by (popcount, value), per bit count
+    const uint16_t *ranks = nullptr;     // rank of a string within its popcount class
+    const int32_t *comb_offs = nullptr;  // class offsets, 17 per bit count
+    const uint32_t *spread = nullptr;    // per run: tile string -> global bits
+    uint32_t amask = 0;                  // alpha qubits (even positions)
+    int n_alpha = 0, n_beta = 0;
+};
+
 template <typename R>
-cudaError_t launch_forward_run(const LaunchCfg &cfg, void *psi, const RunDev &run,
-                               const OpDev *ops, const void *cs, int init_hf, uint32_t hf);
+cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev &run,
+                                 const COpDev *ops, const void *cs, const SweepArgs &sa,
+                                 int init_hf, uint32_t hf);
+
+template <typename R>
+cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, const CRunDev &run,
+                                 const COpDev *ops, const void *cs, const SweepArgs &sa,
+                                 double *gpart, int tile_stride);
+
+// |HF> in every slot (used when the schedule is empty).
+template <typename R>
+cudaError_t launch_set_hf(const LaunchCfg &cfg, void *psi, uint32_t hf);
+
+// Dynamic shared memory opt-in of the sweep kernels.
+cudaError_t configure_sweep_kernels(size_t max_smem);
 
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
                           const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma);
 
-template <typename R>
-cudaError_t launch_adjoint_run(const LaunchCfg &cfg, void *phi, void *lam, const RunDev &run,
-                               const OpDev *ops, const void *cs, double *gpart, int n_tiles);
-
 // E[b] from the per-tile partials (e', n) of sum Re(conj psi (H - shift) psi)
 // and sum |psi|^2: E = shift * n + e' (rayleigh = 0) or shift + e'/n
 // (rayleigh = 1); the gradient is divided by n when rayleigh = 1.
+// gpart[b][o][t] holds op_tiles[o] tile partials of factor o (row stride
+// tile_stride).
 cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles_h,
-                          const double *gpart, int n_tiles_a, int K, const int32_t *k_ptr,
+                          const double *gpart, int tile_stride, const int32_t *op_tiles,
+                          int K, const int32_t *k_ptr,
                           const int32_t *k_ops, const double *op_scale, double shift,
                           int rayleigh, double *E, double *grad);
 
-// Shared memory needed by each kernel for tile bits L.
-template <typename R>
-size_t forward_smem(int L, int c);
-template <typename R>
-size_t adjoint_smem(int L, int c);
+// Shared memory of the H-apply kernel for tile bits LH.
 template <typename R>
 size_t happly_smem(int LH);
 

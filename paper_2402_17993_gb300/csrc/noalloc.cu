@@ -93,8 +93,8 @@ extern "C" uccsd_status uccsd_expectation_noalloc(uccsd_ctx *c, const void *psi,
     else
         e = uccsd::launch_happly<double>(cfg, psi, nullptr, c->LH, c->hf64, c->hsec, partials, 0);
     if (e == cudaSuccess)
-        e = uccsd::launch_reduce(cfg, partials, tiles, nullptr, 1, 0, nullptr, nullptr, nullptr,
-                                 c->shift, c->prec ? 1 : 0, E, nullptr);
+        e = uccsd::launch_reduce(cfg, partials, tiles, nullptr, 1, nullptr, 0, nullptr, nullptr,
+                                 nullptr, c->shift, c->prec ? 1 : 0, E, nullptr);
     if (e != cudaSuccess) {
         c->failed = true;
         c->err = std::string("uccsd_expectation_noalloc kernel: ") + cudaGetErrorString(e);

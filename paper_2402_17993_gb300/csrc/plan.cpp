@@ -69,55 +69,127 @@ void build_schedule(int K, int order, int M, std::vector<int32_t> *op_k,
     }
 }
 
-SweepPlan plan_sweep(int n_qubits, int L, int c_min, const std::vector<CompiledExc> &exc,
+namespace {
+long long binom(int m, int k) {
+    if (k < 0 || k > m) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (m - k + i) / i;
+    return r;
+}
+
+// Largest C(L, a) over the electron counts a that a tile with L bits of one
+// spin can hold when the other N_spin - L bits of that spin carry the rest.
+long long max_binom(int L, int n_spin_bits, int n_el) {
+    int lo = std::max(0, n_el - (n_spin_bits - L)), hi = std::min(L, n_el);
+    long long m = 0;
+    for (int a = lo; a <= hi; ++a) m = std::max(m, binom(L, a));
+    return m;
+}
+
+uint32_t deposit_bits(uint32_t v, uint32_t mask) {
+    uint32_t r = 0;
+    for (uint32_t m = mask; m; m &= m - 1) {
+        if (v & 1u) r |= m & (~m + 1u);
+        v >>= 1;
+    }
+    return r;
+}
+}  // namespace
+
+long long max_tile_entries(int n_qubits, int n_alpha, int n_beta, uint32_t tmask) {
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
+    const uint32_t bmask = ((n_qubits >= 32) ? 0xFFFFFFFFu : ((1u << n_qubits) - 1u)) & ~amask;
+    const int La = popc(tmask & amask), Lb = popc(tmask & bmask);
+    const int Na = popc(amask), Nb = popc(bmask);
+    return max_binom(La, Na, n_alpha) * max_binom(Lb, Nb, n_beta);
+}
+
+SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, int nvec,
+                     size_t budget, const std::vector<CompiledExc> &exc,
                      const std::vector<int32_t> &op_k) {
     SweepPlan plan;
-    L = std::min(L, n_qubits);
-    c_min = std::min(c_min, L);
-    plan.L = L;
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
     const uint32_t all = (n_qubits >= 32) ? 0xFFFFFFFFu : ((1u << n_qubits) - 1u);
-    const uint32_t low = (1u << c_min) - 1u;
+    const uint32_t bmask = all & ~amask;
+    auto fits = [&](uint32_t T) {
+        return (size_t)max_tile_entries(n_qubits, n_alpha, n_beta, T) * amp_bytes * nvec <= budget;
+    };
+    plan.op_tiles.assign(op_k.size(), 1);
     size_t o = 0;
     const size_t n_ops = op_k.size();
     while (o < n_ops) {
-        uint32_t U = low;
-        size_t e = o;
-        while (e < n_ops) {
-            uint32_t V = U | exc[op_k[e]].flip;
-            if (popc(V) > L) break;
-            U = V;
+        uint32_t U = exc[op_k[o]].flip;
+        size_t e = o + 1;
+        while (e < n_ops && fits(U | exc[op_k[e]].flip)) {
+            U |= exc[op_k[e]].flip;
             ++e;
         }
-        // pad with the lowest unused bits
-        for (int q = 0; q < n_qubits && popc(U) < L; ++q) U |= 1u << q;
-        RunDev r{};
+        CRunDev r{};
         r.tmask = U;
         r.rmask = all & ~U;
-        r.L = popc(U);
-        int c = 0;
-        while (c < n_qubits && ((U >> c) & 1u)) ++c;
-        r.c = c;
+        const uint32_t Ta = U & amask, Tb = U & bmask;
+        r.La = popc(Ta);
+        r.Lb = popc(Tb);
+        r.n_tiles = 1 << (n_qubits - r.La - r.Lb);
+        r.max_entries = int(max_tile_entries(n_qubits, n_alpha, n_beta, U));
+        r.spread_off = int(plan.spread.size());
+        for (uint32_t sidx = 0; sidx < (1u << r.La); ++sidx) plan.spread.push_back(deposit_bits(sidx, Ta));
+        for (uint32_t sidx = 0; sidx < (1u << r.Lb); ++sidx) plan.spread.push_back(deposit_bits(sidx, Tb));
         r.op_begin = int(plan.ops.size());
         for (size_t u = o; u < e; ++u) {
             const CompiledExc &x = exc[op_k[u]];
-            OpDev d{};
-            d.flip_l = gather_bits(x.flip, U);
-            d.occ_l = gather_bits(x.occ, U);
-            d.par_l = gather_bits(x.par, U);
+            COpDev d{};
+            d.fa = gather_bits(x.flip, Ta);
+            d.fb = gather_bits(x.flip, Tb);
+            d.oa = gather_bits(x.occ, Ta);
+            d.ob = gather_bits(x.occ, Tb);
+            d.pa = gather_bits(x.par, Ta);
+            d.pb = gather_bits(x.par, Tb);
             d.par_rest = x.par & ~U;
-            d.nb = x.nb;
-            int k = 0;
-            for (int b = 0; b < r.L; ++b)
-                if ((d.flip_l >> b) & 1u) d.pos[k++] = b;
+            d.nfa = popc(d.fa);
+            d.nfb = popc(d.fb);
+            d.noa = popc(d.oa);
+            d.nob = popc(d.ob);
+            int ka = 0, kb = 0;
+            for (int q = 0; q < 32; ++q) {
+                if ((d.fa >> q) & 1u) d.posa[ka++] = q;
+                if ((d.fb >> q) & 1u) d.posb[kb++] = q;
+            }
             d.s0 = x.s0;
             d.op = int(u);
             plan.ops.push_back(d);
+            plan.op_tiles[u] = r.n_tiles;
         }
         r.op_end = int(plan.ops.size());
+        plan.max_tiles = std::max(plan.max_tiles, r.n_tiles);
+        plan.max_entries = std::max(plan.max_entries, r.max_entries);
         plan.runs.push_back(r);
         o = e;
     }
     return plan;
+}
+
+void build_comb_tables(std::vector<uint16_t> *combos, std::vector<uint16_t> *rank,
+                       std::vector<int32_t> *offs) {
+    combos->assign((size_t(1) << (kCombMax + 1)) - 1, 0);
+    rank->assign(combos->size(), 0);
+    offs->assign(size_t(kCombMax + 1) * 17, 0);
+    for (int m = 0; m <= kCombMax; ++m) {
+        const size_t base = (size_t(1) << m) - 1;
+        size_t pos = 0;
+        for (int c = 0; c <= m; ++c) {
+            (*offs)[m * 17 + c] = int32_t(pos);
+            int32_t r = 0;
+            for (uint32_t s = 0; s < (1u << m); ++s)
+                if (popc(s) == c) {
+                    (*combos)[base + pos++] = uint16_t(s);
+                    (*rank)[base + s] = uint16_t(r++);
+                }
+        }
+        (*offs)[m * 17 + m + 1] = int32_t(pos);
+    }
 }
 
 }  // namespace uccsd

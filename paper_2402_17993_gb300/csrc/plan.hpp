@@ -22,15 +22,31 @@ void build_schedule(int K, int order, int M, std::vector<int32_t> *op_k,
                     std::vector<double> *op_scale);
 
 struct SweepPlan {
-    std::vector<RunDev> runs;
-    std::vector<OpDev> ops;   // ops of run r at [runs[r].op_begin, runs[r].op_end)
-    int L = 0;                // tile bits
+    std::vector<CRunDev> runs;
+    std::vector<COpDev> ops;       // ops of run r at [runs[r].op_begin, runs[r].op_end)
+    std::vector<uint32_t> spread;  // per run: deposit tables of alpha and beta strings
+    std::vector<int32_t> op_tiles; // per schedule factor: tiles of its run
+    int max_tiles = 1;
+    int max_entries = 1;
 };
 
-// Split the schedule into maximal consecutive runs whose flips fit in L tile
-// bits that always contain the low bits 0..c_min-1.  Each run's tile is the
-// union of its flips padded with the lowest unused bits.
-SweepPlan plan_sweep(int n_qubits, int L, int c_min, const std::vector<CompiledExc> &exc,
+// Largest compact tile (entries) of a tile bit set: the sector leaves
+// a alpha electrons for the tile's La alpha bits for every feasible split.
+long long max_tile_entries(int n_qubits, int n_alpha, int n_beta, uint32_t tmask);
+
+// Split the schedule into maximal consecutive runs whose flipped bits fit in
+// a tile bit set whose largest compact tile of `nvec` vectors of
+// `amp_bytes` amplitudes stays within `budget` bytes.
+SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, int nvec,
+                     size_t budget, const std::vector<CompiledExc> &exc,
                      const std::vector<int32_t> &op_k);
+
+// Combinatorial tables for bit strings of m <= kCombMax bits: for each m,
+// the 2^m strings sorted by (popcount, value) at combos[2^m - 1 ...], the
+// rank of each string among those of equal popcount at rank[2^m - 1 + s],
+// and offs[m * 17 + c] = start of popcount class c (c = 0..m+1).
+constexpr int kCombMax = 15;
+void build_comb_tables(std::vector<uint16_t> *combos, std::vector<uint16_t> *rank,
+                       std::vector<int32_t> *offs);
 
 }  // namespace uccsd
