@@ -203,7 +203,7 @@ uccsd_status uccsd_get_profile(const uccsd_ctx *ctx, uccsd_profile_t *out);
  *          the same quantity the context's evaluations report
  *
  * Scratch: a fixed device array of 2 * UCCSD_NOALLOC_MAX_TILES doubles
- * (256 KiB) inside the library, held by every GPU that loads the library
+ * (64 KiB) inside the library, held by every GPU that loads the library
  * until the process exits.  States above 26 qubits need more partials and
  * are rejected with UCCSD_ERR_ARG.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
@@ -211,7 +211,7 @@ uccsd_status uccsd_get_profile(const uccsd_ctx *ctx, uccsd_profile_t *out);
  * it keeps the last call's partials; each call overwrites what it reads, so
  * nothing has to be cleared, but calls that overlap on the GPU (different
  * streams or contexts without ordering between them) race on it. */
-#define UCCSD_NOALLOC_MAX_TILES 16384
+#define UCCSD_NOALLOC_MAX_TILES 4096
 uccsd_status uccsd_expectation_noalloc(uccsd_ctx *ctx, const void *psi, double *E,
                                        void *stream);
 

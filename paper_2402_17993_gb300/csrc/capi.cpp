@@ -56,6 +56,11 @@ HamTables<R> make_tables(const CompiledH &H, int LH) {
         g.spec = s.spec;
         g.active = s.active;
         for (int k = 0; k < 4; ++k) g.pos[k] = s.pos[k];
+        g.mla = g.mlb = 0;
+        for (int q = 0; q < LH; ++q)
+            if ((s.xmask >> q) & 1u) ((q & 1) ? g.mlb : g.mla) |= 1u << (q >> 1);
+        g.ha = __builtin_popcount(s.xmask & 0x55555555u) / 2;
+        g.hb = __builtin_popcount(s.xmask & 0xAAAAAAAAu) / 2;
         for (int p = 0; p < 16; ++p) g.lut[p] = R(s.lut[p]);
         T.groups.push_back(g);
     }
@@ -188,33 +193,37 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     return UCCSD_OK;
 }
 
-// Local indices of the H-apply tile (low LH bits, alpha = even bits)
-// grouped by (alpha count, beta count), ascending inside each group.
-uccsd_status upload_sector_lists(uccsd_ctx *c) {
-    const int LH = c->LH, half = LH / 2;
-    const int nk = (half + 1) * (half + 1);
-    std::vector<std::vector<uint16_t>> lists(nk);
-    for (uint32_t l = 0; l < (1u << LH); ++l) {
-        int a = __builtin_popcount(l & 0x55555555u), b = __builtin_popcount(l & 0xAAAAAAAAu);
-        lists[a * (half + 1) + b].push_back(uint16_t(l));
-    }
-    std::vector<uint16_t> perm;
-    std::vector<int32_t> offs;
-    int mx = 0;
-    for (auto &v : lists) {
-        offs.push_back(int32_t(perm.size()));
-        perm.insert(perm.end(), v.begin(), v.end());
-        mx = std::max(mx, int(v.size()));
-    }
-    offs.push_back(int32_t(perm.size()));
-    uint16_t *pp;
-    int32_t *po;
+// Tables of the compact H-apply tiles and the sweeps: combinatorial rank
+// tables (shared) and the deposits of low alpha / beta strings of the
+// H-apply tile (alpha string bit k = qubit 2k, beta string bit k = qubit 2k+1).
+uccsd_status upload_tile_tables(uccsd_ctx *c) {
+    std::vector<uint16_t> combos, ranks;
+    std::vector<int32_t> coffs;
+    build_comb_tables(&combos, &ranks, &coffs);
+    uint16_t *p5;
+    int32_t *p2;
+    uint32_t *p4;
     uccsd_status st;
-    if ((st = upload(c, "sector_perm", perm, &pp))) return st;
-    if ((st = upload(c, "sector_offs", offs, &po))) return st;
-    c->hsec.perm = pp;
-    c->hsec.offs = po;
-    c->hsec.max_list = mx;
+    if ((st = upload(c, "combos", combos, &p5))) return st;
+    c->hsec.combos = p5;
+    if ((st = upload(c, "ranks", ranks, &p5))) return st;
+    c->hsec.ranks = p5;
+    if ((st = upload(c, "comb_offs", coffs, &p2))) return st;
+    c->hsec.comb_offs = p2;
+    const int half = c->LH / 2;
+    std::vector<uint32_t> spread(size_t(2) << half);
+    for (uint32_t s = 0; s < (1u << half); ++s) {
+        uint32_t a = 0, b = 0;
+        for (int k = 0; k < half; ++k)
+            if ((s >> k) & 1u) {
+                a |= 1u << (2 * k);
+                b |= 1u << (2 * k + 1);
+            }
+        spread[s] = a;
+        spread[(size_t(1) << half) + s] = b;
+    }
+    if ((st = upload(c, "hspread", spread, &p4))) return st;
+    c->hsec.spread = p4;
     return UCCSD_OK;
 }
 
@@ -476,7 +485,7 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, con
     c->state_valid = false;
     c->shift = 0.0;
     make_fixed_point(c);
-    if ((st = upload_sector_lists(c))) return st;
+    if ((st = upload_tile_tables(c))) return st;
     if ((st = upload_ham<float>(c, &c->hf32, "h32_"))) return st;
     if ((st = upload_ham<double>(c, &c->hf64, "h64_"))) return st;
     c->have_h = true;
@@ -504,6 +513,8 @@ uccsd_status uccsd_set_reference(uccsd_ctx *c, int n_alpha, int n_beta) {
     c->hf64.diag_q0 = shifted_q0(c);
     c->hsec.n_alpha = n_alpha;
     c->hsec.n_beta = n_beta;
+    c->hsec.max_entries = int(max_tile_entries(c->n, n_alpha, n_beta,
+                                               (c->LH >= 32) ? 0xFFFFFFFFu : ((1u << c->LH) - 1u)));
     c->have_ref = true;
     c->have_exc = false;
     c->state_valid = false;
@@ -576,7 +587,6 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     int32_t *p2;
     double *p3;
     uint32_t *p4;
-    uint16_t *p5;
     if ((st = upload(c, "fwd_ops", c->fwd.ops, &p1))) return st;
     if ((st = upload(c, "adj_ops", c->adj.ops, &p1))) return st;
     if ((st = upload(c, "op_k", c->op_k, &p2))) return st;
@@ -584,17 +594,11 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     if ((st = upload(c, "k_ptr", k_ptr, &p2))) return st;
     if ((st = upload(c, "k_ops", k_ops, &p2))) return st;
     if ((st = upload(c, "op_tiles", c->adj.op_tiles, &p2))) return st;
-    // combinatorial rank tables (shared by both sweeps)
-    std::vector<uint16_t> combos, ranks;
-    std::vector<int32_t> coffs;
-    build_comb_tables(&combos, &ranks, &coffs);
+    // combinatorial rank tables (uploaded with the Hamiltonian)
     SweepArgs base{};
-    if ((st = upload(c, "combos", combos, &p5))) return st;
-    base.combos = p5;
-    if ((st = upload(c, "ranks", ranks, &p5))) return st;
-    base.ranks = p5;
-    if ((st = upload(c, "comb_offs", coffs, &p2))) return st;
-    base.comb_offs = p2;
+    base.combos = c->hsec.combos;
+    base.ranks = c->hsec.ranks;
+    base.comb_offs = c->hsec.comb_offs;
     for (int q = 0; q < n; q += 2) base.amask |= 1u << q;
     base.n_alpha = c->n_alpha;
     base.n_beta = c->n_beta;

@@ -20,6 +20,12 @@ struct GroupT {
     int32_t spec;      // offset into the spectator table (rows of 4), -1 = none
     uint32_t active;   // bit p set: pattern p conserves N_alpha and N_beta
     int32_t pos[4];    // flipped bit positions, ascending
+    // Flip bits inside the H-apply tile (the low LH bits) as alpha / beta
+    // string masks (alpha string bit k = qubit 2k, beta string bit k =
+    // qubit 2k+1), and the occupied flip bits an active source pattern
+    // has among the alpha / beta flip bits (half of them).
+    uint32_t mla, mlb;
+    int32_t ha, hb;
     R lut[16];
 };
 

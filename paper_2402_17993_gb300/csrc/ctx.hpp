@@ -13,7 +13,7 @@
 
 namespace uccsd {
 // Tile bits of the H-apply (low bits of the amplitude index).
-inline constexpr int kHL = 12;
+inline constexpr int kHL = 14;
 // Shared memory budget of one compact sweep tile (forward: one vector,
 // adjoint: phi and lambda), bytes.
 inline constexpr size_t kSweepBudget = 200 * 1024;

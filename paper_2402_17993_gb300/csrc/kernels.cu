@@ -15,7 +15,6 @@ namespace uccsd {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kHThreads = 128;  // H-apply: up to 4 sector entries per thread (<= 512 per tile)
 
 template <typename R>
 struct Vec2;
@@ -93,80 +92,92 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
 
 // ---------------------------------------------------------------------------
 // Hamiltonian action and energy (Section 2.3): sigma = (H - shift) psi over
-// X-mask groups, tile = the low LH bits of the amplitude index.
+// X-mask groups.
 //
-// H conserves N_alpha and N_beta, and psi vanishes outside the
-// (n_alpha, n_beta) sector, so only sector amplitudes are read or
-// produced: inside a tile whose high bits hold (a_h, b_h) electrons the
-// sector entries are the local indices with (n_alpha - a_h, n_beta - b_h)
-// electrons in the tile bits, listed contiguously in `perm` (offsets
-// `offs[a * (LH/2 + 1) + b]`).  For each segment of groups sharing the high
-// part d of their X-mask, the sector entries of the source tile (h ^ d) are
-// gathered into shared memory; a group contributes to output x only for a
-// number-conserving flip pattern, which keeps x ^ xmask inside the sector.
-// The own-tile segment (d = 0) runs last so psi_x is resident for the FP64
-// partials sum Re(conj(psi_x) sigma_x) and sum |psi_x|^2.  Entries of sigma
-// outside the sector are never written (they stay zero).
+// H conserves N_alpha and N_beta and psi vanishes outside the (n_alpha,
+// n_beta) sector, so only sector amplitudes are read or produced.  A CTA
+// owns one compact output tile: the sector amplitudes with fixed high bits
+// h above the low LH bits, stored as a [C(LH/2, a)] x [C(LH/2, b)] array
+// indexed by the ranks of their low alpha / beta strings (a, b = electrons
+// the sector leaves for the low bits).  Each thread keeps up to kHEPT
+// outputs in registers.  Groups are sorted into segments by the high part d
+// of their X-mask; for each segment the compact source tile h ^ d is
+// gathered into shared memory and every group of the segment adds
+//   f_g(y) psi_y,  y = x ^ xmask_g,
+// for the outputs whose flip pattern conserves the electron counts (then y
+// lies in the source tile).  The own tile (d = 0) is the last segment, so
+// psi_x is resident for the diagonal and the FP64 partials
+// sum Re(conj(psi_x) sigma_x) and sum |psi_x|^2.  Entries of sigma outside
+// the sector are never written (they stay zero).
 // ---------------------------------------------------------------------------
-struct SectorLists {
-    const uint16_t *perm;  // 2^LH local indices grouped by (alpha, beta) count
-    const int32_t *offs;   // (LH/2 + 1)^2 + 1 offsets
-    int n_alpha, n_beta;
+constexpr int kHThreadsV = 256;
+constexpr int kHEPT = 5;  // outputs per thread: 1280 >= C(7,3)^2, the largest 14-bit tile
+
+struct HTileView {
+    int a, b, Da, Db;
+    const uint16_t *ca, *cb;  // low alpha / beta strings of the tile's class
 };
 
-__device__ __forceinline__ void sector_range(const SectorLists &sl, int LH, uint32_t hi, int *beg,
-                                             int *end) {
-    const int half = LH >> 1;
-    const int a = sl.n_alpha - __popc(hi & 0x55555555u);
-    const int bb = sl.n_beta - __popc(hi & 0xAAAAAAAAu);
-    if (a < 0 || a > half || bb < 0 || bb > half) {
-        *beg = *end = 0;
-        return;
-    }
-    const int k = a * (half + 1) + bb;
-    *beg = sl.offs[k];
-    *end = sl.offs[k + 1];
+__device__ __forceinline__ bool htile(const HSector &hs, int half, uint32_t hi, HTileView *v) {
+    v->a = hs.n_alpha - __popc(hi & 0x55555555u);
+    v->b = hs.n_beta - __popc(hi & 0xAAAAAAAAu);
+    if (v->a < 0 || v->a > half || v->b < 0 || v->b > half) return false;
+    const int32_t *o = hs.comb_offs + half * 17;
+    v->Da = o[v->a + 1] - o[v->a];
+    v->Db = o[v->b + 1] - o[v->b];
+    v->ca = hs.combos + ((1 << half) - 1) + o[v->a];
+    v->cb = hs.combos + ((1 << half) - 1) + o[v->b];
+    return true;
 }
 
-template <typename R, int APT>
-__global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restrict__ psi,
-                                                           V2<R> *__restrict__ sig, size_t N,
-                                                           int LH, DevHam<R> H, SectorLists sl,
-                                                           double *__restrict__ Epart,
-                                                           int store_sigma) {
+template <typename R>
+__global__ void __launch_bounds__(kHThreadsV) happly_kernel(const V2<R> *__restrict__ psi,
+                                                            V2<R> *__restrict__ sig, size_t N,
+                                                            int LH, DevHam<R> H, HSector hs,
+                                                            double *__restrict__ Epart,
+                                                            int store_sigma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
     __shared__ double red[32];
+    __shared__ uint32_t spa[1 << 8], spb[1 << 8];  // half-width string -> low bits
+    __shared__ uint16_t rk[1 << 8];                 // rank of a half-width string
     const int b = blockIdx.y;
     const uint32_t h = blockIdx.x;
+    const int half = LH >> 1;
     const V2<R> *src = psi + (size_t)b * N;
-    const uint32_t lowmask = (1u << LH) - 1u;
-    int o_beg, o_end;
-    sector_range(sl, LH, h, &o_beg, &o_end);
-    const int cnt = o_end - o_beg;
+    for (int t = threadIdx.x; t < (1 << half); t += blockDim.x) {
+        spa[t] = hs.spread[t];
+        spb[t] = hs.spread[(1 << half) + t];
+        rk[t] = hs.ranks[((1 << half) - 1) + t];
+    }
+    __syncthreads();
+    HTileView ov;
     double e = 0.0, nrm = 0.0;
-    if (cnt > 0) {
-        uint32_t xl[APT];
-        V2<R> acc[APT], comp[APT];
+    if (htile(hs, half, h, &ov)) {
+        const int D = ov.Da * ov.Db;
+        uint32_t str[kHEPT];  // alpha string | beta string << 16, or ~0 when unused
+        V2<R> acc[kHEPT], comp[kHEPT];
 #pragma unroll
-        for (int i = 0; i < APT; ++i) {
+        for (int i = 0; i < kHEPT; ++i) {
             const int j = threadIdx.x + i * blockDim.x;
-            xl[i] = j < cnt ? sl.perm[o_beg + j] : 0xFFFFFFFFu;
-            acc[i].x = (R)0;
-            acc[i].y = (R)0;
-            comp[i].x = (R)0;
-            comp[i].y = (R)0;
+            if (j < D) {
+                const int ia = j / ov.Db;
+                str[i] = (uint32_t)ov.ca[ia] | ((uint32_t)ov.cb[j - ia * ov.Db] << 16);
+            } else {
+                str[i] = 0xFFFFFFFFu;
+            }
+            acc[i].x = acc[i].y = comp[i].x = comp[i].y = (R)0;
         }
         for (int s = 0; s < H.n_seg; ++s) {
-            const uint32_t hs = h ^ H.seg_d[s];
-            int s_beg, s_end;
-            sector_range(sl, LH, hs, &s_beg, &s_end);
-            if (s_beg == s_end && s != H.n_seg - 1) continue;  // source tile is all zero
-            const uint32_t base = hs << LH;
+            const uint32_t hsrc = h ^ H.seg_d[s];
+            HTileView sv;
+            if (!htile(hs, half, hsrc, &sv)) continue;  // source tile is all zero (uniform)
+            const uint32_t base = hsrc << LH;
+            const int Ds = sv.Da * sv.Db;
             __syncthreads();
-            for (int j = s_beg + threadIdx.x; j < s_end; j += blockDim.x) {
-                const uint32_t l = sl.perm[j];
-                tile[l] = src[base + l];
+            for (int j = threadIdx.x; j < Ds; j += blockDim.x) {
+                const int ia = j / sv.Db;
+                tile[j] = src[base | spa[sv.ca[ia]] | spb[sv.cb[j - ia * sv.Db]]];
             }
             __syncthreads();
             const int g_end = H.seg_begin[s + 1];
@@ -174,18 +185,23 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
                 const GroupT<R> *G = H.groups + g;
                 const uint32_t xm = G->xmask;
                 const uint32_t jm = G->jmask;
+                const uint32_t mla = G->mla, mlb = G->mlb;
+                // occupied flip bits the source carries above the tile (uniform)
+                const uint32_t xhi = xm >> LH;
+                const int need_a = G->ha - __popc(hsrc & xhi & 0x55555555u);
+                const int need_b = G->hb - __popc(hsrc & xhi & 0xAAAAAAAAu);
                 const int nb = G->nb;
                 const int spec = G->spec;
-                const uint32_t active = G->active;
                 const int p0 = G->pos[0], p1 = G->pos[1], p2 = G->pos[2], p3 = G->pos[3];
 #pragma unroll
-                for (int i = 0; i < APT; ++i) {
-                    if (xl[i] == 0xFFFFFFFFu) continue;
-                    const uint32_t yl = xl[i] ^ (xm & lowmask);
-                    const uint32_t y = base | yl;
+                for (int i = 0; i < kHEPT; ++i) {
+                    if (str[i] == 0xFFFFFFFFu) continue;
+                    const uint32_t ya = (str[i] & 0xFFFFu) ^ mla;
+                    const uint32_t yb = (str[i] >> 16) ^ mlb;
+                    if (__popc(ya & mla) != need_a || __popc(yb & mlb) != need_b) continue;
+                    const uint32_t y = base | spa[ya] | spb[yb];
                     int pat = ((y >> p0) & 1u) | (((y >> p1) & 1u) << 1);
                     if (nb == 4) pat |= (((y >> p2) & 1u) << 2) | (((y >> p3) & 1u) << 3);
-                    if (!((active >> pat) & 1u)) continue;
                     R v = G->lut[pat];
                     if (spec >= 0) {
                         uint32_t occ = y & ~xm;
@@ -196,20 +212,22 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
                         }
                     }
                     if (__popc(y & jm) & 1u) v = -v;
-                    accumulate<R>(acc[i], comp[i], v, tile[yl]);
+                    accumulate<R>(acc[i], comp[i], v, tile[rk[ya] * sv.Db + rk[yb]]);
                 }
             }
         }
-        // After the last segment (d = 0) the own tile is resident.
+        // The last segment is the own tile (d = 0): psi_x is resident.
         const uint32_t own = h << LH;
         const int n = H.n;
 #pragma unroll
-        for (int i = 0; i < APT; ++i) {
-            if (xl[i] == 0xFFFFFFFFu) continue;
-            const V2<R> p = tile[xl[i]];
+        for (int i = 0; i < kHEPT; ++i) {
+            if (str[i] == 0xFFFFFFFFu) continue;
+            const uint32_t sa = str[i] & 0xFFFFu, sb = str[i] >> 16;
+            const V2<R> p = tile[rk[sa] * ov.Db + rk[sb]];
+            const uint32_t x = own | spa[sa] | spb[sb];
             if (H.has_diag) {
                 long long q = H.diag_q0;
-                uint32_t o1 = own | xl[i];
+                uint32_t o1 = x;
                 while (o1) {
                     const int a = __ffs(o1) - 1;
                     o1 &= o1 - 1u;
@@ -221,12 +239,11 @@ __global__ void __launch_bounds__(kHThreads) happly_kernel(const V2<R> *__restri
                         q += H.diag_qb[a * n + r];
                     }
                 }
-                const R v = (R)q * (R)H.diag_unit;
-                accumulate<R>(acc[i], comp[i], v, p);
+                accumulate<R>(acc[i], comp[i], (R)q * (R)H.diag_unit, p);
             }
             e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
             nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-            if (store_sigma) sig[(size_t)b * N + (own | xl[i])] = acc[i];
+            if (store_sigma) sig[(size_t)b * N + x] = acc[i];
         }
     }
     e = block_sum(e, red);
@@ -293,8 +310,8 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
 // Launch wrappers
 // ---------------------------------------------------------------------------
 template <typename R>
-size_t happly_smem(int LH) {
-    return sizeof(V2<R>) << LH;
+size_t happly_smem(int max_entries) {
+    return sizeof(V2<R>) * (size_t)max_entries;
 }
 
 template <typename R>
@@ -309,12 +326,10 @@ cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const in
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
                           const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma) {
+    if (hs.max_entries > kHEPT * kHThreadsV) return cudaErrorInvalidValue;
     dim3 grid(1u << (cfg.n - LH), cfg.B);
-    const size_t smem = happly_smem<R>(LH);
-    SectorLists sl{hs.perm, hs.offs, hs.n_alpha, hs.n_beta};
-    if (hs.max_list > 4 * kHThreads) return cudaErrorInvalidValue;
-    happly_kernel<R, 4><<<grid, kHThreads, smem, cfg.stream>>>(
-        static_cast<const V2<R> *>(psi), static_cast<V2<R> *>(sig), cfg.N, LH, H, sl, Epart,
+    happly_kernel<R><<<grid, kHThreadsV, happly_smem<R>(hs.max_entries), cfg.stream>>>(
+        static_cast<const V2<R> *>(psi), static_cast<V2<R> *>(sig), cfg.N, LH, H, hs, Epart,
         store_sigma);
     return cudaGetLastError();
 }
@@ -339,8 +354,8 @@ cudaError_t configure_kernels() {
 #define UCCSD_SET(fn)                                                                  \
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big);   \
     if (e != cudaSuccess) return e;
-    UCCSD_SET((happly_kernel<float, 4>));
-    UCCSD_SET((happly_kernel<double, 4>));
+    UCCSD_SET((happly_kernel<float>));
+    UCCSD_SET((happly_kernel<double>));
 #undef UCCSD_SET
     return cudaSuccess;
 }

@@ -28,13 +28,17 @@ struct DevHam {
     int n = 0;                          // qubits (row length of diag_qb)
 };
 
-// Sector index lists of the H-apply tile (low LH bits): local indices
-// grouped by (alpha count, beta count), offsets per (a, b) pair.
+// Compact sector tiles of the H-apply: a tile is the set of sector
+// amplitudes with fixed values of the bits above the low LH bits; its entries
+// form a [C(LH/2, a)] x [C(LH/2, b)] array indexed by the ranks of the low
+// alpha and beta bit strings among strings of equal popcount.
 struct HSector {
-    const uint16_t *perm = nullptr;  // 2^LH
-    const int32_t *offs = nullptr;   // (LH/2 + 1)^2 + 1
+    const uint16_t *combos = nullptr;    // strings sorted by (popcount, value), per bit count
+    const uint16_t *ranks = nullptr;     // rank of a string within its popcount class
+    const int32_t *comb_offs = nullptr;  // class offsets, 17 per bit count
+    const uint32_t *spread = nullptr;    // 2^(LH/2) alpha then 2^(LH/2) beta string deposits
     int n_alpha = 0, n_beta = 0;
-    int max_list = 0;                // largest (a, b) list
+    int max_entries = 0;                 // largest compact tile
 };
 
 struct LaunchCfg {
@@ -93,9 +97,9 @@ cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles
                           const int32_t *k_ops, const double *op_scale, double shift,
                           int rayleigh, double *E, double *grad);
 
-// Shared memory of the H-apply kernel for tile bits LH.
+// Shared memory of the H-apply kernel for its largest compact tile.
 template <typename R>
-size_t happly_smem(int LH);
+size_t happly_smem(int max_entries);
 
 // One-time kernel attribute set-up (dynamic shared memory opt-in).
 cudaError_t configure_kernels();

@@ -20,7 +20,7 @@
 namespace {
 
 // Scratch of the no-allocation entry point: two doubles (energy, norm) per
-// H-apply tile, UCCSD_NOALLOC_MAX_TILES tiles (256 KiB).  Every GPU that
+// H-apply tile, UCCSD_NOALLOC_MAX_TILES tiles (64 KiB).  Every GPU that
 // loads this library holds one copy until the process exits.
 static __device__ __align__(256) double g_noalloc_partials[2 * UCCSD_NOALLOC_MAX_TILES];
 
