@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-scaleup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=512)
+    ap.add_argument("--serving-fp64-requests", type=int, default=48)
     return ap.parse_args()
 
 
@@ -165,12 +168,79 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def algorithmic(ctx_info, fam, B, n, amp_bytes, plan_fracs):
-    """Algorithmic bytes per launch of the pass kernels: one read and one
-    write of every amplitude of every slot (the compulsory traffic of a
-    shared-memory pass)."""
+# Peak of a plain-ALU kernel, derived from unit counts and clock: 152 SMs x
+# 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz; FP64 is GB300's 1.25 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+KERNEL_SOURCES = {"happly": "kernels.cu", "forward": "sweep.cu", "adjoint": "sweep.cu"}
+
+
+def algorithmic_per_state(fam, n, amp_bytes, ijab, n_groups):
+    """Algorithmic work of one evaluation of one state (the per-unit
+    figures of the hot-path table): sweeps move the active pairs of every
+    factor (read + write; 1/2 of the 2^n amplitudes for a single, 1/8 for a
+    double), the adjoint two vectors; the H-apply does one complex-times-
+    real update (4 flops) per X-mask group and amplitude."""
     N = 1 << n
-    return 2.0 * amp_bytes * N * B
+    singles = int(np.sum(ijab[:, 1] < 0))
+    doubles = len(ijab) - singles
+    fwd = 2.0 * amp_bytes * N * (singles / 2 + doubles / 8)
+    if fam == "forward":
+        return fwd, "bytes"
+    if fam == "adjoint":
+        return 2.0 * fwd, "bytes"
+    if fam == "happly":
+        return 4.0 * n_groups * N, "flops"
+    return 0.0, None
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary of this kernel
+    and workload, if the kernel source is unchanged since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    src = os.path.join(ROOT, "paper_2402_17993_gb300", "csrc", KERNEL_SOURCES.get(kernel, ""))
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    rec_sha, traffic = None, None
+    for line in open(path):
+        if line.startswith("kernel source sha256:"):
+            rec_sha = line.split(":", 1)[1].strip()
+        if line.startswith("| DRAM traffic per launch (read + write) |"):
+            traffic = float(line.split("|")[2].split()[0])
+    return traffic if rec_sha == sha else None
+
+
+def roofline(prof, B, n, amp_bytes, ijab, n_groups, prec_fp32, workload):
+    pk, pk_kind = peaks()
+    fams = {}
+    for fam in ("forward", "happly", "adjoint"):
+        if prof["launches"][fam] == 0:
+            continue
+        per_state, kind = algorithmic_per_state(fam, n, amp_bytes, ijab, n_groups)
+        calls = max(1, prof["calls"])
+        ms = prof["ms"][fam] / calls                      # device time per evaluation call
+        launches = prof["launches"][fam] / calls
+        work = per_state * B                              # per evaluation call (all launches)
+        if kind == "bytes":
+            achieved = work / (ms / 1e3) / 1e9
+            peak, unit, bound = pk["hbm_gbs"], "GB/s", "hbm"
+        else:
+            achieved = work / (ms / 1e3) / 1e12
+            peak = FP32_PEAK_TFLOPS if prec_fp32 else FP64_PEAK_TFLOPS
+            unit, bound = "TFLOP/s", "alu"
+        fams[fam] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "ms_per_step": ms, "launches_per_step": launches,
+                     "algorithmic_per_launch": work / max(1.0, launches),
+                     "avg_launch_ms": ms / max(1.0, launches)}
+    dom = max(fams, key=lambda f: fams[f]["ms_per_step"])
+    d = fams[dom]
+    return {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+            "unit": d["unit"], "frac": d["frac"], "traffic": recorded_traffic(dom, workload),
+            "peak_kind": pk_kind if d["bound"] == "hbm" else "derived (SM count x lanes x clock)",
+            "families": fams}
 
 
 def run_ours(args):
@@ -244,18 +314,10 @@ def run_ours(args):
            "h2d_bytes_per_step": B * K * 8, "d2h_bytes_per_step": B * 8 + B * K * 8}
 
     info = ctx.info()
-    pk, pk_kind = peaks()
-    fams = ["forward", "happly", "adjoint"]
-    dom = max(fams, key=lambda f: prof["ms"][f])
-    per_launch_ms = prof["ms"][dom] / max(1, prof["launches"][dom])
-    alg_bytes = algorithmic(info, dom, B, info["n_qubits"], amp_bytes, None)
-    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "peak_kind": pk_kind,
-                "family_ms_per_step": {f: prof["ms"][f] / max(1, prof["calls"]) for f in prof["ms"]},
-                "family_launches_per_step": {f: prof["launches"][f] / max(1, prof["calls"])
-                                             for f in prof["launches"]}}
+    ijab = uc.build_uccsd_list(w["n_orb"], w["n_alpha"], w["n_beta"])
+    workload = f"18q_b{B}_{args.precision}"
+    roof = roofline(prof, B, info["n_qubits"], amp_bytes, ijab, info["n_groups"],
+                    prec == uc.FP32_STATE, workload)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -268,7 +330,7 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MB write)",
                    "fwd_runs": info["n_fwd_runs"], "adj_runs": info["n_adj_runs"],
                    "groups": info["n_groups"], "terms": info["n_terms"]},
-        "roofline": roofline,
+        "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": ck,
@@ -283,6 +345,9 @@ def run_ours(args):
                                           "FP64 oracle, OpenMP)"}
     if rank == 0 and not args.no_scaleup:
         line["scaleup"] = scaleup_26q(uc, local)
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_stream(uc, local, args.serving_requests,
+                                         args.serving_fp64_requests)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -325,6 +390,32 @@ def scaleup_26q(uc, device):
                      "fwd_runs": inf["n_fwd_runs"], "adj_runs": inf["n_adj_runs"]}
         del ctx
         torch.cuda.empty_cache()
+    return out
+
+
+def serving_stream(uc, device, n_req, n_req_fp64):
+    """FMO fragment stream (60% monomers at 8-12 qubits, 40% dimers at 16-18
+    qubits, 40 fixed-step L-BFGS evaluations per solve): capacity of the
+    batched FP32 server (closed loop), latency percentiles at 0.8x that
+    capacity with Poisson arrivals (seed 7), and the one-request-at-a-time
+    FP64 form on the first requests of the same stream."""
+    from paper_2402_17993_gb300.serving import FragmentServer, Request, capacity_rate
+    frags = synth.stream_fragments(n_req, 7)
+    reqs = [Request(d["r"], d["t_unit"], d["n_orb"], d["n_alpha"], d["n_beta"], d["h"], d["eri"],
+                    d["e_core"]) for d in frags]
+    out = {}
+    srv = FragmentServer(precision=uc.FP32_STATE, device=device, max_active=64, n_streams=16)
+    srv.run(reqs[:64])  # warm the context pool and graph paths
+    _, cap = srv.run(reqs)
+    rate = capacity_rate(cap)
+    _, op = srv.run(reqs, rate=0.8 * rate)
+    srv.close()
+    out["batched_fp32"] = {"closed_loop": cap, "open_loop_0.8x": dict(op, rate_req_per_s=0.8 * rate)}
+    one = FragmentServer(precision=uc.FP64, device=device, max_active=1, n_streams=1,
+                         use_graphs=False)
+    _, st1 = one.run(reqs[:n_req_fp64])
+    one.close()
+    out["one_at_a_time_fp64"] = dict(st1, note=f"first {n_req_fp64} requests of the stream")
     return out
 
 

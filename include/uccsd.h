@@ -152,6 +152,20 @@ uccsd_status uccsd_energy_grad_batch(uccsd_ctx *ctx, int B, const double *theta,
                                      int theta_on_device, double *E, double *grad,
                                      void *stream);
 
+/* Capture one B-slot evaluation (as uccsd_energy_grad_batch with device
+ * pointers: theta B*K, E B, grad B*K or NULL) into a CUDA graph owned by the
+ * context, replacing any earlier capture.  The graph keeps the pointers:
+ * each uccsd_replay re-reads theta from the same buffer and rewrites E and
+ * grad.  Nothing runs during the capture itself.  Profiling must be off.
+ * Used by serving loops to replace an evaluation's kernel launches by one
+ * graph launch (the paper's per-evaluation cost, Section 3.1, is dominated
+ * by overheads the GPU cannot hide). */
+uccsd_status uccsd_capture(uccsd_ctx *ctx, int B, const double *theta_dev, double *E_dev,
+                           double *grad_dev, void *stream);
+
+/* Launch the captured graph on `stream`. */
+uccsd_status uccsd_replay(uccsd_ctx *ctx, void *stream);
+
 /* Copy the state vector of slot `slot` after the last uccsd_energy or
  * energies-only batch call to host memory as 2*2^n interleaved (re, im)
  * doubles.  len must be >= 2*2^n.  Synchronises the context's last stream.

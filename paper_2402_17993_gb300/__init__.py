@@ -31,6 +31,7 @@ EXPORTS = [
     "uccsd_set_excitations", "uccsd_set_batch", "uccsd_energy", "uccsd_energy_grad",
     "uccsd_energy_grad_batch", "uccsd_get_state", "uccsd_info", "uccsd_hamiltonian_stats",
     "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile", "uccsd_expectation_noalloc",
+    "uccsd_capture", "uccsd_replay",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -95,6 +96,8 @@ def lib():
                                               ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]
         L.uccsd_expectation_noalloc.argtypes = [vp, vp, vp, vp]
+        L.uccsd_capture.argtypes = [vp, ip, dp, dp, dp, vp]
+        L.uccsd_replay.argtypes = [vp, vp]
         L.uccsd_set_profiling.argtypes = [vp, ip]
         L.uccsd_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
@@ -262,6 +265,17 @@ class Context:
         self._check(self._L.uccsd_energy_grad_batch(self._c, B, theta.data_ptr(), 1, E.data_ptr(),
                                                     gp, _stream_ptr(stream)),
                     "energy_grad_batch(device)")
+
+    def capture(self, theta, E, grad, stream):
+        """Capture one evaluation reading the CUDA tensor theta (B, K) into a
+        graph writing E (B,) and grad (B, K) or None; replay() reruns it."""
+        B = 1 if theta.dim() == 1 else theta.shape[0]
+        gp = None if grad is None else grad.data_ptr()
+        self._check(self._L.uccsd_capture(self._c, B, theta.data_ptr(), E.data_ptr(), gp,
+                                          _stream_ptr(stream)), "capture")
+
+    def replay(self, stream):
+        self._check(self._L.uccsd_replay(self._c, _stream_ptr(stream)), "replay")
 
     def state(self, slot=0):
         N = 1 << self.n_qubits

@@ -446,6 +446,8 @@ uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec, size_t h
 void uccsd_destroy(uccsd_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     for (auto &kv : c->mem) cudaFree(kv.second.first);
     delete c;
@@ -644,6 +646,56 @@ uccsd_status uccsd_energy_grad(uccsd_ctx *c, const double *theta, int on_dev, do
 uccsd_status uccsd_energy_grad_batch(uccsd_ctx *c, int B, const double *theta, int on_dev, double *E,
                                      double *grad, void *stream) {
     return eval(c, B, theta, on_dev, E, grad, stream);
+}
+
+uccsd_status uccsd_capture(uccsd_ctx *c, int B, const double *theta, double *E, double *grad,
+                           void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->profiling) return fail(c, UCCSD_ERR_STATE, "capture needs profiling off");
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
+    if (B < 1 || B > c->B || !E || (!theta && c->K > 0))
+        return fail(c, UCCSD_ERR_ARG, "bad capture arguments");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (!s) return fail(c, UCCSD_ERR_ARG, "capture needs a non-default stream");
+    if (c->graph_exec) {
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+    }
+    if (c->graph) {
+        cudaGraphDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+    const uint64_t l0 = c->launches;
+    uccsd_status st = c->prec ? run_eval<float>(c, B, theta, 1, E, grad, s)
+                              : run_eval<double>(c, B, theta, 1, E, grad, s);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(s, &g);
+    c->graph_kernels = c->launches - l0;  // kernels inside the graph
+    c->launches = l0;
+    if (st) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+    c->graph = g;
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_replay(uccsd_ctx *c, void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->graph_exec) return fail(c, UCCSD_ERR_STATE, "no captured graph");
+    cudaError_t e = cudaGraphLaunch(c->graph_exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    c->launches += c->graph_kernels;
+    return UCCSD_OK;
 }
 
 uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {

@@ -58,6 +58,11 @@ struct uccsd_ctx {
     double diag_unit = 0.0;
     double shift = 0.0;
 
+    // captured evaluation graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_kernels = 0;
+
     // profiling
     bool profiling = false;
     uccsd_profile_t prof{};

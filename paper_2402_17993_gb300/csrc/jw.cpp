@@ -50,6 +50,64 @@ int expand(int len, const int *idx, const bool *dag, double coef, XZTerm *out) {
 
 inline uint64_t key(uint32_t x, uint32_t z) { return (uint64_t(x) << 32) | z; }
 
+// Open-addressing accumulator of X^x Z^z coefficients (linear probing,
+// power-of-two capacity, splitmix64 finaliser as the hash).
+class TermTable {
+  public:
+    explicit TermTable(size_t expected) {
+        size_t cap = 64;
+        while (cap < 2 * expected) cap <<= 1;
+        keys_.assign(cap, kEmpty);
+        vals_.assign(cap, 0.0);
+        mask_ = cap - 1;
+    }
+    void add(uint64_t k, double v) {
+        size_t i = hash(k) & mask_;
+        while (keys_[i] != kEmpty && keys_[i] != k) i = (i + 1) & mask_;
+        if (keys_[i] == kEmpty) {
+            keys_[i] = k;
+            if (++count_ * 2 > keys_.size()) {
+                vals_[i] += v;
+                grow();
+                return;
+            }
+        }
+        vals_[i] += v;
+    }
+    template <typename F>
+    void each(F f) const {
+        for (size_t i = 0; i < keys_.size(); ++i)
+            if (keys_[i] != kEmpty) f(keys_[i], vals_[i]);
+    }
+
+  private:
+    static constexpr uint64_t kEmpty = ~0ull;
+    static uint64_t hash(uint64_t z) {
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+    void grow() {
+        std::vector<uint64_t> k2;
+        std::vector<double> v2;
+        k2.swap(keys_);
+        v2.swap(vals_);
+        keys_.assign(k2.size() * 2, kEmpty);
+        vals_.assign(k2.size() * 2, 0.0);
+        mask_ = keys_.size() - 1;
+        for (size_t i = 0; i < k2.size(); ++i)
+            if (k2[i] != kEmpty) {
+                size_t j = hash(k2[i]) & mask_;
+                while (keys_[j] != kEmpty) j = (j + 1) & mask_;
+                keys_[j] = k2[i];
+                vals_[j] = v2[i];
+            }
+    }
+    std::vector<uint64_t> keys_;
+    std::vector<double> vals_;
+    size_t mask_ = 0, count_ = 0;
+};
+
 // Jordan-Wigner interval parity of a flip mask: bits outside the mask that
 // lie below an odd number of the mask's bits.
 uint32_t interval_mask(uint32_t x) {
@@ -74,11 +132,12 @@ bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e
         *err = "n_orb out of range";
         return false;
     }
-    std::unordered_map<uint64_t, double> acc;
-    acc.reserve(size_t(1) << std::min(22, 2 * n));
+    // distinct keys: 16 Z-patterns per flip mask of 0, 2 or 4 bits
+    const size_t n2 = size_t(n) * (n - 1) / 2, n4 = n2 * (n - 2) * (n - 3) / 12;
+    TermTable acc(16 * (1 + n2 + n4));
     XZTerm buf[16];
     auto add = [&](int cnt) {
-        for (int i = 0; i < cnt; ++i) acc[key(buf[i].x, buf[i].z)] += buf[i].c;
+        for (int i = 0; i < cnt; ++i) acc.add(key(buf[i].x, buf[i].z), buf[i].c);
     };
     // one-body: sum_PQ h_PQ a+_P a_Q  (same spin)
     for (int P = 0; P < n; ++P)
@@ -90,10 +149,12 @@ bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e
             bool dag[2] = {true, false};
             add(expand(2, idx, dag, c, buf));
         }
-    // two-body: 1/2 sum_PQRS <PQ|RS> a+_P a+_Q a_S a_R, <PQ|RS> = (pr|qs)
+    // two-body: 1/2 sum_PQRS <PQ|RS> a+_P a+_Q a_S a_R, <PQ|RS> = (pr|qs).
+    // (P,Q,R,S) and (Q,P,S,R) give the same operator with the same
+    // coefficient (two anticommutations; <QP|SR> = <PQ|RS>), so the sum runs
+    // over P < Q with weight 1 instead of 1/2; P = Q vanishes.
     for (int P = 0; P < n; ++P)
-        for (int Q = 0; Q < n; ++Q) {
-            if (P == Q) continue;
+        for (int Q = P + 1; Q < n; ++Q) {
             for (int R = 0; R < n; ++R) {
                 if ((P & 1) != (R & 1)) continue;
                 for (int S = 0; S < n; ++S) {
@@ -103,20 +164,19 @@ bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e
                     if (g == 0.0) continue;
                     int idx[4] = {P, Q, S, R};
                     bool dag[4] = {true, true, false, false};
-                    add(expand(4, idx, dag, 0.5 * g, buf));
+                    add(expand(4, idx, dag, g, buf));
                 }
             }
         }
-    acc[key(0, 0)] += e_core;
+    acc.add(key(0, 0), e_core);
 
     // merge residue: drop |c| <= 1e-13 max|c| (no approximate truncation)
     double cmax = 0.0;
-    for (auto &kv : acc) cmax = std::max(cmax, std::fabs(kv.second));
+    acc.each([&](uint64_t, double v) { cmax = std::max(cmax, std::fabs(v)); });
     std::vector<XZTerm> terms;
-    terms.reserve(acc.size());
-    for (auto &kv : acc)
-        if (std::fabs(kv.second) > 1e-13 * cmax)
-            terms.push_back(XZTerm{uint32_t(kv.first >> 32), uint32_t(kv.first), kv.second});
+    acc.each([&](uint64_t k, double v) {
+        if (std::fabs(v) > 1e-13 * cmax) terms.push_back(XZTerm{uint32_t(k >> 32), uint32_t(k), v});
+    });
     std::sort(terms.begin(), terms.end(), [](const XZTerm &a, const XZTerm &b) {
         return a.x != b.x ? a.x < b.x : a.z < b.z;
     });

@@ -1,0 +1,246 @@
+"""Continuous-batching server for a stream of FMO fragment VQE solves.
+
+A two-body FMO job (Eq. 1 of the paper) needs one correlation solve per
+monomer and per dimer; the paper ran them as separate jobs (Section 3.1).
+Here requests arrive over time (monomers at 8-12 qubits, dimers at 16-18
+qubits, each with its own integrals) and share one GPU:
+
+* admission: a request enters when a slot is free and its device footprint
+  (Hamiltonian tables, state and adjoint vectors, partial sums) fits the
+  remaining HBM budget; the library enforces the same budget per context;
+* residency: every admitted fragment keeps its context, state vectors and
+  amplitudes on the device until its solve finishes;
+* continuous batching: each tick launches one energy + gradient evaluation
+  for every active fragment, each as a captured CUDA graph on one of several
+  streams so that the evaluations of different fragments overlap on the
+  device; the host then applies one fixed-step L-BFGS update per fragment
+  and admits newly arrived requests into freed slots;
+* each solve runs a fixed number of optimiser steps (one evaluation each);
+  its latency is arrival -> last step done.
+
+Fragments never share device buffers or reductions, so a fragment's result
+does not depend on what else is in flight (checked by the GPU tests).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import FP32_STATE, FP64, Context, build_uccsd_list
+from .vqe import LBFGS
+
+
+@dataclass
+class Request:
+    r: int
+    t_unit: float     # arrival time at unit rate (seconds = t_unit / rate)
+    n_orb: int
+    n_alpha: int
+    n_beta: int
+    h: np.ndarray     # (n_orb, n_orb) one-electron integrals
+    eri: np.ndarray   # (n_orb,)*4 chemist-notation two-electron integrals
+    e_core: float = 0.0
+
+    @property
+    def n_elec(self):
+        return self.n_alpha + self.n_beta
+
+
+@dataclass
+class Result:
+    r: int
+    n_qubits: int
+    t_arrive: float
+    t_admit: float
+    t_done: float
+    energy: float
+    energies: list = field(default_factory=list)
+    theta: np.ndarray | None = None
+
+    @property
+    def latency(self):
+        return self.t_done - self.t_arrive
+
+
+def footprint_bytes(n_orb: int, n_alpha: int, n_beta: int, precision: int) -> int:
+    """Upper estimate of one context's device memory (bytes)."""
+    n = 2 * n_orb
+    N = 1 << n
+    A = 8 if precision == FP32_STATE else 16
+    K = len(build_uccsd_list(n_orb, n_alpha, n_beta))
+    tiles = max(1, N >> 10)
+    tables = 200 * (n_orb ** 4) + (4 << 20)
+    return 2 * N * A + K * tiles * 8 + K * 256 + tables
+
+
+class _Slot:
+    def __init__(self, req, ctx, precision, stream, t_admit, steps):
+        import torch
+        self.req = req
+        self.ctx = ctx
+        self.stream = stream
+        self.K = ctx.K
+        self.t_admit = t_admit
+        self.steps_left = steps
+        self.theta = np.zeros(self.K)
+        self.opt = LBFGS(self.K)
+        dev = torch.device("cuda", ctx.device)
+        self.th_dev = torch.zeros(max(self.K, 1), dtype=torch.float64, device=dev)
+        self.E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.g_dev = torch.zeros(max(self.K, 1), dtype=torch.float64, device=dev)
+        self.th_host = torch.zeros(max(self.K, 1), dtype=torch.float64).pin_memory()
+        self.out_host = torch.zeros(1 + max(self.K, 1), dtype=torch.float64).pin_memory()
+        self.event = torch.cuda.Event()
+        self.energies = []
+        self.used_graph = False
+
+    def launch(self, use_graph: bool):
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.th_host[: self.K] = torch.from_numpy(self.theta)
+            self.th_dev.copy_(self.th_host, non_blocking=True)
+            if use_graph:
+                if not self.used_graph:
+                    self.ctx.capture(self.th_dev[: self.K].view(1, -1), self.E_dev,
+                                     self.g_dev[: self.K].view(1, -1), self.stream)
+                    self.used_graph = True
+                self.ctx.replay(self.stream)
+            else:
+                self.ctx.energy_grad_device(self.th_dev[: self.K].view(1, -1), self.E_dev,
+                                            self.g_dev[: self.K].view(1, -1), self.stream)
+            self.out_host[0:1].copy_(self.E_dev, non_blocking=True)
+            self.out_host[1: 1 + self.K].copy_(self.g_dev[: self.K], non_blocking=True)
+            self.event.record(self.stream)
+
+    def finish_step(self):
+        self.event.synchronize()
+        E = float(self.out_host[0])
+        g = self.out_host[1: 1 + self.K].numpy().copy()
+        self.energies.append(E)
+        self.steps_left -= 1
+        if self.steps_left > 0 and self.K > 0:
+            self.theta = self.opt.step(self.theta, g)
+        return E
+
+
+class FragmentServer:
+    """Serve fragment VQE solves with continuous batching on one GPU.
+
+    precision: FP32_STATE (batched form) or FP64.  max_active = 1 with
+    use_graphs = False gives the plain one-request-at-a-time form."""
+
+    def __init__(self, precision=FP32_STATE, device=0, hbm_budget=8 << 30, max_active=48,
+                 n_streams=16, steps=40, use_graphs=True):
+        import torch
+        self.precision = precision
+        self.device = device
+        self.hbm_budget = hbm_budget
+        self.max_active = max_active
+        self.steps = steps
+        self.use_graphs = use_graphs
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
+        self.pool = {}
+
+    def _context(self, req, used):
+        """A context for the request: a recycled one of the same shape class
+        (its device buffers are reused, nothing is allocated) or a new one
+        whose HBM budget is what the server has left."""
+        key = (req.n_orb, req.n_alpha, req.n_beta)
+        pool = self.pool.get(key)
+        ctx = pool.pop() if pool else Context(self.device, self.precision,
+                                              max(1, self.hbm_budget - used))
+        ctx.set_hamiltonian(req.n_orb, req.h, req.eri, req.e_core)
+        ctx.set_reference(req.n_alpha, req.n_beta)
+        ctx.set_excitations(build_uccsd_list(req.n_orb, req.n_alpha, req.n_beta))
+        return ctx
+
+    def _release(self, req, ctx):
+        self.pool.setdefault((req.n_orb, req.n_alpha, req.n_beta), []).append(ctx)
+
+    def close(self):
+        for lst in self.pool.values():
+            for ctx in lst:
+                ctx.close()
+        self.pool = {}
+
+    def run(self, requests, rate=None, keep_theta=False):
+        """Serve `requests` (arrivals at t_unit / rate seconds; rate None =
+        all at once).  Returns (results, stats)."""
+        reqs = sorted(requests, key=lambda q: q.t_unit)
+        arrive = [0.0 if rate is None else q.t_unit / rate for q in reqs]
+        t0 = time.perf_counter()
+        pending = 0
+        active: list[_Slot] = []
+        results: list[Result] = []
+        used = 0
+        peak_used = 0
+        n_evals = 0
+        active_hist = []
+        next_stream = 0
+        while pending < len(reqs) or active:
+            now = time.perf_counter() - t0
+            # admission: FIFO over arrived requests while slots and HBM allow
+            while (pending < len(reqs) and arrive[pending] <= now
+                   and len(active) < self.max_active):
+                q = reqs[pending]
+                need = footprint_bytes(q.n_orb, q.n_alpha, q.n_beta, self.precision)
+                if used + need > self.hbm_budget and active:
+                    break
+                ctx = self._context(q, used)
+                dev_bytes = ctx.info()["device_bytes"]
+                slot = _Slot(q, ctx, self.precision, self.streams[next_stream % len(self.streams)],
+                             now, self.steps)
+                slot.bytes = dev_bytes
+                slot.t_arrive = arrive[pending]
+                next_stream += 1
+                used += dev_bytes
+                peak_used = max(peak_used, used)
+                active.append(slot)
+                pending += 1
+            if not active:
+                time.sleep(max(0.0, min(arrive[pending] - (time.perf_counter() - t0), 0.01)))
+                continue
+            active_hist.append(len(active))
+            for s in active:
+                s.launch(self.use_graphs)
+            still = []
+            for s in active:
+                s.finish_step()
+                n_evals += 1
+                if s.steps_left <= 0:
+                    t_done = time.perf_counter() - t0
+                    results.append(Result(s.req.r, 2 * s.req.n_orb, s.t_arrive, s.t_admit, t_done,
+                                          s.energies[-1], s.energies,
+                                          s.theta.copy() if keep_theta else None))
+                    used -= s.bytes
+                    self._release(s.req, s.ctx)
+                else:
+                    still.append(s)
+            active = still
+        makespan = time.perf_counter() - t0
+        lat = np.array([r.latency for r in results])
+        stats = {
+            "requests": len(results), "steps_per_solve": self.steps, "evals": n_evals,
+            "makespan_s": makespan, "evals_per_s": n_evals / makespan,
+            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+            "mean_active": float(np.mean(active_hist)) if active_hist else 0.0,
+            "peak_hbm_bytes": int(peak_used),
+            "precision": "fp32" if self.precision == FP32_STATE else "fp64",
+            "max_active": self.max_active, "graphs": self.use_graphs,
+        }
+        return sorted(results, key=lambda r: r.r), stats
+
+
+def fmo2_sum(monomer_E, dimer_E, n_frag):
+    """Two-body FMO total (Eq. 1): sum over dimers minus (N_f - 2) times the
+    sum over monomers."""
+    return float(np.sum(dimer_E) - (n_frag - 2) * np.sum(monomer_E))
+
+
+def capacity_rate(stats) -> float:
+    """Requests per second the server sustained in a closed-loop run."""
+    return stats["requests"] / stats["makespan_s"] if stats["makespan_s"] > 0 else math.inf

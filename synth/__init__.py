@@ -168,6 +168,17 @@ def workload(name: str):
                 n_alpha=w["n_elec"] // 2, n_beta=w["n_elec"] // 2)
 
 
+def stream_fragments(n_req: int, seed: int = 7):
+    """stream_requests() with each fragment's integrals attached
+    (h, eri, e_core, n_alpha, n_beta)."""
+    out = []
+    for d in stream_requests(n_req, seed):
+        h, eri, e_core = make_integrals(d["n_orb"], d["n_chol"], d["seed"])
+        out.append(dict(d, h=h, eri=eri, e_core=e_core, n_alpha=d["n_elec"] // 2,
+                        n_beta=d["n_elec"] - d["n_elec"] // 2))
+    return out
+
+
 def stream_requests(n_req: int, seed: int = 7):
     """Fragment request mix of a two-body FMO job: 60% monomers with
     n_orb in {4,5,6} (8/10/12 qubits; 4/4/6 electrons) and 40% dimers with

@@ -1,0 +1,99 @@
+"""GPU tests of the VQE driver (12-qubit workload) and the fragment server."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def uc():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2402_17993_gb300 as uc
+    uc.lib()
+    return uc
+
+
+def test_vqe_12q_lbfgs_to_gradient_tolerance(uc, oracle_mod):
+    from paper_2402_17993_gb300 import vqe
+    w = synth.workload("12q")
+    e_fci = oracle_mod.fci_energy(6, w["h"], w["eri"], 0.0, 3, 3)
+    res = {}
+    for prec in (uc.FP64, uc.FP32_STATE):
+        ctx = uc.make_context(6, w["h"], w["eri"], 0.0, 3, 3, precision=prec)
+        E, theta, n_eval, gnorm = vqe.minimize(ctx, gtol=1e-6 if prec == uc.FP64 else 1e-3)
+        res[prec] = (E, theta)
+        e_hf = ctx.energy(np.zeros(ctx.K))
+        assert E < e_hf
+        assert E >= e_fci - 1e-9
+        if prec == uc.FP64:
+            assert gnorm < 1e-6
+            # the converged point: the oracle agrees on energy and gradient
+            E0, g0 = oracle_mod.energy_grad(6, w["h"], w["eri"], 0.0, 3, 3,
+                                            oracle_mod.excitations(6, 3, 3), theta)
+            assert abs(E0 - E) < 1e-10 and np.linalg.norm(g0) < 1e-6
+    assert abs(res[uc.FP64][0] - res[uc.FP32_STATE][0]) < 1e-4
+
+
+def _requests(n, seed=7):
+    from paper_2402_17993_gb300.serving import Request
+    return [Request(d["r"], d["t_unit"], d["n_orb"], d["n_alpha"], d["n_beta"], d["h"], d["eri"],
+                    d["e_core"]) for d in synth.stream_fragments(n, seed)]
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_server_result_is_the_same_alone_and_in_the_mix(uc, prec):
+    from paper_2402_17993_gb300.serving import FragmentServer
+    reqs = _requests(12)
+    srv = FragmentServer(precision=prec, steps=6, max_active=12)
+    mixed, stats = srv.run(reqs, rate=None, keep_theta=True)
+    assert stats["requests"] == 12 and stats["evals"] == 72
+    assert stats["mean_active"] > 1.5
+    for q, m in zip(reqs, mixed):
+        alone, _ = srv.run([q], rate=None, keep_theta=True)
+        a = alone[0]
+        assert a.r == m.r
+        assert a.energies == m.energies          # bitwise: no cross-fragment coupling
+        assert np.array_equal(a.theta, m.theta)
+    srv.close()
+    # energies decrease from the HF value over the fixed L-BFGS steps
+    assert all(r.energies[-1] <= r.energies[0] + 1e-9 for r in mixed)
+
+
+def test_server_first_step_energy_matches_oracle_hf(uc, oracle_mod):
+    from paper_2402_17993_gb300.serving import FragmentServer
+    reqs = _requests(6, seed=11)
+    srv = FragmentServer(precision=uc.FP64, steps=1, max_active=6)
+    res, _ = srv.run(reqs)
+    for q, r in zip(reqs, res):
+        ex = oracle_mod.excitations(q.n_orb, q.n_alpha, q.n_beta)
+        e0 = oracle_mod.energy_grad(q.n_orb, q.h, q.eri, q.e_core, q.n_alpha, q.n_beta, ex,
+                                    np.zeros(len(ex)), grad=False)[0]
+        assert abs(r.energies[0] - e0) < 1e-10
+    srv.close()
+
+
+def test_server_admission_respects_hbm_budget(uc):
+    from paper_2402_17993_gb300.serving import FragmentServer, footprint_bytes
+    reqs = _requests(10)
+    big = max(footprint_bytes(q.n_orb, q.n_alpha, q.n_beta, 1) for q in reqs)
+    srv = FragmentServer(precision=1, steps=3, max_active=10, hbm_budget=2 * big)
+    res, stats = srv.run(reqs)
+    assert stats["requests"] == 10
+    assert stats["peak_hbm_bytes"] <= 2 * big
+    assert stats["mean_active"] <= 2.0 + 1e-9
+    srv.close()
+
+
+def test_server_open_loop_latencies(uc):
+    from paper_2402_17993_gb300.serving import FragmentServer
+    reqs = _requests(16)
+    srv = FragmentServer(precision=1, steps=4, max_active=16)
+    res, stats = srv.run(reqs, rate=200.0)
+    assert stats["requests"] == 16
+    assert 0 < stats["p50_latency_ms"] <= stats["p99_latency_ms"]
+    assert all(r.t_done >= r.t_arrive for r in res)
+    srv.close()
