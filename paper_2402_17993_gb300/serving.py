@@ -175,8 +175,10 @@ class FragmentServer:
         pending = 0
         active: list[_Slot] = []
         results: list[Result] = []
-        used = 0
+        used = 0          # reserved by admission (upper estimates)
         peak_used = 0
+        dev_used = 0      # device bytes the active contexts report
+        peak_dev = 0
         n_evals = 0
         active_hist = []
         next_stream = 0
@@ -190,14 +192,16 @@ class FragmentServer:
                 if used + need > self.hbm_budget and active:
                     break
                 ctx = self._context(q, used)
-                dev_bytes = ctx.info()["device_bytes"]
                 slot = _Slot(q, ctx, self.precision, self.streams[next_stream % len(self.streams)],
                              now, self.steps)
-                slot.bytes = dev_bytes
+                slot.reserved = need
+                slot.dev_bytes = ctx.info()["device_bytes"]
                 slot.t_arrive = arrive[pending]
                 next_stream += 1
-                used += dev_bytes
+                used += need
+                dev_used += slot.dev_bytes
                 peak_used = max(peak_used, used)
+                peak_dev = max(peak_dev, dev_used)
                 active.append(slot)
                 pending += 1
             if not active:
@@ -215,7 +219,8 @@ class FragmentServer:
                     results.append(Result(s.req.r, 2 * s.req.n_orb, s.t_arrive, s.t_admit, t_done,
                                           s.energies[-1], s.energies,
                                           s.theta.copy() if keep_theta else None))
-                    used -= s.bytes
+                    used -= s.reserved
+                    dev_used -= s.dev_bytes
                     self._release(s.req, s.ctx)
                 else:
                     still.append(s)
@@ -228,7 +233,8 @@ class FragmentServer:
             "p50_latency_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
             "p99_latency_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
             "mean_active": float(np.mean(active_hist)) if active_hist else 0.0,
-            "peak_hbm_bytes": int(peak_used),
+            "peak_hbm_reserved_bytes": int(peak_used),
+            "peak_hbm_device_bytes": int(peak_dev),
             "precision": "fp32" if self.precision == FP32_STATE else "fp64",
             "max_active": self.max_active, "graphs": self.use_graphs,
         }
