@@ -62,6 +62,26 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(x: float, world: int) -> float:
+    """Max of x over the ranks (the job's timed region ends with its slowest
+    rank).  Uses the process group's backend: NCCL on GPUs, gloo on CPUs."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Weak scaling: every rank evaluates its own units (no data-path
+    collective); the job rate is all ranks' units over the slowest rank's
+    time."""
+    return world * units_per_rank / (max_ms / 1e3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -294,11 +314,8 @@ def run_ours(args):
     prof = ctx.profile()
     ctx.set_profiling(False)
     launches = ctx.info()["launches"] - launches0
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * B * args.steps / (total_ms / 1e3)
+    total_ms = reduce_max(total_ms, world)
+    value = whole_job_rate(B * args.steps, world, total_ms)
 
     # end to end through the C ABI with pinned host buffers
     th_pin = torch.tensor(th_host, dtype=torch.float64).pin_memory()
