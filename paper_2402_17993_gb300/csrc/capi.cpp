@@ -19,60 +19,84 @@ using namespace uccsd;
 namespace {
 
 
+int binom_int(int m, int k) {
+    if (k < 0 || k > m) return 0;
+    long long r = 1;
+    for (int i = 1; i <= k; ++i) r = r * (m - k + i) / i;
+    return int(r);
+}
+
+int pair_idx(int p, int q) { return q * (q - 1) / 2 + p; }  // p < q
+
 template <typename R>
 struct HamTables {
-    std::vector<GroupT<R>> groups;
-    std::vector<int32_t> seg_begin;
-    std::vector<uint32_t> seg_d;
+    std::vector<MixT<R>> mix;
+    std::vector<SglT<R>> s1a, s1b;
+    std::vector<DblT<R>> d2a, d2b;
     std::vector<R> spec;
 };
 
+// Sort the compiled X-mask groups into the class tables of the H-apply.
+// Returns false for a group outside the spin-conserving classes.
 template <typename R>
-HamTables<R> make_tables(const CompiledH &H, int LH) {
-    HamTables<R> T;
-    std::vector<std::pair<uint32_t, int>> order;  // (sort key, group index)
-    for (size_t g = 0; g < H.groups.size(); ++g) {
-        uint32_t d = H.groups[g].xmask >> LH;
-        order.push_back({d == 0 ? 0xFFFFFFFFu : d, int(g)});
-    }
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<uint32_t, int> &a, const std::pair<uint32_t, int> &b) {
-                         return a.first < b.first;
-                     });
-    uint32_t cur = 0;
-    bool open = false;
-    for (auto &kv : order) {
-        const GroupT<double> &s = H.groups[kv.second];
-        if (!open || kv.first != cur) {
-            T.seg_begin.push_back(int(T.groups.size()));
-            T.seg_d.push_back(kv.first == 0xFFFFFFFFu ? 0u : kv.first);
-            cur = kv.first;
-            open = true;
+bool make_tables(const CompiledH &H, int n_orb, HamTables<R> *T, std::string *err) {
+    const int np = n_orb * (n_orb - 1) / 2;
+    const int nq = binom_int(n_orb, 4);
+    T->mix.assign(size_t(std::max(np, 1)) * std::max(np, 1), MixT<R>{});
+    T->s1a.assign(std::max(np, 1), SglT<R>{});
+    T->s1b.assign(std::max(np, 1), SglT<R>{});
+    T->d2a.assign(std::max(nq, 1), DblT<R>{});
+    T->d2b.assign(std::max(nq, 1), DblT<R>{});
+    for (auto &v : T->s1a) v.spec = -1;
+    for (auto &v : T->s1b) v.spec = -1;
+    auto orbs = [](uint32_t m, int *o) {
+        int k = 0;
+        for (int t = 0; t < 32; ++t)
+            if ((m >> t) & 1u) o[k++] = t;
+    };
+    for (const GroupT<double> &g : H.groups) {
+        uint32_t xa = 0, xb = 0, ja = 0, jb = 0;
+        for (int k = 0; k < g.nb; ++k) ((g.pos[k] & 1) ? xb : xa) |= 1u << (g.pos[k] >> 1);
+        for (int q = 0; q < 2 * n_orb; ++q)
+            if ((g.jmask >> q) & 1u) ((q & 1) ? jb : ja) |= 1u << (q >> 1);
+        const uint32_t j = ja | (jb << 16);
+        const int na = __builtin_popcount(xa), nbv = __builtin_popcount(xb);
+        int o[4];
+        if (g.nb == 2 && (na == 2 || nbv == 2)) {
+            orbs(na ? xa : xb, o);
+            SglT<R> &S = (na ? T->s1a : T->s1b)[pair_idx(o[0], o[1])];
+            S.lut[0] = R(g.lut[1]);  // source occupies the lower orbital
+            S.lut[1] = R(g.lut[2]);  // source occupies the higher orbital
+            S.j = j;
+            S.spec = g.spec;
+        } else if (g.nb == 4 && (na == 4 || nbv == 4)) {
+            orbs(na ? xa : xb, o);
+            DblT<R> &D = (na ? T->d2a : T->d2b)[binom_int(o[3], 4) + binom_int(o[2], 3) +
+                                                binom_int(o[1], 2) + o[0]];
+            for (int p = 0; p < 16; ++p) D.lut[p] = R(g.lut[p]);
+            D.j = j;
+        } else if (g.nb == 4 && na == 2 && nbv == 2) {
+            int oa[4], ob[4];
+            orbs(xa, oa);
+            orbs(xb, ob);
+            MixT<R> &M = T->mix[size_t(pair_idx(oa[0], oa[1])) * np + pair_idx(ob[0], ob[1])];
+            for (int asel = 0; asel < 2; ++asel)
+                for (int bsel = 0; bsel < 2; ++bsel) {
+                    const int qa = 2 * oa[asel], qb = 2 * ob[bsel] + 1;  // occupied by the source
+                    int pat = 0;
+                    for (int k = 0; k < 4; ++k)
+                        if (g.pos[k] == qa || g.pos[k] == qb) pat |= 1 << k;
+                    M.lut[asel + 2 * bsel] = R(g.lut[pat]);
+                }
+            M.j = j;
+        } else {
+            *err = "X-mask group outside the spin-conserving classes";
+            return false;
         }
-        GroupT<R> g{};
-        g.xmask = s.xmask;
-        g.jmask = s.jmask;
-        g.nb = s.nb;
-        g.spec = s.spec;
-        g.active = s.active;
-        for (int k = 0; k < 4; ++k) g.pos[k] = s.pos[k];
-        g.mla = g.mlb = 0;
-        for (int q = 0; q < LH; ++q)
-            if ((s.xmask >> q) & 1u) ((q & 1) ? g.mlb : g.mla) |= 1u << (q >> 1);
-        g.ha = __builtin_popcount(s.xmask & 0x55555555u) / 2;
-        g.hb = __builtin_popcount(s.xmask & 0xAAAAAAAAu) / 2;
-        for (int p = 0; p < 16; ++p) g.lut[p] = R(s.lut[p]);
-        T.groups.push_back(g);
     }
-    // the own-tile (d = 0) segment is always last, possibly empty
-    if (T.seg_d.empty() || cur != 0xFFFFFFFFu) {
-        T.seg_begin.push_back(int(T.groups.size()));
-        T.seg_d.push_back(0u);
-    }
-    T.seg_begin.push_back(int(T.groups.size()));
-    for (double v : H.spec) T.spec.push_back(R(v));
-    if (T.spec.empty()) T.spec.push_back(R(0));
-    return T;
+    for (double v : H.spec) T->spec.push_back(R(v));
+    if (T->spec.empty()) T->spec.push_back(R(0));
+    return true;
 }
 
 }  // namespace
@@ -165,24 +189,29 @@ long long shifted_q0(const uccsd_ctx *c) {
 
 template <typename R>
 uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
-    HamTables<R> T = make_tables<R>(c->H, c->LH);
+    HamTables<R> T;
+    std::string err;
+    if (!make_tables<R>(c->H, c->n_orb, &T, &err)) return fail(c, UCCSD_ERR_ARG, err);
     std::string t(tag);
-    GroupT<R> *g;
-    int32_t *sb;
-    uint32_t *sd;
+    MixT<R> *mx;
+    SglT<R> *sa, *sb;
+    DblT<R> *da, *db;
     R *sp;
     long long *qa, *qb;
     uccsd_status st;
-    if ((st = upload(c, t + "groups", T.groups, &g))) return st;
-    if ((st = upload(c, t + "seg_begin", T.seg_begin, &sb))) return st;
-    if ((st = upload(c, t + "seg_d", T.seg_d, &sd))) return st;
+    if ((st = upload(c, t + "mix", T.mix, &mx))) return st;
+    if ((st = upload(c, t + "s1a", T.s1a, &sa))) return st;
+    if ((st = upload(c, t + "s1b", T.s1b, &sb))) return st;
+    if ((st = upload(c, t + "d2a", T.d2a, &da))) return st;
+    if ((st = upload(c, t + "d2b", T.d2b, &db))) return st;
     if ((st = upload(c, t + "spec", T.spec, &sp))) return st;
     if ((st = upload(c, "diag_qa", c->diag_qa, &qa))) return st;
     if ((st = upload(c, "diag_qb", c->diag_qb, &qb))) return st;
-    dh->groups = g;
-    dh->seg_begin = sb;
-    dh->seg_d = sd;
-    dh->n_seg = int(T.seg_d.size());
+    dh->mix = mx;
+    dh->s1a = sa;
+    dh->s1b = sb;
+    dh->d2a = da;
+    dh->d2b = db;
     dh->spec = sp;
     dh->diag_qa = qa;
     dh->diag_qb = qb;
@@ -190,12 +219,14 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     dh->diag_unit = c->diag_unit;
     dh->has_diag = c->H.has_diag ? 1 : 0;
     dh->n = c->n;
+    dh->n_orb = c->n_orb;
+    dh->n_pairs = c->n_orb * (c->n_orb - 1) / 2;
     return UCCSD_OK;
 }
 
-// Tables of the compact H-apply tiles and the sweeps: combinatorial rank
-// tables (shared) and the deposits of low alpha / beta strings of the
-// H-apply tile (alpha string bit k = qubit 2k, beta string bit k = qubit 2k+1).
+// Combinatorial rank tables (shared by the sweeps and the H-apply) and the
+// string -> global bit deposits of the H-apply's row/column layout (alpha
+// string bit t = qubit 2t, beta string bit t = qubit 2t + 1).
 uccsd_status upload_tile_tables(uccsd_ctx *c) {
     std::vector<uint16_t> combos, ranks;
     std::vector<int32_t> coffs;
@@ -205,31 +236,53 @@ uccsd_status upload_tile_tables(uccsd_ctx *c) {
     uint32_t *p4;
     uccsd_status st;
     if ((st = upload(c, "combos", combos, &p5))) return st;
-    c->hsec.combos = p5;
+    c->comb_combos = p5;
     if ((st = upload(c, "ranks", ranks, &p5))) return st;
-    c->hsec.ranks = p5;
+    c->comb_ranks = p5;
     if ((st = upload(c, "comb_offs", coffs, &p2))) return st;
-    c->hsec.comb_offs = p2;
-    const int half = c->LH / 2;
-    std::vector<uint32_t> spread(size_t(2) << half);
-    for (uint32_t s = 0; s < (1u << half); ++s) {
+    c->comb_offs = p2;
+    c->comb_offs_host = coffs;
+    const int no = c->n_orb;
+    std::vector<uint32_t> spread(size_t(2) << no);
+    for (uint32_t s = 0; s < (1u << no); ++s) {
         uint32_t a = 0, b = 0;
-        for (int k = 0; k < half; ++k)
+        for (int k = 0; k < no; ++k)
             if ((s >> k) & 1u) {
                 a |= 1u << (2 * k);
                 b |= 1u << (2 * k + 1);
             }
         spread[s] = a;
-        spread[(size_t(1) << half) + s] = b;
+        spread[(size_t(1) << no) + s] = b;
     }
     if ((st = upload(c, "hspread", spread, &p4))) return st;
-    c->hsec.spread = p4;
+    c->hsec.aspread = p4;
+    c->hsec.bspread = p4 + (size_t(1) << no);
+    std::vector<int32_t> bn(16 * 5);
+    for (int t = 0; t < 16; ++t)
+        for (int k = 0; k <= 4; ++k) bn[t * 5 + k] = binom_int(t, k);
+    if ((st = upload(c, "binom", bn, &p2))) return st;
+    c->hsec.binom = p2;
+    c->hsec.brank = c->comb_ranks + ((size_t(1) << no) - 1);
     return UCCSD_OK;
+}
+
+// Row/column layout of the sector for the reference's electron counts.
+void set_row_layout(uccsd_ctx *c) {
+    const int no = c->n_orb;
+    const size_t base = (size_t(1) << no) - 1;
+    c->hsec.astr = c->comb_combos + base + c->comb_offs_host[no * 17 + c->n_alpha];
+    c->hsec.bstr = c->comb_combos + base + c->comb_offs_host[no * 17 + c->n_beta];
+    c->hsec.Da = binom_int(no, c->n_alpha);
+    c->hsec.Db = binom_int(no, c->n_beta);
+    c->hsec.colblock = std::min(c->hsec.Db, kHColBlock);
+    c->hsec.ncb = (c->hsec.Db + c->hsec.colblock - 1) / c->hsec.colblock;
+    c->hsec.n_alpha = c->n_alpha;
+    c->hsec.n_beta = c->n_beta;
 }
 
 size_t state_bytes(const uccsd_ctx *c) { return size_t(1) << c->n; }
 size_t amp_bytes(const uccsd_ctx *c) { return c->prec ? 8 : 16; }
-int n_tiles_h(const uccsd_ctx *c) { return 1 << (c->n - c->LH); }
+int n_tiles_h(const uccsd_ctx *c) { return c->hsec.Da * c->hsec.ncb; }
 int n_tiles_a(const uccsd_ctx *c) { return c->adj.max_tiles; }
 
 // Per-slot buffers sized for c->B slots.
@@ -482,7 +535,7 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, con
     c->n_orb = n_orb;
     c->n = 2 * n_orb;
     c->H = std::move(H);
-    c->LH = std::min(kHL, c->n);
+    c->LH = 0;
     c->have_h = c->have_ref = c->have_exc = false;
     c->state_valid = false;
     c->shift = 0.0;
@@ -513,10 +566,7 @@ uccsd_status uccsd_set_reference(uccsd_ctx *c, int n_alpha, int n_beta) {
     c->shift = c->H.has_diag ? sft : c->H.c0;
     c->hf32.diag_q0 = shifted_q0(c);
     c->hf64.diag_q0 = shifted_q0(c);
-    c->hsec.n_alpha = n_alpha;
-    c->hsec.n_beta = n_beta;
-    c->hsec.max_entries = int(max_tile_entries(c->n, n_alpha, n_beta,
-                                               (c->LH >= 32) ? 0xFFFFFFFFu : ((1u << c->LH) - 1u)));
+    set_row_layout(c);
     c->have_ref = true;
     c->have_exc = false;
     c->state_valid = false;
@@ -598,9 +648,9 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     if ((st = upload(c, "op_tiles", c->adj.op_tiles, &p2))) return st;
     // combinatorial rank tables (uploaded with the Hamiltonian)
     SweepArgs base{};
-    base.combos = c->hsec.combos;
-    base.ranks = c->hsec.ranks;
-    base.comb_offs = c->hsec.comb_offs;
+    base.combos = c->comb_combos;
+    base.ranks = c->comb_ranks;
+    base.comb_offs = c->comb_offs;
     for (int q = 0; q < n; q += 2) base.amask |= 1u << q;
     base.n_alpha = c->n_alpha;
     base.n_beta = c->n_beta;

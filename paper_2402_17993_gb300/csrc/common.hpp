@@ -29,6 +29,37 @@ struct GroupT {
     R lut[16];
 };
 
+// H-apply tables by group class.  Orbital strings: bit t of an alpha
+// string is qubit 2t, bit t of a beta string is qubit 2t+1.  Pair index of
+// orbitals p < q: q(q-1)/2 + p; quad index of p < q < r < s:
+// C(s,4) + C(r,3) + C(q,2) + p.  j packs the Jordan-Wigner interval mask of
+// the group as (alpha string) | (beta string) << 16.  Absent groups have
+// zero tables.
+//
+// Mixed group (alpha pair, beta pair): lut[asel + 2 bsel] is f_g at the
+// source y that occupies the higher (asel = 1) or lower alpha orbital of the
+// pair and the higher (bsel = 1) or lower beta orbital.
+template <typename R>
+struct MixT {
+    R lut[4];
+    uint32_t j;
+};
+// Same-spin single (pair): lut[sel] at the source occupying the higher
+// (sel = 1) or lower orbital; spectator rows start at spec (rows of 4,
+// pattern 1 = lower occupied, 2 = higher occupied).
+template <typename R>
+struct SglT {
+    R lut[2];
+    uint32_t j;
+    int32_t spec;
+};
+// Same-spin double (quad): lut[pattern of the source over the sorted quad].
+template <typename R>
+struct DblT {
+    R lut[16];
+    uint32_t j;
+};
+
 // A shared-memory pass over compact sector tiles.  The factors
 // [op_begin, op_end) of the schedule flip only bits inside the tile bit set
 // `tmask`, so every tile (fixed values of the other bits) evolves on its

@@ -12,8 +12,9 @@
 #include "plan.hpp"
 
 namespace uccsd {
-// Tile bits of the H-apply (low bits of the amplitude index).
-inline constexpr int kHL = 14;
+// Columns (beta strings) per H-apply CTA.
+inline constexpr int kHColBlock = 2048;
+inline constexpr int kHL = 0;  // unused by the row layout
 // Shared memory budget of one compact sweep tile (forward: one vector,
 // adjoint: phi and lambda), bytes.
 inline constexpr size_t kSweepBudget = 200 * 1024;
@@ -51,6 +52,10 @@ struct uccsd_ctx {
     uccsd::DevHam<float> hf32;
     uccsd::DevHam<double> hf64;
     uccsd::HSector hsec;
+    // combinatorial rank tables (shared by the sweeps and the H-apply)
+    const uint16_t *comb_combos = nullptr, *comb_ranks = nullptr;
+    const int32_t *comb_offs = nullptr;
+    std::vector<int32_t> comb_offs_host;
 
     // diagonal in fixed point; energy shift (the reference determinant's
     // diagonal energy) applied to H on the device and added back in FP64

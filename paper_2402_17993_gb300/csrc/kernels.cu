@@ -91,166 +91,252 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
 }
 
 // ---------------------------------------------------------------------------
-// Hamiltonian action and energy (Section 2.3): sigma = (H - shift) psi over
-// X-mask groups.
+// Hamiltonian action and energy (Section 2.3): sigma = (H - shift) psi,
+// accumulated over the X-mask groups of the Jordan-Wigner Hamiltonian.
 //
-// H conserves N_alpha and N_beta and psi vanishes outside the (n_alpha,
-// n_beta) sector, so only sector amplitudes are read or produced.  A CTA
-// owns one compact output tile: the sector amplitudes with fixed high bits
-// h above the low LH bits, stored as a [C(LH/2, a)] x [C(LH/2, b)] array
-// indexed by the ranks of their low alpha / beta strings (a, b = electrons
-// the sector leaves for the low bits).  Each thread keeps up to kHEPT
-// outputs in registers.  Groups are sorted into segments by the high part d
-// of their X-mask; for each segment the compact source tile h ^ d is
-// gathered into shared memory and every group of the segment adds
-//   f_g(y) psi_y,  y = x ^ xmask_g,
-// for the outputs whose flip pattern conserves the electron counts (then y
-// lies in the source tile).  The own tile (d = 0) is the last segment, so
-// psi_x is resident for the diagonal and the FP64 partials
-// sum Re(conj(psi_x) sigma_x) and sum |psi_x|^2.  Entries of sigma outside
-// the sector are never written (they stay zero).
+// H conserves N_alpha and N_beta, and psi vanishes outside the (n_alpha,
+// n_beta) sector, so every output and every source is a sector amplitude,
+// written x = (alpha string, beta string).  A CTA owns a block of columns
+// (beta strings, one per lane and slot) of one row (alpha string R).  For
+// output x the groups with a nonzero contribution are exactly those whose
+// flip connects x to a sector source y = x ^ xmask_g, so the CTA visits them
+// by class instead of testing all groups:
+//   - the diagonal group (occupation quadratic form, 64-bit fixed point);
+//   - beta-only groups from the own row: each lane enumerates the beta
+//     single (j -> b) and double (j1 j2 -> b1 b2) excitations of its column;
+//   - for every alpha single excitation p -> q of R the source row
+//     R ^ {p, q} is gathered into shared memory; the alpha-only pair group
+//     acts column-wise and the mixed groups (alpha pair, beta pair) through
+//     each lane's beta single excitations;
+//   - for every alpha double excitation of R the alpha-only quad group reads
+//     the source amplitude of the same column directly.
+// Every lane runs the same loop trip counts (its column has n_beta
+// electrons), so the warps do not diverge.  The contribution of group g is
+// f_g(y) psi_y with f_g(y) = (-1)^{popc(y & J_g)} (LUT_g[pattern of y] +
+// sum of the spectator rows of y's other occupied orbitals).  FP32
+// accumulators are Kahan-compensated.  The FP64 partials sum Re(conj(psi_x)
+// sigma_x) and sum |psi_x|^2 feed the energy; sigma outside the sector is
+// never written (it stays zero).
 // ---------------------------------------------------------------------------
-constexpr int kHThreadsV = 256;
-constexpr int kHEPT = 5;  // outputs per thread: 1280 >= C(7,3)^2, the largest 14-bit tile
+constexpr int kRowThreads = 256;
 
-struct HTileView {
-    int a, b, Da, Db;
-    const uint16_t *ca, *cb;  // low alpha / beta strings of the tile's class
-};
-
-__device__ __forceinline__ bool htile(const HSector &hs, int half, uint32_t hi, HTileView *v) {
-    v->a = hs.n_alpha - __popc(hi & 0x55555555u);
-    v->b = hs.n_beta - __popc(hi & 0xAAAAAAAAu);
-    if (v->a < 0 || v->a > half || v->b < 0 || v->b > half) return false;
-    const int32_t *o = hs.comb_offs + half * 17;
-    v->Da = o[v->a + 1] - o[v->a];
-    v->Db = o[v->b + 1] - o[v->b];
-    v->ca = hs.combos + ((1 << half) - 1) + o[v->a];
-    v->cb = hs.combos + ((1 << half) - 1) + o[v->b];
-    return true;
+__device__ __forceinline__ int pair_index(int p, int q) {  // p < q
+    return (q * (q - 1) >> 1) + p;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kHThreadsV) happly_kernel(const V2<R> *__restrict__ psi,
-                                                            V2<R> *__restrict__ sig, size_t N,
-                                                            int LH, DevHam<R> H, HSector hs,
-                                                            double *__restrict__ Epart,
-                                                            int store_sigma) {
+__device__ __forceinline__ int jw_parity(uint32_t ya, uint32_t yb, uint32_t j) {
+    return (__popc(ya & (j & 0xFFFFu)) + __popc(yb & (j >> 16))) & 1;
+}
+
+template <typename R, int EPT>
+__global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__restrict__ psi,
+                                                             V2<R> *__restrict__ sig, size_t N,
+                                                             DevHam<R> H, HSector hs,
+                                                             double *__restrict__ Epart,
+                                                             int store_sigma) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
+    V2<R> *src = reinterpret_cast<V2<R> *>(smem_raw);                  // one source row
+    uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
     __shared__ double red[32];
-    __shared__ uint32_t spa[1 << 8], spb[1 << 8];  // half-width string -> low bits
-    __shared__ uint16_t rk[1 << 8];                 // rank of a half-width string
+    __shared__ int nb4[16 * 5];
     const int b = blockIdx.y;
-    const uint32_t h = blockIdx.x;
-    const int half = LH >> 1;
-    const V2<R> *src = psi + (size_t)b * N;
-    for (int t = threadIdx.x; t < (1 << half); t += blockDim.x) {
-        spa[t] = hs.spread[t];
-        spb[t] = hs.spread[(1 << half) + t];
-        rk[t] = hs.ranks[((1 << half) - 1) + t];
+    const int row = blockIdx.x / hs.ncb;
+    const int cb = blockIdx.x - row * hs.ncb;
+    const int n_orb = H.n_orb;
+    const uint32_t full = (1u << n_orb) - 1u;
+    const uint32_t sR = hs.astr[row];
+    const V2<R> *st = psi + (size_t)b * N;
+    for (int t = threadIdx.x; t < (1 << n_orb); t += blockDim.x) brk[t] = hs.brank[t];
+    for (int t = threadIdx.x; t < 16 * 5; t += blockDim.x) nb4[t] = hs.binom[t];
+    {
+        const uint32_t xR = hs.aspread[sR];
+        for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
+            src[c] = st[xR | hs.bspread[hs.bstr[c]]];
     }
     __syncthreads();
-    HTileView ov;
+
+    int cix[EPT];
+    uint32_t sc[EPT];
+    V2<R> acc[EPT], comp[EPT], own[EPT];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        const int loc = threadIdx.x + i * blockDim.x;
+        const int c = cb * hs.colblock + loc;
+        cix[i] = (loc < hs.colblock && c < hs.Db) ? c : -1;
+        sc[i] = cix[i] >= 0 ? hs.bstr[c] : 0u;
+        own[i] = cix[i] >= 0 ? src[c] : V2<R>{(R)0, (R)0};
+        acc[i] = V2<R>{(R)0, (R)0};
+        comp[i] = V2<R>{(R)0, (R)0};
+    }
+
+    // ---- own row: diagonal, beta singles, beta doubles ----
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+        if (cix[i] < 0) continue;
+        const uint32_t cb_str = sc[i];
+        if (H.has_diag) {
+            long long q = H.diag_q0;
+            uint32_t o1 = hs.aspread[sR] | hs.bspread[cb_str];
+            const int n = H.n;
+            while (o1) {
+                const int a = __ffs(o1) - 1;
+                o1 &= o1 - 1u;
+                q += H.diag_qa[a];
+                uint32_t o2 = o1;
+                while (o2) {
+                    const int r = __ffs(o2) - 1;
+                    o2 &= o2 - 1u;
+                    q += H.diag_qb[a * n + r];
+                }
+            }
+            accumulate<R>(acc[i], comp[i], (R)q * (R)H.diag_unit, own[i]);
+        }
+        const uint32_t vir = full & ~cb_str;
+        for (uint32_t o = cb_str; o; o &= o - 1u) {
+            const int j = __ffs(o) - 1;
+            for (uint32_t v = vir; v; v &= v - 1u) {
+                const int bb = __ffs(v) - 1;
+                const int lo = min(j, bb), hi = max(j, bb);
+                const SglT<R> &S = H.s1b[pair_index(lo, hi)];
+                const int sel = bb > j;
+                const uint32_t yb = cb_str ^ (1u << j) ^ (1u << bb);
+                R val = S.lut[sel];
+                if (S.spec >= 0) {
+                    const int pat = sel ? 2 : 1;
+                    for (uint32_t w = sR; w; w &= w - 1u)
+                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + pat];
+                    for (uint32_t w = yb & ~(1u << bb); w; w &= w - 1u)
+                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
+                }
+                if (jw_parity(sR, yb, S.j)) val = -val;
+                accumulate<R>(acc[i], comp[i], val, src[brk[yb]]);
+            }
+        }
+        for (uint32_t o1 = cb_str; o1; o1 &= o1 - 1u) {
+            const int j1 = __ffs(o1) - 1;
+            for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
+                const int j2 = __ffs(o2) - 1;
+                for (uint32_t v1 = vir; v1; v1 &= v1 - 1u) {
+                    const int b1 = __ffs(v1) - 1;
+                    for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
+                        const int b2 = __ffs(v2) - 1;
+                        // sorted quad and the ranks of b1 < b2 in it
+                        const uint32_t m = (1u << j1) | (1u << j2) | (1u << b1) | (1u << b2);
+                        uint32_t t = m;
+                        const int q0 = __ffs(t) - 1; t &= t - 1u;
+                        const int q1 = __ffs(t) - 1; t &= t - 1u;
+                        const int q2 = __ffs(t) - 1; t &= t - 1u;
+                        const int q3 = __ffs(t) - 1;
+                        const int qi = nb4[q3 * 5 + 4] + nb4[q2 * 5 + 3] + nb4[q1 * 5 + 2] + q0;
+                        const int rb1 = __popc(m & ((1u << b1) - 1u));
+                        const int rb2 = __popc(m & ((1u << b2) - 1u));
+                        const DblT<R> &Dq = H.d2b[qi];
+                        const uint32_t yb = cb_str ^ m;
+                        R val = Dq.lut[(1 << rb1) | (1 << rb2)];
+                        if (jw_parity(sR, yb, Dq.j)) val = -val;
+                        accumulate<R>(acc[i], comp[i], val, src[brk[yb]]);
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- alpha singles: source row R ^ {p, q} ----
+    const uint32_t virA = full & ~sR;
+    for (uint32_t op = sR; op; op &= op - 1u) {
+        const int p = __ffs(op) - 1;
+        for (uint32_t vq = virA; vq; vq &= vq - 1u) {
+            const int q = __ffs(vq) - 1;
+            const uint32_t sRp = sR ^ (1u << p) ^ (1u << q);
+            const uint32_t xRp = hs.aspread[sRp];
+            __syncthreads();
+            for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
+                src[c] = st[xRp | hs.bspread[hs.bstr[c]]];
+            __syncthreads();
+            const int pa = pair_index(min(p, q), max(p, q));
+            const int asel = q > p;
+            const SglT<R> &S = H.s1a[pa];
+            const MixT<R> *Mrow = H.mix + (size_t)pa * H.n_pairs;
+#pragma unroll
+            for (int i = 0; i < EPT; ++i) {
+                if (cix[i] < 0) continue;
+                const uint32_t cb_str = sc[i];
+                // alpha-only pair group: same column
+                R val = S.lut[asel];
+                if (S.spec >= 0) {
+                    const int pat = asel ? 2 : 1;
+                    for (uint32_t w = sRp & ~(1u << q); w; w &= w - 1u)
+                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + pat];
+                    for (uint32_t w = cb_str; w; w &= w - 1u)
+                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
+                }
+                if (jw_parity(sRp, cb_str, S.j)) val = -val;
+                accumulate<R>(acc[i], comp[i], val, src[cix[i]]);
+                // mixed groups through the lane's beta single excitations
+                const uint32_t vir = full & ~cb_str;
+                for (uint32_t o = cb_str; o; o &= o - 1u) {
+                    const int j = __ffs(o) - 1;
+                    for (uint32_t v = vir; v; v &= v - 1u) {
+                        const int bb = __ffs(v) - 1;
+                        const MixT<R> &M = Mrow[pair_index(min(j, bb), max(j, bb))];
+                        const uint32_t yb = cb_str ^ (1u << j) ^ (1u << bb);
+                        R w = M.lut[asel + 2 * (bb > j)];
+                        if (jw_parity(sRp, yb, M.j)) w = -w;
+                        accumulate<R>(acc[i], comp[i], w, src[brk[yb]]);
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- alpha doubles: source amplitude of the same column ----
+    for (uint32_t o1 = sR; o1; o1 &= o1 - 1u) {
+        const int p1 = __ffs(o1) - 1;
+        for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
+            const int p2 = __ffs(o2) - 1;
+            for (uint32_t v1 = virA; v1; v1 &= v1 - 1u) {
+                const int q1 = __ffs(v1) - 1;
+                for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
+                    const int q2 = __ffs(v2) - 1;
+                    const uint32_t m = (1u << p1) | (1u << p2) | (1u << q1) | (1u << q2);
+                    uint32_t t = m;
+                    const int k0 = __ffs(t) - 1; t &= t - 1u;
+                    const int k1 = __ffs(t) - 1; t &= t - 1u;
+                    const int k2 = __ffs(t) - 1; t &= t - 1u;
+                    const int k3 = __ffs(t) - 1;
+                    const int qi = nb4[k3 * 5 + 4] + nb4[k2 * 5 + 3] + nb4[k1 * 5 + 2] + k0;
+                    const int rq1 = __popc(m & ((1u << q1) - 1u));
+                    const int rq2 = __popc(m & ((1u << q2) - 1u));
+                    const DblT<R> &Dq = H.d2a[qi];
+                    const uint32_t sRp = sR ^ m;
+                    const uint32_t xRp = hs.aspread[sRp];
+                    const R base = Dq.lut[(1 << rq1) | (1 << rq2)];
+#pragma unroll
+                    for (int i = 0; i < EPT; ++i) {
+                        if (cix[i] < 0) continue;
+                        R val = jw_parity(sRp, sc[i], Dq.j) ? -base : base;
+                        accumulate<R>(acc[i], comp[i], val, st[xRp | hs.bspread[sc[i]]]);
+                    }
+                }
+            }
+        }
+    }
+
     double e = 0.0, nrm = 0.0;
-    if (htile(hs, half, h, &ov)) {
-        const int D = ov.Da * ov.Db;
-        uint32_t str[kHEPT];  // alpha string | beta string << 16, or ~0 when unused
-        V2<R> acc[kHEPT], comp[kHEPT];
 #pragma unroll
-        for (int i = 0; i < kHEPT; ++i) {
-            const int j = threadIdx.x + i * blockDim.x;
-            if (j < D) {
-                const int ia = j / ov.Db;
-                str[i] = (uint32_t)ov.ca[ia] | ((uint32_t)ov.cb[j - ia * ov.Db] << 16);
-            } else {
-                str[i] = 0xFFFFFFFFu;
-            }
-            acc[i].x = acc[i].y = comp[i].x = comp[i].y = (R)0;
-        }
-        for (int s = 0; s < H.n_seg; ++s) {
-            const uint32_t hsrc = h ^ H.seg_d[s];
-            HTileView sv;
-            if (!htile(hs, half, hsrc, &sv)) continue;  // source tile is all zero (uniform)
-            const uint32_t base = hsrc << LH;
-            const int Ds = sv.Da * sv.Db;
-            __syncthreads();
-            for (int j = threadIdx.x; j < Ds; j += blockDim.x) {
-                const int ia = j / sv.Db;
-                tile[j] = src[base | spa[sv.ca[ia]] | spb[sv.cb[j - ia * sv.Db]]];
-            }
-            __syncthreads();
-            const int g_end = H.seg_begin[s + 1];
-            for (int g = H.seg_begin[s]; g < g_end; ++g) {
-                const GroupT<R> *G = H.groups + g;
-                const uint32_t xm = G->xmask;
-                const uint32_t jm = G->jmask;
-                const uint32_t mla = G->mla, mlb = G->mlb;
-                // occupied flip bits the source carries above the tile (uniform)
-                const uint32_t xhi = xm >> LH;
-                const int need_a = G->ha - __popc(hsrc & xhi & 0x55555555u);
-                const int need_b = G->hb - __popc(hsrc & xhi & 0xAAAAAAAAu);
-                const int nb = G->nb;
-                const int spec = G->spec;
-                const int p0 = G->pos[0], p1 = G->pos[1], p2 = G->pos[2], p3 = G->pos[3];
-#pragma unroll
-                for (int i = 0; i < kHEPT; ++i) {
-                    if (str[i] == 0xFFFFFFFFu) continue;
-                    const uint32_t ya = (str[i] & 0xFFFFu) ^ mla;
-                    const uint32_t yb = (str[i] >> 16) ^ mlb;
-                    if (__popc(ya & mla) != need_a || __popc(yb & mlb) != need_b) continue;
-                    const uint32_t y = base | spa[ya] | spb[yb];
-                    int pat = ((y >> p0) & 1u) | (((y >> p1) & 1u) << 1);
-                    if (nb == 4) pat |= (((y >> p2) & 1u) << 2) | (((y >> p3) & 1u) << 3);
-                    R v = G->lut[pat];
-                    if (spec >= 0) {
-                        uint32_t occ = y & ~xm;
-                        while (occ) {
-                            const int w = __ffs(occ) - 1;
-                            occ &= occ - 1u;
-                            v += H.spec[(size_t)(spec + w) * 4 + pat];
-                        }
-                    }
-                    if (__popc(y & jm) & 1u) v = -v;
-                    accumulate<R>(acc[i], comp[i], v, tile[rk[ya] * sv.Db + rk[yb]]);
-                }
-            }
-        }
-        // The last segment is the own tile (d = 0): psi_x is resident.
-        const uint32_t own = h << LH;
-        const int n = H.n;
-#pragma unroll
-        for (int i = 0; i < kHEPT; ++i) {
-            if (str[i] == 0xFFFFFFFFu) continue;
-            const uint32_t sa = str[i] & 0xFFFFu, sb = str[i] >> 16;
-            const V2<R> p = tile[rk[sa] * ov.Db + rk[sb]];
-            const uint32_t x = own | spa[sa] | spb[sb];
-            if (H.has_diag) {
-                long long q = H.diag_q0;
-                uint32_t o1 = x;
-                while (o1) {
-                    const int a = __ffs(o1) - 1;
-                    o1 &= o1 - 1u;
-                    q += H.diag_qa[a];
-                    uint32_t o2 = o1;
-                    while (o2) {
-                        const int r = __ffs(o2) - 1;
-                        o2 &= o2 - 1u;
-                        q += H.diag_qb[a * n + r];
-                    }
-                }
-                accumulate<R>(acc[i], comp[i], (R)q * (R)H.diag_unit, p);
-            }
-            e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
-            nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-            if (store_sigma) sig[(size_t)b * N + x] = acc[i];
-        }
+    for (int i = 0; i < EPT; ++i) {
+        if (cix[i] < 0) continue;
+        const V2<R> p = own[i];
+        e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
+        nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
+        if (store_sigma)
+            sig[(size_t)b * N + (hs.aspread[sR] | hs.bspread[sc[i]])] = acc[i];
     }
     e = block_sum(e, red);
     nrm = block_sum(nrm, red);
     if (threadIdx.x == 0) {
-        Epart[2 * ((size_t)b * gridDim.x + h)] = e;
-        Epart[2 * ((size_t)b * gridDim.x + h) + 1] = nrm;
+        Epart[2 * ((size_t)b * gridDim.x + blockIdx.x)] = e;
+        Epart[2 * ((size_t)b * gridDim.x + blockIdx.x) + 1] = nrm;
     }
 }
 
@@ -310,8 +396,8 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
 // Launch wrappers
 // ---------------------------------------------------------------------------
 template <typename R>
-size_t happly_smem(int max_entries) {
-    return sizeof(V2<R>) * (size_t)max_entries;
+size_t happly_smem(const HSector &hs, int n_orb) {
+    return sizeof(V2<R>) * (size_t)hs.Db + sizeof(uint16_t) * ((size_t)1 << n_orb);
 }
 
 template <typename R>
@@ -326,11 +412,20 @@ cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const in
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
                           const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma) {
-    if (hs.max_entries > kHEPT * kHThreadsV) return cudaErrorInvalidValue;
-    dim3 grid(1u << (cfg.n - LH), cfg.B);
-    happly_kernel<R><<<grid, kHThreadsV, happly_smem<R>(hs.max_entries), cfg.stream>>>(
-        static_cast<const V2<R> *>(psi), static_cast<V2<R> *>(sig), cfg.N, LH, H, hs, Epart,
-        store_sigma);
+    (void)LH;
+    dim3 grid(hs.Da * hs.ncb, cfg.B);
+    const int threads = std::min(kRowThreads, std::max(32, ((hs.colblock + 31) / 32) * 32));
+    const int ept = (hs.colblock + threads - 1) / threads;
+    const size_t smem = happly_smem<R>(hs, H.n_orb);
+    const V2<R> *p = static_cast<const V2<R> *>(psi);
+    V2<R> *s = static_cast<V2<R> *>(sig);
+    switch (ept <= 1 ? 1 : ept <= 2 ? 2 : ept <= 4 ? 4 : ept <= 8 ? 8 : 0) {
+        case 1: happly_kernel<R, 1><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
+        case 2: happly_kernel<R, 2><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
+        case 4: happly_kernel<R, 4><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
+        case 8: happly_kernel<R, 8><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -354,14 +449,20 @@ cudaError_t configure_kernels() {
 #define UCCSD_SET(fn)                                                                  \
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, big);   \
     if (e != cudaSuccess) return e;
-    UCCSD_SET((happly_kernel<float>));
-    UCCSD_SET((happly_kernel<double>));
+    UCCSD_SET((happly_kernel<float, 1>));
+    UCCSD_SET((happly_kernel<float, 2>));
+    UCCSD_SET((happly_kernel<float, 4>));
+    UCCSD_SET((happly_kernel<float, 8>));
+    UCCSD_SET((happly_kernel<double, 1>));
+    UCCSD_SET((happly_kernel<double, 2>));
+    UCCSD_SET((happly_kernel<double, 4>));
+    UCCSD_SET((happly_kernel<double, 8>));
 #undef UCCSD_SET
     return cudaSuccess;
 }
 
 #define UCCSD_INST(R)                                                                          \
-    template size_t happly_smem<R>(int);                                                       \
+    template size_t happly_smem<R>(const HSector &, int);                                      \
     template cudaError_t launch_cs<R>(const LaunchCfg &, const double *, int, const int32_t *, \
                                       const double *, void *);                                 \
     template cudaError_t launch_happly<R>(const LaunchCfg &, const void *, void *, int,        \

@@ -9,14 +9,15 @@
 
 namespace uccsd {
 
-// Device copy of the compiled Hamiltonian for one precision R.
+// Device copy of the compiled Hamiltonian for one precision R, by group class.
 template <typename R>
 struct DevHam {
-    const GroupT<R> *groups = nullptr;  // sorted by segment, diagonal segment last
-    const int32_t *seg_begin = nullptr; // n_seg + 1
-    const uint32_t *seg_d = nullptr;    // high-part XOR of each segment
-    int n_seg = 0;
-    const R *spec = nullptr;            // spectator rows [row][4]
+    const MixT<R> *mix = nullptr;  // [n_pairs * n_pairs], alpha pair major
+    const SglT<R> *s1a = nullptr;  // [n_pairs] alpha singles
+    const SglT<R> *s1b = nullptr;  // [n_pairs] beta singles
+    const DblT<R> *d2a = nullptr;  // [n_quads] alpha doubles
+    const DblT<R> *d2b = nullptr;  // [n_quads] beta doubles
+    const R *spec = nullptr;       // spectator rows [row][4]
     // Diagonal group as an occupation quadratic form in 64-bit fixed point
     // (one unit = diag_unit Ha), summed exactly:
     //   d(x) - shift = q0 + sum_{q in occ(x)} qa[q] + sum_{q<r in occ(x)} qb[q*n + r]
@@ -25,20 +26,24 @@ struct DevHam {
     long long diag_q0 = 0;
     double diag_unit = 0.0;
     int has_diag = 0;
-    int n = 0;                          // qubits (row length of diag_qb)
+    int n = 0;                          // qubits
+    int n_orb = 0, n_pairs = 0;
 };
 
-// Compact sector tiles of the H-apply: a tile is the set of sector
-// amplitudes with fixed values of the bits above the low LH bits; its entries
-// form a [C(LH/2, a)] x [C(LH/2, b)] array indexed by the ranks of the low
-// alpha and beta bit strings among strings of equal popcount.
+// Sector layout of the H-apply: a row is one alpha string of the sector
+// (n_alpha electrons), its columns are the beta strings (n_beta electrons),
+// both in rank order (rank = position among strings of equal popcount).
+// A CTA owns the columns [cb * colblock, (cb + 1) * colblock) of one row.
 struct HSector {
-    const uint16_t *combos = nullptr;    // strings sorted by (popcount, value), per bit count
-    const uint16_t *ranks = nullptr;     // rank of a string within its popcount class
-    const int32_t *comb_offs = nullptr;  // class offsets, 17 per bit count
-    const uint32_t *spread = nullptr;    // 2^(LH/2) alpha then 2^(LH/2) beta string deposits
+    const uint16_t *astr = nullptr;    // Da alpha strings
+    const uint16_t *bstr = nullptr;    // Db beta strings
+    const uint16_t *brank = nullptr;   // rank of any n_orb-bit string in its popcount class
+    const uint32_t *aspread = nullptr; // alpha string -> global bits (2^n_orb)
+    const uint32_t *bspread = nullptr; // beta string -> global bits (2^n_orb)
+    const int32_t *binom = nullptr;    // binom[t * 5 + k], t < 16, k <= 4
     int n_alpha = 0, n_beta = 0;
-    int max_entries = 0;                 // largest compact tile
+    int Da = 0, Db = 0;
+    int colblock = 0, ncb = 1;
 };
 
 struct LaunchCfg {
@@ -97,9 +102,9 @@ cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles
                           const int32_t *k_ops, const double *op_scale, double shift,
                           int rayleigh, double *E, double *grad);
 
-// Shared memory of the H-apply kernel for its largest compact tile.
+// Shared memory of the H-apply kernel.
 template <typename R>
-size_t happly_smem(int max_entries);
+size_t happly_smem(const HSector &hs, int n_orb);
 
 // One-time kernel attribute set-up (dynamic shared memory opt-in).
 cudaError_t configure_kernels();

@@ -61,7 +61,7 @@ extern "C" uccsd_status uccsd_expectation_noalloc(uccsd_ctx *c, const void *psi,
         c->err = "uccsd_expectation_noalloc: null state or result pointer";
         return UCCSD_ERR_ARG;
     }
-    const int tiles = 1 << (c->n - c->LH);
+    const int tiles = c->hsec.Da * c->hsec.ncb;
     if (tiles > UCCSD_NOALLOC_MAX_TILES) {
         c->err = "uccsd_expectation_noalloc: " + std::to_string(c->n) +
                  " qubits need " + std::to_string(tiles) +
