@@ -76,6 +76,7 @@ struct CRunDev {
     int32_t spread_off;  // run's spread table: 2^La alpha then 2^Lb beta entries
     int32_t n_tiles;     // 2^(n - La - Lb)
     int32_t max_entries; // largest compact tile over the run's CTAs
+    int32_t max_da, max_db;  // largest C(La, a), C(Lb, b) over the run's CTAs
 };
 
 // One factor exp(angle * G) of the schedule in the string spaces of its

@@ -96,6 +96,20 @@ uint32_t deposit_bits(uint32_t v, uint32_t mask) {
 }
 }  // namespace
 
+void max_tile_sides(int n_qubits, int n_alpha, int n_beta, uint32_t tmask, long long *da,
+                    long long *db) {
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
+    const uint32_t bmask = ((n_qubits >= 32) ? 0xFFFFFFFFu : ((1u << n_qubits) - 1u)) & ~amask;
+    *da = max_binom(popc(tmask & amask), popc(amask), n_alpha);
+    *db = max_binom(popc(tmask & bmask), popc(bmask), n_beta);
+}
+
+size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
+                        int nvec) {
+    return size_t(entries) * amp_bytes * nvec + 2 * size_t(da + db) * 8;
+}
+
 long long max_tile_entries(int n_qubits, int n_alpha, int n_beta, uint32_t tmask) {
     uint32_t amask = 0;
     for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
@@ -114,7 +128,10 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
     const uint32_t all = (n_qubits >= 32) ? 0xFFFFFFFFu : ((1u << n_qubits) - 1u);
     const uint32_t bmask = all & ~amask;
     auto fits = [&](uint32_t T) {
-        return (size_t)max_tile_entries(n_qubits, n_alpha, n_beta, T) * amp_bytes * nvec <= budget;
+        long long da, db;
+        max_tile_sides(n_qubits, n_alpha, n_beta, T, &da, &db);
+        return sweep_smem_bytes(max_tile_entries(n_qubits, n_alpha, n_beta, T), da, db,
+                                amp_bytes, nvec) <= budget;
     };
     plan.op_tiles.assign(op_k.size(), 1);
     size_t o = 0;
@@ -134,6 +151,12 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
         r.Lb = popc(Tb);
         r.n_tiles = 1 << (n_qubits - r.La - r.Lb);
         r.max_entries = int(max_tile_entries(n_qubits, n_alpha, n_beta, U));
+        {
+            long long da, db;
+            max_tile_sides(n_qubits, n_alpha, n_beta, U, &da, &db);
+            r.max_da = int(da);
+            r.max_db = int(db);
+        }
         r.spread_off = int(plan.spread.size());
         for (uint32_t sidx = 0; sidx < (1u << r.La); ++sidx) plan.spread.push_back(deposit_bits(sidx, Ta));
         for (uint32_t sidx = 0; sidx < (1u << r.Lb); ++sidx) plan.spread.push_back(deposit_bits(sidx, Tb));

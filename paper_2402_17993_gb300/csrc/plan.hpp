@@ -33,6 +33,13 @@ struct SweepPlan {
 // Largest compact tile (entries) of a tile bit set: the sector leaves
 // a alpha electrons for the tile's La alpha bits for every feasible split.
 long long max_tile_entries(int n_qubits, int n_alpha, int n_beta, uint32_t tmask);
+// Largest alpha / beta string counts C(La, a), C(Lb, b) of a tile bit set.
+void max_tile_sides(int n_qubits, int n_alpha, int n_beta, uint32_t tmask, long long *da,
+                    long long *db);
+// Shared memory of one sweep CTA: nvec tiles plus the two double-buffered
+// alpha/beta pair-side lists (8 bytes per string).
+size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
+                        int nvec);
 
 // Split the schedule into maximal consecutive runs whose flipped bits fit in
 // a tile bit set whose largest compact tile of `nvec` vectors of

@@ -17,7 +17,9 @@
 namespace uccsd {
 namespace {
 
-constexpr int kSweepThreads = 512;
+constexpr int kSweepThreadsLarge = 1024;  // tiles of >= kLargeTile entries
+constexpr int kSweepThreadsSmall = 256;
+constexpr int kLargeTile = 4096;
 
 template <typename R>
 struct Vec2;
@@ -56,7 +58,8 @@ __device__ __forceinline__ int comb_count(const int32_t *offs, int m, int k) {
     return (k < 0 || k > m) ? 0 : offs[m * 17 + k + 1] - offs[m * 17 + k];
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -99,7 +102,8 @@ __device__ __forceinline__ uint32_t entry_index(const TileView &v, int e) {
 
 // Pairs of factor `op` inside the tile: occupied-side strings have the op's
 // occupied bits set and its other flip bits clear; the remaining free bits
-// carry (a - noa) alpha and (b - nob) beta electrons.
+// carry (a - noa) alpha and (b - nob) beta electrons.  The pairs are the
+// product of an alpha-side list (Va strings) and a beta-side list (Vb).
 struct PairSet {
     int Va, Vb;
     const uint16_t *fa, *fb;  // free-bit strings
@@ -117,25 +121,47 @@ __device__ __forceinline__ PairSet pair_set(const CRunDev &run, const SweepArgs 
     return p;
 }
 
-// Tile entries (e, e2) of pair j and whether its sign is negated.
-__device__ __forceinline__ void pair_entries(const PairSet &p, const TileView &v, const COpDev &op,
-                                             const int32_t *posa, const int32_t *posb,
-                                             uint32_t rpar, int j, int *e, int *e2, bool *neg) {
-    const int ja = j / p.Vb;
-    const int jb = j - ja * p.Vb;
-    const uint32_t sa = insert_zeros(p.fa[ja], posa, op.nfa) | op.oa;
-    const uint32_t sb = insert_zeros(p.fb[jb], posb, op.nfb) | op.ob;
-    *e = v.ra[sa] * v.Db + v.rb[sb];
-    *e2 = v.ra[sa ^ op.fa] * v.Db + v.rb[sb ^ op.fb];
-    *neg = ((__popc(sa & op.pa) + __popc(sb & op.pb) + rpar) & 1u) != 0u;
+// Side lists of one factor in shared memory: for alpha string ja the row
+// offsets of the occupied side and of its partner, for beta string jb the
+// column offsets; bit 31 of the first word carries the string's Jordan-Wigner
+// parity.  Entry (ja, jb) of the pair set is then
+//   e = A[ja].x + B[jb].x,  e' = A[ja].y + B[jb].y  (parity bits removed).
+__device__ __forceinline__ void build_sides(const PairSet &p, const TileView &v, const COpDev &op,
+                                            int2 *A, int2 *B) {
+    const int32_t posa[4] = {op.posa[0], op.posa[1], op.posa[2], op.posa[3]};
+    const int32_t posb[4] = {op.posb[0], op.posb[1], op.posb[2], op.posb[3]};
+    for (int t = threadIdx.x; t < p.Va + p.Vb; t += blockDim.x) {
+        if (t < p.Va) {
+            const uint32_t s = insert_zeros(p.fa[t], posa, op.nfa) | op.oa;
+            const int par = __popc(s & op.pa) & 1;
+            A[t] = make_int2((int)(v.ra[s] * v.Db) | (par << 31), (int)(v.ra[s ^ op.fa] * v.Db));
+        } else {
+            const int u = t - p.Va;
+            const uint32_t s = insert_zeros(p.fb[u], posb, op.nfb) | op.ob;
+            const int par = __popc(s & op.pb) & 1;
+            B[u] = make_int2((int)v.rb[s] | (par << 31), (int)v.rb[s ^ op.fb]);
+        }
+    }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kSweepThreads) forward_sweep_kernel(
+// j -> (ja, jb) = (j / Vb, j % Vb) by a float reciprocal with an exact fix-up
+// (j < 2^24).
+__device__ __forceinline__ void split_index(int j, int Vb, float inv, int *ja, int *jb) {
+    int q = __float2int_rz(((float)j + 0.5f) * inv);
+    if (q * Vb > j) --q;
+    if ((q + 1) * Vb <= j) ++q;
+    *ja = q;
+    *jb = j - q * Vb;
+}
+
+template <typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
     V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
     const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
+    int2 *lists = reinterpret_cast<int2 *>(tile + run.max_entries);  // [2][max_da + max_db]
+    const int lstride = run.max_da + run.max_db;
     TileView v;
     if (!make_view(run, sa, &v)) return;  // no sector entries in this tile
     const int b = blockIdx.y;
@@ -152,39 +178,56 @@ __global__ void __launch_bounds__(kSweepThreads) forward_sweep_kernel(
         }
         tile[e] = val;
     }
+    if (run.op_begin < run.op_end) {
+        const PairSet p0 = pair_set(run, sa, v, ops[run.op_begin]);
+        build_sides(p0, v, ops[run.op_begin], lists, lists + p0.Va);
+    }
     __syncthreads();
+    int buf = 0;
     for (int o = run.op_begin; o < run.op_end; ++o) {
         const COpDev &op = ops[o];
         const PairSet p = pair_set(run, sa, v, op);
+        int2 *A = lists + buf * lstride;
+        int2 *B = A + p.Va;
+        // next factor's side lists go to the other buffer (independent of psi)
+        if (o + 1 < run.op_end) {
+            const PairSet pn = pair_set(run, sa, v, ops[o + 1]);
+            int2 *An = lists + (buf ^ 1) * lstride;
+            build_sides(pn, v, ops[o + 1], An, An + pn.Va);
+        }
         const int P = p.Va * p.Vb;
-        if (P == 0) continue;  // uniform over the CTA
-        const V2<R> csv = cs[(size_t)b * n_ops + op.op];
-        const R ct = csv.x;
-        const R st0 = op.s0 > 0 ? csv.y : -csv.y;
-        const uint32_t rpar = __popc(v.rest & op.par_rest) & 1u;
-        const int32_t posa[4] = {op.posa[0], op.posa[1], op.posa[2], op.posa[3]};
-        const int32_t posb[4] = {op.posb[0], op.posb[1], op.posb[2], op.posb[3]};
-        for (int j = threadIdx.x; j < P; j += blockDim.x) {
-            int e, e2;
-            bool neg;
-            pair_entries(p, v, op, posa, posb, rpar, j, &e, &e2, &neg);
-            const R ss = neg ? -st0 : st0;
-            const V2<R> x0 = tile[e], x1 = tile[e2];
-            V2<R> y0, y1;
-            y0.x = ct * x0.x - ss * x1.x;
-            y0.y = ct * x0.y - ss * x1.y;
-            y1.x = ct * x1.x + ss * x0.x;
-            y1.y = ct * x1.y + ss * x0.y;
-            tile[e] = y0;
-            tile[e2] = y1;
+        if (P > 0) {
+            const V2<R> csv = cs[(size_t)b * n_ops + op.op];
+            const R ct = csv.x;
+            const R st0 = op.s0 > 0 ? csv.y : -csv.y;
+            const int rpar = __popc(v.rest & op.par_rest) & 1;
+            const float inv = 1.0f / (float)p.Vb;
+            for (int j = threadIdx.x; j < P; j += blockDim.x) {
+                int ja, jb;
+                split_index(j, p.Vb, inv, &ja, &jb);
+                const int2 a2 = A[ja], b2 = B[jb];
+                const int e = (a2.x & 0x7FFFFFFF) + (b2.x & 0x7FFFFFFF);
+                const int e2 = a2.y + b2.y;
+                const int neg = ((((unsigned)(a2.x ^ b2.x)) >> 31) ^ rpar) & 1;
+                const R ss = neg ? -st0 : st0;
+                const V2<R> x0 = tile[e], x1 = tile[e2];
+                V2<R> y0, y1;
+                y0.x = ct * x0.x - ss * x1.x;
+                y0.y = ct * x0.y - ss * x1.y;
+                y1.x = ct * x1.x + ss * x0.x;
+                y1.y = ct * x1.y + ss * x0.y;
+                tile[e] = y0;
+                tile[e2] = y1;
+            }
         }
         __syncthreads();
+        buf ^= 1;
     }
     for (int e = threadIdx.x; e < D; e += blockDim.x) st[entry_index(v, e)] = tile[e];
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kSweepThreads) adjoint_sweep_kernel(
+template <typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
     double *__restrict__ gpart, int tile_stride) {
@@ -201,6 +244,8 @@ __global__ void __launch_bounds__(kSweepThreads) adjoint_sweep_kernel(
     const int D = v.Da * v.Db;
     V2<R> *tp = reinterpret_cast<V2<R> *>(smem_raw);
     V2<R> *tl = tp + run.max_entries;
+    int2 *lists = reinterpret_cast<int2 *>(tl + run.max_entries);
+    const int lstride = run.max_da + run.max_db;
     V2<R> *sp = phi + (size_t)b * N;
     V2<R> *sl = lam + (size_t)b * N;
     const int nw = blockDim.x >> 5;
@@ -210,58 +255,73 @@ __global__ void __launch_bounds__(kSweepThreads) adjoint_sweep_kernel(
         tp[e] = sp[x];
         tl[e] = sl[x];
     }
+    if (run.op_begin < run.op_end) {
+        const COpDev &opl = ops[run.op_end - 1];
+        const PairSet p0 = pair_set(run, sa, v, opl);
+        build_sides(p0, v, opl, lists, lists + p0.Va);
+    }
     __syncthreads();
-    int it = 0;
+    int it = 0, buf = 0;
     for (int o = run.op_end - 1; o >= run.op_begin; --o) {
         const COpDev &op = ops[o];
         const PairSet p = pair_set(run, sa, v, op);
+        int2 *A = lists + buf * lstride;
+        int2 *B = A + p.Va;
+        if (o - 1 >= run.op_begin) {
+            const PairSet pn = pair_set(run, sa, v, ops[o - 1]);
+            int2 *An = lists + (buf ^ 1) * lstride;
+            build_sides(pn, v, ops[o - 1], An, An + pn.Va);
+        }
         const int P = p.Va * p.Vb;
         const size_t gidx = ((size_t)b * n_ops + op.op) * tile_stride + blockIdx.x;
-        if (P == 0) {
-            if (threadIdx.x == 0) gpart[gidx] = 0.0;
-            continue;
-        }
-        const V2<R> csv = cs[(size_t)b * n_ops + op.op];
-        const R ct = csv.x;
-        const R st0 = op.s0 > 0 ? csv.y : -csv.y;
-        const uint32_t rpar = __popc(v.rest & op.par_rest) & 1u;
-        const int32_t posa[4] = {op.posa[0], op.posa[1], op.posa[2], op.posa[3]};
-        const int32_t posb[4] = {op.posb[0], op.posb[1], op.posb[2], op.posb[3]};
         R part = (R)0;
-        for (int j = threadIdx.x; j < P; j += blockDim.x) {
-            int e, e2;
-            bool neg;
-            pair_entries(p, v, op, posa, posb, rpar, j, &e, &e2, &neg);
-            const V2<R> fa = tp[e], fb = tp[e2];
-            const V2<R> la = tl[e], lb = tl[e2];
-            // (G phi)_x = -s phi_x', (G phi)_x' = s phi_x
-            const R d = (lb.x * fa.x + lb.y * fa.y) - (la.x * fb.x + la.y * fb.y);
-            part += neg ? -d : d;
-            const R ss = neg ? -st0 : st0;
-            V2<R> w;
-            w.x = ct * fa.x + ss * fb.x;
-            w.y = ct * fa.y + ss * fb.y;
-            tp[e] = w;
-            w.x = ct * fb.x - ss * fa.x;
-            w.y = ct * fb.y - ss * fa.y;
-            tp[e2] = w;
-            w.x = ct * la.x + ss * lb.x;
-            w.y = ct * la.y + ss * lb.y;
-            tl[e] = w;
-            w.x = ct * lb.x - ss * la.x;
-            w.y = ct * lb.y - ss * la.y;
-            tl[e2] = w;
+        if (P > 0) {
+            const V2<R> csv = cs[(size_t)b * n_ops + op.op];
+            const R ct = csv.x;
+            const R st0 = op.s0 > 0 ? csv.y : -csv.y;
+            const int rpar = __popc(v.rest & op.par_rest) & 1;
+            const float inv = 1.0f / (float)p.Vb;
+            for (int j = threadIdx.x; j < P; j += blockDim.x) {
+                int ja, jb;
+                split_index(j, p.Vb, inv, &ja, &jb);
+                const int2 a2 = A[ja], b2 = B[jb];
+                const int e = (a2.x & 0x7FFFFFFF) + (b2.x & 0x7FFFFFFF);
+                const int e2 = a2.y + b2.y;
+                const bool neg = ((((unsigned)(a2.x ^ b2.x)) >> 31) ^ rpar) & 1;
+                const V2<R> fa = tp[e], fb = tp[e2];
+                const V2<R> la = tl[e], lb = tl[e2];
+                // (G phi)_x = -s phi_x', (G phi)_x' = s phi_x
+                const R d = (lb.x * fa.x + lb.y * fa.y) - (la.x * fb.x + la.y * fb.y);
+                part += neg ? -d : d;
+                const R ss = neg ? -st0 : st0;
+                V2<R> w;
+                w.x = ct * fa.x + ss * fb.x;
+                w.y = ct * fa.y + ss * fb.y;
+                tp[e] = w;
+                w.x = ct * fb.x - ss * fa.x;
+                w.y = ct * fb.y - ss * fa.y;
+                tp[e2] = w;
+                w.x = ct * la.x + ss * lb.x;
+                w.y = ct * la.y + ss * lb.y;
+                tl[e] = w;
+                w.x = ct * lb.x - ss * la.x;
+                w.y = ct * lb.y - ss * la.y;
+                tl[e2] = w;
+            }
         }
-        double dp = warp_sum((double)part * (double)op.s0);
-        const int buf = it & 1;
+        // per-warp partial in the state precision (<= 32 thread partials of a
+        // few products each), then FP64 across warps, tiles and factors
+        const double dp = (double)warp_sum(part) * (double)op.s0;
+        const int rb = it & 1;
         ++it;
-        if (lane == 0) wring[buf][warp] = dp;
+        if (lane == 0) wring[rb][warp] = dp;
         __syncthreads();
         if (warp == 0) {
-            double s = (lane < nw) ? wring[buf][lane] : 0.0;
-            s = warp_sum(s);
-            if (lane == 0) gpart[gidx] = s;
+            double s2 = (lane < nw) ? wring[rb][lane] : 0.0;
+            s2 = warp_sum<double>(s2);
+            if (lane == 0) gpart[gidx] = s2;
         }
+        buf ^= 1;
     }
     for (int e = threadIdx.x; e < D; e += blockDim.x) {
         const uint32_t x = entry_index(v, e);
@@ -286,10 +346,16 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
                                  int init_hf, uint32_t hf) {
     dim3 grid(run.n_tiles, cfg.B);
-    const size_t smem = sizeof(V2<R>) * (size_t)run.max_entries;
-    forward_sweep_kernel<R><<<grid, kSweepThreads, smem, cfg.stream>>>(
-        static_cast<V2<R> *>(psi), cfg.N, run, ops, static_cast<const V2<R> *>(cs), cfg.n_ops, sa,
-        init_hf, hf);
+    const size_t smem = sizeof(V2<R>) * (size_t)run.max_entries +
+                        2 * sizeof(int2) * (size_t)(run.max_da + run.max_db);
+    V2<R> *p = static_cast<V2<R> *>(psi);
+    const V2<R> *c = static_cast<const V2<R> *>(cs);
+    if (run.max_entries >= kLargeTile)
+        forward_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
+            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+    else
+        forward_sweep_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
+            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
     return cudaGetLastError();
 }
 
@@ -298,10 +364,17 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
                                  double *gpart, int tile_stride) {
     dim3 grid(run.n_tiles, cfg.B);
-    const size_t smem = 2 * sizeof(V2<R>) * (size_t)run.max_entries;
-    adjoint_sweep_kernel<R><<<grid, kSweepThreads, smem, cfg.stream>>>(
-        static_cast<V2<R> *>(phi), static_cast<V2<R> *>(lam), cfg.N, run, ops,
-        static_cast<const V2<R> *>(cs), cfg.n_ops, sa, gpart, tile_stride);
+    const size_t smem = 2 * sizeof(V2<R>) * (size_t)run.max_entries +
+                        2 * sizeof(int2) * (size_t)(run.max_da + run.max_db);
+    V2<R> *f = static_cast<V2<R> *>(phi);
+    V2<R> *l = static_cast<V2<R> *>(lam);
+    const V2<R> *c = static_cast<const V2<R> *>(cs);
+    if (run.max_entries >= kLargeTile)
+        adjoint_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
+            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+    else
+        adjoint_sweep_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
+            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
     return cudaGetLastError();
 }
 
@@ -312,19 +385,20 @@ cudaError_t launch_set_hf(const LaunchCfg &cfg, void *psi, uint32_t hf) {
 }
 
 cudaError_t configure_sweep_kernels(size_t max_smem) {
-    cudaError_t e;
     const int bytes = (int)max_smem;
-    if ((e = cudaFuncSetAttribute(forward_sweep_kernel<float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    if ((e = cudaFuncSetAttribute(forward_sweep_kernel<double>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    if ((e = cudaFuncSetAttribute(adjoint_sweep_kernel<float>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
-        return e;
-    return cudaFuncSetAttribute(adjoint_sweep_kernel<double>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaSuccess;
+#define UCCSD_SWEEP_ATTR(K)                                                               \
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    UCCSD_SWEEP_ATTR((forward_sweep_kernel<float, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((forward_sweep_kernel<float, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((forward_sweep_kernel<double, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((forward_sweep_kernel<double, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<float, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<float, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<double, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<double, kSweepThreadsSmall>))
+#undef UCCSD_SWEEP_ATTR
+    return e;
 }
 
 #define UCCSD_SWEEP_INST(R)                                                                    \
