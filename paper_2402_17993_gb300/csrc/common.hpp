@@ -84,16 +84,13 @@ struct CRunDev {
 // The occupied side of a pair has the bits oa/ob set and the other flip
 // bits clear; the partner flips fa/fb.  JW sign of the pair:
 //   s0 * (-1)^{popc(sa & pa) + popc(sb & pb) + popc(rest & par_rest)}.
+// op_s0: index of the factor in the schedule, bit 31 set when s0 = -1.
 struct COpDev {
     uint32_t fa, fb;      // flipped bits
     uint32_t oa, ob;      // occupied-side bits
     uint32_t pa, pb;      // Jordan-Wigner parity bits inside the tile
     uint32_t par_rest;    // Jordan-Wigner parity bits outside the tile (global)
-    int32_t nfa, nfb;     // popcounts of fa, fb
-    int32_t noa, nob;     // popcounts of oa, ob
-    int32_t posa[4], posb[4];  // flip positions, ascending
-    int32_t s0;           // +1 or -1
-    int32_t op;           // index of this factor in the schedule
+    uint32_t op_s0;
 };
 
 }  // namespace uccsd

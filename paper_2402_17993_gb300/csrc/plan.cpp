@@ -106,8 +106,17 @@ void max_tile_sides(int n_qubits, int n_alpha, int n_beta, uint32_t tmask, long 
 }
 
 size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
-                        int nvec) {
-    return size_t(entries) * amp_bytes * nvec + 2 * size_t(da + db) * 8;
+                        int nvec, int n_ops_run, int lmax) {
+    size_t b = size_t(entries) * amp_bytes * nvec + 2 * size_t(da + db) * 8 +
+               size_t(n_ops_run) * sizeof(COpDev);
+    if (lmax <= kStageLmax) b += sweep_table_bytes(lmax);
+    return b;
+}
+
+size_t sweep_table_bytes(int lmax) {
+    // combos and ranks prefixes (bit counts <= lmax) and their class offsets
+    return 2 * (((size_t(1) << (lmax + 1)) - 1) * sizeof(uint16_t)) +
+           size_t(lmax + 1) * 17 * sizeof(int32_t) + 16;
 }
 
 long long max_tile_entries(int n_qubits, int n_alpha, int n_beta, uint32_t tmask) {
@@ -127,11 +136,12 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
     for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
     const uint32_t all = (n_qubits >= 32) ? 0xFFFFFFFFu : ((1u << n_qubits) - 1u);
     const uint32_t bmask = all & ~amask;
-    auto fits = [&](uint32_t T) {
+    auto fits = [&](uint32_t T, int run_ops) {
         long long da, db;
         max_tile_sides(n_qubits, n_alpha, n_beta, T, &da, &db);
+        const int lmax = std::max(popc(T & amask), popc(T & bmask));
         return sweep_smem_bytes(max_tile_entries(n_qubits, n_alpha, n_beta, T), da, db,
-                                amp_bytes, nvec) <= budget;
+                                amp_bytes, nvec, run_ops, lmax) <= budget;
     };
     plan.op_tiles.assign(op_k.size(), 1);
     size_t o = 0;
@@ -139,7 +149,7 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
     while (o < n_ops) {
         uint32_t U = exc[op_k[o]].flip;
         size_t e = o + 1;
-        while (e < n_ops && fits(U | exc[op_k[e]].flip)) {
+        while (e < n_ops && fits(U | exc[op_k[e]].flip, int(e - o + 1))) {
             U |= exc[op_k[e]].flip;
             ++e;
         }
@@ -171,17 +181,7 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
             d.pa = gather_bits(x.par, Ta);
             d.pb = gather_bits(x.par, Tb);
             d.par_rest = x.par & ~U;
-            d.nfa = popc(d.fa);
-            d.nfb = popc(d.fb);
-            d.noa = popc(d.oa);
-            d.nob = popc(d.ob);
-            int ka = 0, kb = 0;
-            for (int q = 0; q < 32; ++q) {
-                if ((d.fa >> q) & 1u) d.posa[ka++] = q;
-                if ((d.fb >> q) & 1u) d.posb[kb++] = q;
-            }
-            d.s0 = x.s0;
-            d.op = int(u);
+            d.op_s0 = uint32_t(u) | (x.s0 < 0 ? 0x80000000u : 0u);
             plan.ops.push_back(d);
             plan.op_tiles[u] = r.n_tiles;
         }

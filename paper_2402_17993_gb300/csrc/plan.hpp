@@ -36,10 +36,16 @@ long long max_tile_entries(int n_qubits, int n_alpha, int n_beta, uint32_t tmask
 // Largest alpha / beta string counts C(La, a), C(Lb, b) of a tile bit set.
 void max_tile_sides(int n_qubits, int n_alpha, int n_beta, uint32_t tmask, long long *da,
                     long long *db);
-// Shared memory of one sweep CTA: nvec tiles plus the two double-buffered
-// alpha/beta pair-side lists (8 bytes per string).
+// Bit counts up to which a sweep CTA stages the combinatorial tables in
+// shared memory.
+constexpr int kStageLmax = 10;
+// Shared memory of the staged combinatorial tables for bit counts <= lmax.
+size_t sweep_table_bytes(int lmax);
+// Shared memory of one sweep CTA: nvec tiles, the two double-buffered
+// alpha/beta pair-side lists (8 bytes per string), the run's factor
+// descriptors and (lmax <= kStageLmax) the staged tables.
 size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
-                        int nvec);
+                        int nvec, int n_ops_run, int lmax);
 
 // Split the schedule into maximal consecutive runs whose flipped bits fit in
 // a tile bit set whose largest compact tile of `nvec` vectors of

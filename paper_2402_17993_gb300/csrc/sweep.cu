@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "kernels.cuh"
+#include "plan.hpp"
 
 namespace uccsd {
 namespace {
@@ -45,10 +46,10 @@ __device__ __forceinline__ uint32_t deposit(uint32_t v, uint32_t mask) {
     return r;
 }
 
-// Insert a zero bit at each ascending position pos[0..nb).
-__device__ __forceinline__ uint32_t insert_zeros(uint32_t j, const int32_t *pos, int nb) {
-    for (int k = 0; k < nb; ++k) {
-        const uint32_t lowm = (1u << pos[k]) - 1u;
+// Insert a zero bit at each set bit position of mask, lowest first.
+__device__ __forceinline__ uint32_t insert_zeros(uint32_t j, uint32_t mask) {
+    for (; mask; mask &= mask - 1u) {
+        const uint32_t lowm = (mask & (0u - mask)) - 1u;
         j = ((j & ~lowm) << 1) | (j & lowm);
     }
     return j;
@@ -112,8 +113,8 @@ struct PairSet {
 __device__ __forceinline__ PairSet pair_set(const CRunDev &run, const SweepArgs &sa,
                                             const TileView &v, const COpDev &op) {
     PairSet p;
-    const int ma = run.La - op.nfa, mb = run.Lb - op.nfb;
-    const int ka = v.a - op.noa, kb = v.b - op.nob;
+    const int ma = run.La - __popc(op.fa), mb = run.Lb - __popc(op.fb);
+    const int ka = v.a - __popc(op.oa), kb = v.b - __popc(op.ob);
     p.Va = comb_count(sa.comb_offs, ma, ka);
     p.Vb = comb_count(sa.comb_offs, mb, kb);
     p.fa = p.Va ? sa.combos + ((1 << ma) - 1) + sa.comb_offs[ma * 17 + ka] : nullptr;
@@ -128,20 +129,50 @@ __device__ __forceinline__ PairSet pair_set(const CRunDev &run, const SweepArgs 
 //   e = A[ja].x + B[jb].x,  e' = A[ja].y + B[jb].y  (parity bits removed).
 __device__ __forceinline__ void build_sides(const PairSet &p, const TileView &v, const COpDev &op,
                                             int2 *A, int2 *B) {
-    const int32_t posa[4] = {op.posa[0], op.posa[1], op.posa[2], op.posa[3]};
-    const int32_t posb[4] = {op.posb[0], op.posb[1], op.posb[2], op.posb[3]};
     for (int t = threadIdx.x; t < p.Va + p.Vb; t += blockDim.x) {
         if (t < p.Va) {
-            const uint32_t s = insert_zeros(p.fa[t], posa, op.nfa) | op.oa;
+            const uint32_t s = insert_zeros(p.fa[t], op.fa) | op.oa;
             const int par = __popc(s & op.pa) & 1;
             A[t] = make_int2((int)(v.ra[s] * v.Db) | (par << 31), (int)(v.ra[s ^ op.fa] * v.Db));
         } else {
             const int u = t - p.Va;
-            const uint32_t s = insert_zeros(p.fb[u], posb, op.nfb) | op.ob;
+            const uint32_t s = insert_zeros(p.fb[u], op.fb) | op.ob;
             const int par = __popc(s & op.pb) & 1;
             B[u] = make_int2((int)v.rb[s] | (par << 31), (int)v.rb[s ^ op.fb]);
         }
     }
+}
+
+// Stage the run's factor descriptors and (small tiles) the combinatorial
+// table prefixes into shared memory at `base`; returns the table view the
+// CTA uses.  Callers synchronise before use.
+__device__ __forceinline__ SweepArgs stage_tables(const CRunDev &run, const SweepArgs &sa,
+                                                  const COpDev *ops, unsigned char *base,
+                                                  COpDev **sops) {
+    const int nops = run.op_end - run.op_begin;
+    COpDev *so = reinterpret_cast<COpDev *>(base);
+    const uint32_t *gsrc = reinterpret_cast<const uint32_t *>(ops + run.op_begin);
+    uint32_t *gdst = reinterpret_cast<uint32_t *>(so);
+    for (int t = threadIdx.x; t < nops * 8; t += blockDim.x) gdst[t] = gsrc[t];
+    *sops = so;
+    SweepArgs la = sa;
+    const int lmax = max(run.La, run.Lb);
+    if (lmax <= kStageLmax) {
+        int32_t *offs = reinterpret_cast<int32_t *>(so + nops);
+        const int n_offs = (lmax + 1) * 17;
+        uint16_t *cmb = reinterpret_cast<uint16_t *>(offs + n_offs);
+        const int n_str = (1 << (lmax + 1)) - 1;
+        uint16_t *rnk = cmb + n_str;
+        for (int t = threadIdx.x; t < n_offs; t += blockDim.x) offs[t] = sa.comb_offs[t];
+        for (int t = threadIdx.x; t < n_str; t += blockDim.x) {
+            cmb[t] = sa.combos[t];
+            rnk[t] = sa.ranks[t];
+        }
+        la.comb_offs = offs;
+        la.combos = cmb;
+        la.ranks = rnk;
+    }
+    return la;
 }
 
 // j -> (ja, jb) = (j / Vb, j % Vb) by a float reciprocal with an exact fix-up
@@ -164,6 +195,10 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
     const int lstride = run.max_da + run.max_db;
     TileView v;
     if (!make_view(run, sa, &v)) return;  // no sector entries in this tile
+    COpDev *sops;
+    const SweepArgs la = stage_tables(run, sa, ops, reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops);
+    __syncthreads();
+    make_view(run, la, &v);
     const int b = blockIdx.y;
     V2<R> *st = psi + (size_t)b * N;
     const int D = v.Da * v.Db;
@@ -179,27 +214,28 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
         tile[e] = val;
     }
     if (run.op_begin < run.op_end) {
-        const PairSet p0 = pair_set(run, sa, v, ops[run.op_begin]);
-        build_sides(p0, v, ops[run.op_begin], lists, lists + p0.Va);
+        const PairSet p0 = pair_set(run, la, v, sops[0]);
+        build_sides(p0, v, sops[0], lists, lists + p0.Va);
     }
     __syncthreads();
     int buf = 0;
-    for (int o = run.op_begin; o < run.op_end; ++o) {
-        const COpDev &op = ops[o];
-        const PairSet p = pair_set(run, sa, v, op);
+    const int nops = run.op_end - run.op_begin;
+    for (int o = 0; o < nops; ++o) {
+        const COpDev &op = sops[o];
+        const PairSet p = pair_set(run, la, v, op);
         int2 *A = lists + buf * lstride;
         int2 *B = A + p.Va;
         // next factor's side lists go to the other buffer (independent of psi)
-        if (o + 1 < run.op_end) {
-            const PairSet pn = pair_set(run, sa, v, ops[o + 1]);
+        if (o + 1 < nops) {
+            const PairSet pn = pair_set(run, la, v, sops[o + 1]);
             int2 *An = lists + (buf ^ 1) * lstride;
-            build_sides(pn, v, ops[o + 1], An, An + pn.Va);
+            build_sides(pn, v, sops[o + 1], An, An + pn.Va);
         }
         const int P = p.Va * p.Vb;
         if (P > 0) {
-            const V2<R> csv = cs[(size_t)b * n_ops + op.op];
+            const V2<R> csv = cs[(size_t)b * n_ops + (op.op_s0 & 0x7FFFFFFFu)];
             const R ct = csv.x;
-            const R st0 = op.s0 > 0 ? csv.y : -csv.y;
+            const R st0 = (op.op_s0 >> 31) ? -csv.y : csv.y;
             const int rpar = __popc(v.rest & op.par_rest) & 1;
             const float inv = 1.0f / (float)p.Vb;
             for (int j = threadIdx.x; j < P; j += blockDim.x) {
@@ -238,47 +274,52 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     if (!make_view(run, sa, &v)) {
         // all-zero tile: its gradient partials are zero
         for (int o = run.op_begin + threadIdx.x; o < run.op_end; o += blockDim.x)
-            gpart[((size_t)b * n_ops + ops[o].op) * tile_stride + blockIdx.x] = 0.0;
+            gpart[((size_t)b * n_ops + (ops[o].op_s0 & 0x7FFFFFFFu)) * tile_stride + blockIdx.x] = 0.0;
         return;
     }
-    const int D = v.Da * v.Db;
     V2<R> *tp = reinterpret_cast<V2<R> *>(smem_raw);
     V2<R> *tl = tp + run.max_entries;
     int2 *lists = reinterpret_cast<int2 *>(tl + run.max_entries);
     const int lstride = run.max_da + run.max_db;
+    COpDev *sops;
+    const SweepArgs la = stage_tables(run, sa, ops, reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops);
+    __syncthreads();
+    make_view(run, la, &v);
+    const int D = v.Da * v.Db;
     V2<R> *sp = phi + (size_t)b * N;
     V2<R> *sl = lam + (size_t)b * N;
     const int nw = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nops = run.op_end - run.op_begin;
     for (int e = threadIdx.x; e < D; e += blockDim.x) {
         const uint32_t x = entry_index(v, e);
         tp[e] = sp[x];
         tl[e] = sl[x];
     }
-    if (run.op_begin < run.op_end) {
-        const COpDev &opl = ops[run.op_end - 1];
-        const PairSet p0 = pair_set(run, sa, v, opl);
-        build_sides(p0, v, opl, lists, lists + p0.Va);
+    if (nops > 0) {
+        const PairSet p0 = pair_set(run, la, v, sops[nops - 1]);
+        build_sides(p0, v, sops[nops - 1], lists, lists + p0.Va);
     }
     __syncthreads();
     int it = 0, buf = 0;
-    for (int o = run.op_end - 1; o >= run.op_begin; --o) {
-        const COpDev &op = ops[o];
-        const PairSet p = pair_set(run, sa, v, op);
+    for (int o = nops - 1; o >= 0; --o) {
+        const COpDev &op = sops[o];
+        const PairSet p = pair_set(run, la, v, op);
         int2 *A = lists + buf * lstride;
         int2 *B = A + p.Va;
-        if (o - 1 >= run.op_begin) {
-            const PairSet pn = pair_set(run, sa, v, ops[o - 1]);
+        if (o - 1 >= 0) {
+            const PairSet pn = pair_set(run, la, v, sops[o - 1]);
             int2 *An = lists + (buf ^ 1) * lstride;
-            build_sides(pn, v, ops[o - 1], An, An + pn.Va);
+            build_sides(pn, v, sops[o - 1], An, An + pn.Va);
         }
         const int P = p.Va * p.Vb;
-        const size_t gidx = ((size_t)b * n_ops + op.op) * tile_stride + blockIdx.x;
+        const int opi = (int)(op.op_s0 & 0x7FFFFFFFu);
+        const size_t gidx = ((size_t)b * n_ops + opi) * tile_stride + blockIdx.x;
         R part = (R)0;
         if (P > 0) {
-            const V2<R> csv = cs[(size_t)b * n_ops + op.op];
+            const V2<R> csv = cs[(size_t)b * n_ops + opi];
             const R ct = csv.x;
-            const R st0 = op.s0 > 0 ? csv.y : -csv.y;
+            const R st0 = (op.op_s0 >> 31) ? -csv.y : csv.y;
             const int rpar = __popc(v.rest & op.par_rest) & 1;
             const float inv = 1.0f / (float)p.Vb;
             for (int j = threadIdx.x; j < P; j += blockDim.x) {
@@ -311,7 +352,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
         }
         // per-warp partial in the state precision (<= 32 thread partials of a
         // few products each), then FP64 across warps, tiles and factors
-        const double dp = (double)warp_sum(part) * (double)op.s0;
+        const double dp = (op.op_s0 >> 31) ? -(double)warp_sum(part) : (double)warp_sum(part);
         const int rb = it & 1;
         ++it;
         if (lane == 0) wring[rb][warp] = dp;
@@ -346,8 +387,8 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
                                  int init_hf, uint32_t hf) {
     dim3 grid(run.n_tiles, cfg.B);
-    const size_t smem = sizeof(V2<R>) * (size_t)run.max_entries +
-                        2 * sizeof(int2) * (size_t)(run.max_da + run.max_db);
+    const size_t smem = sweep_smem_bytes(run.max_entries, run.max_da, run.max_db, sizeof(V2<R>), 1,
+                                         run.op_end - run.op_begin, max(run.La, run.Lb));
     V2<R> *p = static_cast<V2<R> *>(psi);
     const V2<R> *c = static_cast<const V2<R> *>(cs);
     if (run.max_entries >= kLargeTile)
@@ -364,8 +405,8 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
                                  double *gpart, int tile_stride) {
     dim3 grid(run.n_tiles, cfg.B);
-    const size_t smem = 2 * sizeof(V2<R>) * (size_t)run.max_entries +
-                        2 * sizeof(int2) * (size_t)(run.max_da + run.max_db);
+    const size_t smem = sweep_smem_bytes(run.max_entries, run.max_da, run.max_db, sizeof(V2<R>), 2,
+                                         run.op_end - run.op_begin, max(run.La, run.Lb));
     V2<R> *f = static_cast<V2<R> *>(phi);
     V2<R> *l = static_cast<V2<R> *>(lam);
     const V2<R> *c = static_cast<const V2<R> *>(cs);
