@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             const int j1 = __ffs(o1) - 1;
             for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
                 const int j2 = __ffs(o2) - 1;
+                V2<R> seg = V2<R>{(R)0, (R)0};  // plain partial per occupied pair
                 for (uint32_t v1 = vir; v1; v1 &= v1 - 1u) {
                     const int b1 = __ffs(v1) - 1;
                     for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
@@ -234,9 +235,12 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                         const uint32_t yb = cb_str ^ m;
                         R val = Dq.lut[(1 << rb1) | (1 << rb2)];
                         if (jw_parity(sR, yb, Dq.j)) val = -val;
-                        accumulate<R>(acc[i], comp[i], val, src[brk[yb]]);
+                        const V2<R> y = src[brk[yb]];
+                        seg.x += val * y.x;
+                        seg.y += val * y.y;
                     }
                 }
+                accumulate<R>(acc[i], comp[i], (R)1, seg);
             }
         }
     }
@@ -272,8 +276,10 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                 }
                 if (jw_parity(sRp, cb_str, S.j)) val = -val;
                 accumulate<R>(acc[i], comp[i], val, src[cix[i]]);
-                // mixed groups through the lane's beta single excitations
+                // mixed groups through the lane's beta single excitations:
+                // a plain partial sum per segment, added with compensation
                 const uint32_t vir = full & ~cb_str;
+                V2<R> seg = V2<R>{(R)0, (R)0};
                 for (uint32_t o = cb_str; o; o &= o - 1u) {
                     const int j = __ffs(o) - 1;
                     for (uint32_t v = vir; v; v &= v - 1u) {
@@ -282,9 +288,12 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                         const uint32_t yb = cb_str ^ (1u << j) ^ (1u << bb);
                         R w = M.lut[asel + 2 * (bb > j)];
                         if (jw_parity(sRp, yb, M.j)) w = -w;
-                        accumulate<R>(acc[i], comp[i], w, src[brk[yb]]);
+                        const V2<R> y = src[brk[yb]];
+                        seg.x += w * y.x;
+                        seg.y += w * y.y;
                     }
                 }
+                accumulate<R>(acc[i], comp[i], (R)1, seg);
             }
         }
     }
