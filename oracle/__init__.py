@@ -10,10 +10,13 @@ The arithmetic lives in ``uccsd_oracle.c`` (ladder operators on occupation
 bit strings; Eq. 2 literally and by Slater-Condon rules; Eq. 4 generators;
 Eq. 5/6 schedules; adjoint gradient).  This module adds the list builders,
 the dense-matrix helpers (FCI by numpy.linalg.eigh, Trotter-free energies by
-scipy.linalg.expm) and ctypes marshalling.
+scipy.linalg.expm), the magnitude ordering of Section 2.3 with first-order
+amplitudes, the Trotter-error extrapolation of Section 3.2 and ctypes
+marshalling.
 
 Parity pins: every function here is checked against something other than
-itself in ``tests/test_oracle_pins.py``; none is "parity unpinned".
+itself in ``tests/test_oracle_pins.py`` and ``tests/test_oracle_trotter.py``;
+none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -283,3 +286,79 @@ def trotter_free_energy(n_orb, h, eri, e_core, n_alpha, n_beta, ijab, theta):
     psi = scipy.linalg.expm(A) @ hf
     sig = h_apply(n_orb, h, eri, e_core, psi)
     return float(np.vdot(psi, sig).real), psi
+
+
+# ---------------------------------------------------------------------------
+# Trotter-product ordering (Section 2.3) and Trotter-error extrapolation
+# (Section 3.2, Fig. 3)
+# ---------------------------------------------------------------------------
+def fock_diagonal(n_orb, h, eri, n_alpha, n_beta):
+    """Spin-orbital Fock diagonal of the reference determinant,
+    eps_P = h_pp + sum_{I occupied} [(pp|ii) - delta(s_P, s_I) (pi|ip)],
+    for spin orbital P = 2p + s_P (the orbital energies of Moller-Plesset
+    partitioning)."""
+    n = 2 * n_orb
+    hf = hf_index(n_alpha, n_beta)
+    eps = np.zeros(n)
+    for P in range(n):
+        p = P >> 1
+        v = h[p, p]
+        for I in range(n):
+            if not (hf >> I) & 1:
+                continue
+            i = I >> 1
+            v += eri[p, p, i, i]
+            if (P & 1) == (I & 1):
+                v -= eri[p, i, i, p]
+        eps[P] = v
+    return eps
+
+
+def mp1_amplitudes(n_orb, h, eri, e_core, n_alpha, n_beta, ijab):
+    """First-order (Moller-Plesset) amplitude of every excitation,
+    t_k = <Phi_k|H|HF> / (eps_i + eps_j - eps_a - eps_b), Phi_k = tau_k|HF>
+    (singles: eps_i - eps_a).  The numerator is taken from the state vector:
+    tau_k|HF> = G_k|HF> because tau_k^dag annihilates |HF>.
+    Returns (t, numerators)."""
+    n = 2 * n_orb
+    hf = np.zeros(1 << n, dtype=np.complex128)
+    hf[hf_index(n_alpha, n_beta)] = 1.0
+    sig = h_apply(n_orb, h, eri, e_core, hf)
+    eps = fock_diagonal(n_orb, h, eri, n_alpha, n_beta)
+    rows = np.asarray(ijab, dtype=np.int32).reshape(-1, 4)
+    t = np.zeros(len(rows))
+    num = np.zeros(len(rows))
+    for k, (i, j, a, b) in enumerate(rows):
+        phi = apply_generator(n, rows[k], hf)
+        num[k] = np.vdot(phi, sig).real
+        den = eps[i] - eps[a] + ((eps[j] - eps[b]) if j >= 0 else 0.0)
+        t[k] = num[k] / den
+    return t, num
+
+
+def magnitude_order(ijab, t):
+    """Magnitude ordering of the cluster operators (Section 2.3): rows by
+    decreasing |t|, equal magnitudes in list order.  Returns (rows, perm)
+    with rows = ijab[perm]."""
+    rows = np.asarray(ijab, dtype=np.int32).reshape(-1, 4)
+    mag = np.abs(np.asarray(t, dtype=np.float64))
+    perm = sorted(range(len(rows)), key=lambda k: (-mag[k], k))
+    perm = np.array(perm, dtype=np.int64)
+    return rows[perm], perm
+
+
+def trotter_extrapolate(Ms, Es):
+    """Least-squares fit of E(M) = alpha (1/M)^beta + gamma (Section 3.2,
+    Fig. 3) by scipy.optimize.curve_fit (Levenberg-Marquardt).
+    Returns (alpha, beta, gamma); gamma estimates the Trotter-free energy."""
+    import scipy.optimize
+    x = 1.0 / np.asarray(Ms, dtype=np.float64)
+    E = np.asarray(Es, dtype=np.float64)
+
+    def model(x, a, b, g):
+        return a * x ** b + g
+
+    p0 = (E[0] - E[-1] if E[0] != E[-1] else 1.0, 2.0, E[-1])
+    popt, _ = scipy.optimize.curve_fit(model, x, E, p0=p0, maxfev=100000,
+                                       xtol=1e-15, ftol=1e-15, gtol=1e-15)
+    return float(popt[0]), float(popt[1]), float(popt[2])
