@@ -10,7 +10,8 @@ The arithmetic lives in ``uccsd_oracle.c`` (ladder operators on occupation
 bit strings; Eq. 2 literally and by Slater-Condon rules; Eq. 4 generators;
 Eq. 5/6 schedules; adjoint gradient).  This module adds the list builders,
 the dense-matrix helpers (FCI by numpy.linalg.eigh, Trotter-free energies by
-scipy.linalg.expm), the magnitude ordering of Section 2.3 with first-order
+scipy.linalg.expm on the full space and by scipy.sparse.linalg.expm_multiply
+on the electron sector), the magnitude ordering of Section 2.3 with first-order
 amplitudes, the Trotter-error extrapolation of Section 3.2 and ctypes
 marshalling.
 
@@ -59,6 +60,9 @@ def _load():
                                            dp, dp, dp, dp]
         lib.oracle_sector_size.argtypes = [c_int, c_int, c_int, ctypes.POINTER(ctypes.c_int64)]
         lib.oracle_num_threads.restype = c_int
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.oracle_generator_sum_sector.argtypes = [c_int, c_int, c_int, c_int, ip, dp,
+                                                    ctypes.c_int64, i64p, i64p, dp, i64p]
         _lib = lib
     return _lib
 
@@ -362,3 +366,49 @@ def trotter_extrapolate(Ms, Es):
     popt, _ = scipy.optimize.curve_fit(model, x, E, p0=p0, maxfev=100000,
                                        xtol=1e-15, ftol=1e-15, gtol=1e-15)
     return float(popt[0]), float(popt[1]), float(popt[2])
+
+
+# ---------------------------------------------------------------------------
+# Trotter-free ansatz exp(T - T^dag)|HF> (Eq. 3) on the electron sector
+# ---------------------------------------------------------------------------
+def generator_sum_sector(n_qubits, n_alpha, n_beta, ijab, theta):
+    """A = sum_k theta_k G_k as a scipy.sparse CSC matrix on the sector basis
+    (ascending basis states, the order of sector_basis), built column by
+    column from the ladder operators."""
+    import scipy.sparse
+    lib = _load()
+    ijab = np.ascontiguousarray(ijab, dtype=np.int32).reshape(-1, 4)
+    theta = np.ascontiguousarray(theta, dtype=np.float64).reshape(ijab.shape[0])
+    dim = sector_size(n_qubits, n_alpha, n_beta)
+    nnz = ctypes.c_int64(0)
+    col = np.zeros(dim + 1, dtype=np.int64)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    _check(lib.oracle_generator_sum_sector(n_qubits, n_alpha, n_beta, ijab.shape[0], _ip(ijab),
+                                           _dp(theta), 0, col.ctypes.data_as(i64p), None, None,
+                                           ctypes.byref(nnz)), "generator_sum_sector")
+    row = np.zeros(max(nnz.value, 1), dtype=np.int64)
+    val = np.zeros(max(nnz.value, 1))
+    _check(lib.oracle_generator_sum_sector(n_qubits, n_alpha, n_beta, ijab.shape[0], _ip(ijab),
+                                           _dp(theta), nnz.value, col.ctypes.data_as(i64p),
+                                           row.ctypes.data_as(i64p), _dp(val),
+                                           ctypes.byref(nnz)), "generator_sum_sector")
+    n = nnz.value
+    return scipy.sparse.csc_matrix((val[:n], row[:n], col), shape=(dim, dim))
+
+
+def trotter_free_energy_sector(n_orb, h, eri, e_core, n_alpha, n_beta, ijab, theta):
+    """E of exp(sum_k theta_k G_k)|HF> on the sector by
+    scipy.sparse.linalg.expm_multiply, the routine named for the paper's
+    Trotter-free reference (Section 3.2); H acts by Slater-Condon rules.
+    Returns (E, psi) with psi the full 2^n vector."""
+    import scipy.sparse.linalg
+    n = 2 * n_orb
+    A = generator_sum_sector(n, n_alpha, n_beta, ijab, theta)
+    basis = sector_basis(n, n_alpha, n_beta)
+    e0 = np.zeros(len(basis))
+    e0[int(np.searchsorted(basis, hf_index(n_alpha, n_beta)))] = 1.0
+    v = scipy.sparse.linalg.expm_multiply(A, e0)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[basis] = v
+    sig = h_apply(n_orb, h, eri, e_core, psi)
+    return float(np.vdot(psi, sig).real), psi

@@ -480,3 +480,78 @@ int oracle_num_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Sum of generators A = sum_k theta_k G_k (Eq. 4, G = tau - tau^dag) as a
+ * sparse matrix on the (n_alpha, n_beta) sector basis (ascending basis
+ * states), one column per basis state, each entry taken from the ladder
+ * operators acting on that single state.  This is the exponent of the
+ * Trotter-free ansatz exp(T - T^dag)|HF> of Eq. 3.
+ * Outputs: col_ptr[dim + 1]; row[nnz] (row positions in the sector list);
+ * val[nnz].  With cap < required nnz nothing but *nnz_out is written.
+ * ---------------------------------------------------------------------- */
+static int64_t sector_pos(const uint64_t *lst, int64_t cnt, uint64_t y) {
+    int64_t lo = 0, hi = cnt - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (lst[mid] == y) return mid;
+        if (lst[mid] < y) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+}
+
+int oracle_generator_sum_sector(int n_qubits, int n_alpha, int n_beta, int K, const int32_t *ijab,
+                                const double *theta, int64_t cap, int64_t *col_ptr, int64_t *row,
+                                double *val, int64_t *nnz_out) {
+    if (n_qubits < 1 || n_qubits > 30 || K < 0 || check_excitations(n_qubits, K, ijab))
+        return ORACLE_ERR_ARG;
+    uint64_t *lst = NULL;
+    int64_t cnt = sector_list(n_qubits, n_alpha, n_beta, &lst);
+    if (cnt < 0) return ORACLE_ERR_NOMEM;
+    int64_t nnz = 0;
+    int bad = 0;
+    for (int pass = 0; pass < 2 && !bad; ++pass) {
+        if (pass == 1 && nnz > cap) break;
+        int64_t w = 0;
+        for (int64_t c = 0; c < cnt; ++c) {
+            if (pass == 1) col_ptr[c] = w;
+            for (int k = 0; k < K; ++k) {
+                const int32_t *e = ijab + 4 * k;
+                int tl[4], tdg[4], ul[4], udg[4], len;
+                if (e[1] < 0) {
+                    len = 2;
+                    tl[0] = e[2]; tdg[0] = 1; tl[1] = e[0]; tdg[1] = 0;
+                    ul[0] = e[0]; udg[0] = 1; ul[1] = e[2]; udg[1] = 0;
+                } else {
+                    len = 4;
+                    tl[0] = e[2]; tdg[0] = 1; tl[1] = e[3]; tdg[1] = 1;
+                    tl[2] = e[1]; tdg[2] = 0; tl[3] = e[0]; tdg[3] = 0;
+                    ul[0] = e[0]; udg[0] = 1; ul[1] = e[1]; udg[1] = 1;
+                    ul[2] = e[3]; udg[2] = 0; ul[3] = e[2]; udg[3] = 0;
+                }
+                uint64_t y;
+                int s = apply_ladder_string(len, tl, tdg, lst[c], &y);
+                double coef = theta[k];
+                if (!s) {
+                    s = apply_ladder_string(len, ul, udg, lst[c], &y);
+                    coef = -theta[k];
+                }
+                if (!s) continue;
+                if (pass == 1) {
+                    int64_t r = sector_pos(lst, cnt, y);
+                    if (r < 0) { bad = 1; break; }
+                    row[w] = r;
+                    val[w] = s * coef;
+                }
+                ++w;
+            }
+            if (bad) break;
+        }
+        if (pass == 0) nnz = w;
+        else col_ptr[cnt] = w;
+    }
+    free(lst);
+    if (bad) return ORACLE_ERR_SECTOR;
+    *nnz_out = nnz;
+    return ORACLE_OK;
+}

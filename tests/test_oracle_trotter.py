@@ -94,3 +94,72 @@ def test_magnitude_order_by_brute_force(oracle_mod):
     out, perm = oracle_mod.magnitude_order(rows, t)
     assert list(perm) == [5, 1, 2, 6, 0, 4, 3]  # |t| descending, ties in list order
     assert np.array_equal(out, rows[perm])
+
+
+@pytest.mark.parametrize("order,beta", [(1, 1.0), (2, 2.0)])
+def test_fixed_theta_trotter_error_has_the_product_formula_order(oracle_mod, order, beta):
+    # at fixed theta the first-order product (Eq. 5) converges as 1/M and the
+    # symmetric second-order one (Eq. 6) as 1/M^2 to exp(sum theta G)|HF>;
+    # the fit's gamma lands far closer to that limit than E(M = 5) does
+    w = synth.workload("8q")
+    ex = oracle_mod.excitations(4, 2, 2)
+    th = synth.theta_normal(len(ex), 0.05, 1000)
+    E_free, _ = oracle_mod.trotter_free_energy(4, w["h"], w["eri"], 0.0, 2, 2, ex, th)
+    Ms = [1, 2, 3, 4, 5]
+    Es = [oracle_mod.energy_grad(4, w["h"], w["eri"], 0.0, 2, 2, ex, th, order=order, M=M,
+                                 grad=False)[0] for M in Ms]
+    a, b, c = oracle_mod.trotter_extrapolate(Ms, Es)
+    assert abs(b - beta) < 0.1 * beta
+    assert abs(c - E_free) < 0.1 * abs(Es[-1] - E_free)
+
+
+# --- Trotter-free ansatz on the sector (Eq. 3, Section 3.2's expm_multiply reference) ---
+
+def test_sector_generator_sum_is_the_dense_sum_restricted_to_the_sector(oracle_mod):
+    ex = oracle_mod.excitations(4, 2, 2)
+    th = synth.theta_normal(len(ex), 0.3, 77)
+    A = oracle_mod.generator_sum_sector(8, 2, 2, ex, th).toarray()
+    dense = sum(th[k] * oracle_mod.generator_matrix(8, ex[k]) for k in range(len(ex)))
+    basis = oracle_mod.sector_basis(8, 2, 2)
+    assert np.array_equal(A, dense[np.ix_(basis, basis)])
+    assert np.array_equal(A, -A.T)  # real antisymmetric: exp(A) is orthogonal
+
+
+def test_sector_trotter_free_energy_equals_dense_expm(oracle_mod):
+    w = synth.workload("8q")
+    ex = oracle_mod.excitations(4, 2, 2)
+    th = synth.theta_normal(len(ex), 0.3, 77)
+    E1, p1 = oracle_mod.trotter_free_energy_sector(4, w["h"], w["eri"], 0.0, 2, 2, ex, th)
+    E2, p2 = oracle_mod.trotter_free_energy(4, w["h"], w["eri"], 0.0, 2, 2, ex, th)
+    assert abs(E1 - E2) < 1e-12 and np.max(np.abs(p1 - p2)) < 1e-13
+    assert abs(np.linalg.norm(p1) - 1.0) < 1e-13
+
+
+def test_trotter_free_equals_trotter_for_commuting_or_single_generators(oracle_mod):
+    w = synth.workload("12q")
+    ex = oracle_mod.excitations(6, 3, 3)
+    # generators on disjoint spin orbitals commute: the product is exact
+    used, pick = set(), []
+    for k, r in enumerate(ex):
+        q = {int(v) for v in r if v >= 0}
+        if not q & used:
+            used |= q
+            pick.append(k)
+    sub = ex[pick]
+    assert len(sub) >= 2
+    for rows in (sub, ex[5:6], ex[40:41]):
+        th = synth.theta_normal(len(rows), 0.4, 5)
+        Ef, _ = oracle_mod.trotter_free_energy_sector(6, w["h"], w["eri"], 0.0, 3, 3, rows, th)
+        Et = oracle_mod.energy_grad(6, w["h"], w["eri"], 0.0, 3, 3, rows, th, grad=False)[0]
+        assert abs(Ef - Et) < 1e-12
+
+
+def test_trotter_energies_converge_to_the_trotter_free_energy(oracle_mod):
+    w = synth.workload("12q")
+    ex = oracle_mod.excitations(6, 3, 3)
+    th = synth.theta_normal(len(ex), 0.05, 1001)
+    Ef, _ = oracle_mod.trotter_free_energy_sector(6, w["h"], w["eri"], 0.0, 3, 3, ex, th)
+    e = [abs(oracle_mod.energy_grad(6, w["h"], w["eri"], 0.0, 3, 3, ex, th, M=M, grad=False)[0] - Ef)
+         for M in (1, 4, 16)]
+    assert e[1] < e[0] / 3 and e[2] < e[1] / 3
+    assert Ef >= oracle_mod.fci_energy(6, w["h"], w["eri"], 0.0, 3, 3) - 1e-12
