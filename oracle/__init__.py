@@ -412,3 +412,30 @@ def trotter_free_energy_sector(n_orb, h, eri, e_core, n_alpha, n_beta, ijab, the
     psi[basis] = v
     sig = h_apply(n_orb, h, eri, e_core, psi)
     return float(np.vdot(psi, sig).real), psi
+
+
+def trotter_free_energy_grad_sector(n_orb, h, eri, e_core, n_alpha, n_beta, ijab, theta):
+    """E and gradient of exp(A)|HF>, A = sum_k theta_k G_k, on the sector:
+    dE/dtheta_k = 2 <H psi| L(A, G_k) |HF> with L the Frechet derivative of
+    the matrix exponential (scipy.linalg.expm_frechet).  Dense sector
+    matrices: small sectors only.  Returns (E, g)."""
+    import scipy.linalg
+    n = 2 * n_orb
+    rows = np.asarray(ijab, dtype=np.int32).reshape(-1, 4)
+    theta = np.asarray(theta, dtype=np.float64).reshape(len(rows))
+    A = generator_sum_sector(n, n_alpha, n_beta, rows, theta).toarray()
+    basis = sector_basis(n, n_alpha, n_beta)
+    e0 = np.zeros(len(basis))
+    e0[int(np.searchsorted(basis, hf_index(n_alpha, n_beta)))] = 1.0
+    v = scipy.linalg.expm(A) @ e0
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[basis] = v
+    sig = h_apply(n_orb, h, eri, e_core, psi)
+    E = float(np.vdot(psi, sig).real)
+    s = sig[basis].real
+    g = np.zeros(len(rows))
+    for k in range(len(rows)):
+        Gk = generator_sum_sector(n, n_alpha, n_beta, rows[k:k + 1], [1.0]).toarray()
+        L = scipy.linalg.expm_frechet(A, Gk, compute_expm=False)
+        g[k] = 2.0 * s @ (L @ e0)
+    return E, g

@@ -163,3 +163,36 @@ def test_trotter_energies_converge_to_the_trotter_free_energy(oracle_mod):
          for M in (1, 4, 16)]
     assert e[1] < e[0] / 3 and e[2] < e[1] / 3
     assert Ef >= oracle_mod.fci_energy(6, w["h"], w["eri"], 0.0, 3, 3) - 1e-12
+
+
+def test_trotter_free_gradient_matches_central_differences(oracle_mod):
+    w = synth.workload("8q")
+    ex = oracle_mod.excitations(4, 2, 2)
+    th = synth.theta_normal(len(ex), 0.3, 77)
+    E, g = oracle_mod.trotter_free_energy_grad_sector(4, w["h"], w["eri"], 0.0, 2, 2, ex, th)
+    E1, _ = oracle_mod.trotter_free_energy_sector(4, w["h"], w["eri"], 0.0, 2, 2, ex, th)
+    assert abs(E - E1) < 1e-12
+    hstep = 1e-5
+    for k in range(len(ex)):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += hstep
+        tm[k] -= hstep
+        ep = oracle_mod.trotter_free_energy_sector(4, w["h"], w["eri"], 0.0, 2, 2, ex, tp)[0]
+        em = oracle_mod.trotter_free_energy_sector(4, w["h"], w["eri"], 0.0, 2, 2, ex, tm)[0]
+        assert abs((ep - em) / (2 * hstep) - g[k]) < 1e-8
+
+
+def test_trotter_free_gradient_equals_trotter_gradient_for_commuting_generators(oracle_mod):
+    w = synth.workload("12q")
+    ex = oracle_mod.excitations(6, 3, 3)
+    used, pick = set(), []
+    for k, r in enumerate(ex):
+        q = {int(v) for v in r if v >= 0}
+        if not q & used:
+            used |= q
+            pick.append(k)
+    sub = ex[pick]
+    th = synth.theta_normal(len(sub), 0.4, 5)
+    E, g = oracle_mod.trotter_free_energy_grad_sector(6, w["h"], w["eri"], 0.0, 3, 3, sub, th)
+    Et, gt = oracle_mod.energy_grad(6, w["h"], w["eri"], 0.0, 3, 3, sub, th)
+    assert abs(E - Et) < 1e-12 and np.max(np.abs(g - gt)) < 1e-12
