@@ -242,6 +242,70 @@ uccsd_status uccsd_pauli_terms(int n_orb, const double *h, const double *eri, do
                                uint32_t *xmask, uint32_t *zmask, double *coef, int cap,
                                int *n_out);
 
+/* Energy of the Trotter-free ansatz (Eq. 3), the reference of Section 3.2
+ * (the paper computes it with SciPy's expm_multiply):
+ *   |Psi> = exp(sum_k theta_k G_k) |HF>,   E = <Psi|H|Psi>,
+ * for the context's excitation list (its order, trotter_order and n_slices
+ * do not enter).  exp is a truncated Taylor series on the device in s steps
+ * of m terms, chosen from the bound ||sum theta_k G_k|| <= sum |theta_k| so
+ * that the truncation error of the state stays below the state precision's
+ * unit roundoff (2^-53 FP64, 2^-24 FP32 state); cost s*m generator-sum
+ * passes, about sum |theta_k| * 20.  theta: K doubles on the host
+ * (theta_on_device = 0) or the device (1; read back to the host for the
+ * step choice); E: one double, same residency.  Synchronises `stream`.
+ * Afterwards uccsd_get_state(ctx, 0, ...) returns |Psi>.  Errors:
+ * UCCSD_ERR_STATE before set_excitations, UCCSD_ERR_ARG for null or non-
+ * finite theta; uses two extra state vectors of device memory (allocated on
+ * first use, counted against the HBM budget: UCCSD_ERR_BUDGET). */
+uccsd_status uccsd_energy_trotter_free(uccsd_ctx *ctx, const double *theta, int theta_on_device,
+                                       double *E, void *stream);
+
+/* Energy and gradient of the Trotter-free ansatz (see uccsd_energy_trotter_free).
+ * The gradient is the Duhamel integral
+ *   dE/dtheta_k = 2 int_0^1 Re <lambda(tau)|G_k|phi(tau)> dtau,
+ *   phi(tau) = exp(tau A)|HF>,  lambda(tau) = exp(tau A) exp(-A) (H - s)|Psi>,
+ * A = sum_k theta_k G_k, by Gauss-Legendre quadrature with the node count
+ * chosen from a derivative bound of the integrand; cost about four times
+ * the energy's.  grad: K doubles, same residency as theta.  Afterwards the
+ * device state is not |Psi> (uccsd_get_state returns UCCSD_ERR_STATE). */
+uccsd_status uccsd_energy_grad_trotter_free(uccsd_ctx *ctx, const double *theta, int theta_on_device,
+                                            double *E, double *grad, void *stream);
+
+/* ---- Trotter-schedule helpers (Section 2.3 ordering; Section 3.2 extrapolation) ---- */
+
+/* First-order (Moller-Plesset) amplitude of every excitation of the context's
+ * list, the magnitudes by which Section 2.3 orders the cluster operators
+ * (magnitude ordering after Tranter et al.):
+ *   t_k = <HF|H tau_k|HF> / (eps_i + eps_j - eps_a - eps_b)   (singles: eps_i - eps_a)
+ * with eps the Fock diagonal of the reference determinant.  The numerator is
+ * half the adjoint gradient at theta = 0, computed on the device by one
+ * energy-and-gradient evaluation on `stream` (the call synchronises it); the
+ * denominators come from the diagonal of H on the host.  t: host array of K
+ * doubles, in list order.  Requires uccsd_set_excitations.  Errors:
+ * UCCSD_ERR_STATE before set_excitations, UCCSD_ERR_ARG for a null t or a
+ * denominator of magnitude <= 1e-12.  In UCCSD_FP32_STATE contexts the
+ * numerators carry FP32 state rounding (relative error about 1e-6). */
+uccsd_status uccsd_mp1_amplitudes(uccsd_ctx *ctx, double *t, void *stream);
+
+/* Host-only: magnitude ordering (Section 2.3).  Writes the K rows of ijab
+ * (K x 4 int32, the layout of uccsd_set_excitations) to ijab_out in order of
+ * decreasing |t[k]|, rows of equal |t| in their input order (a stable sort),
+ * and perm[k] = the input index of output row k (perm may be NULL).  ijab_out
+ * may alias ijab.  The gradient of a context built from ijab_out is in the
+ * output order: grad_in[perm[k]] = grad_out[k].  Errors: UCCSD_ERR_ARG for
+ * K < 0, null arrays with K > 0, or a non-finite t. */
+uccsd_status uccsd_magnitude_order(int K, const int32_t *ijab, const double *t, int32_t *ijab_out,
+                                   int32_t *perm);
+
+/* Host-only: Trotter-error extrapolation (Section 3.2, Fig. 3).  Least-
+ * squares fit of E(M) = alpha (1/M)^beta + gamma to n energies E[m] at slice
+ * counts M[m] (>= 1, at least 3 distinct values); out[0..2] = alpha, beta,
+ * gamma, where gamma estimates the Trotter-free energy.  beta is searched in
+ * [1e-3, 64] (variable projection: alpha and gamma solved exactly for each
+ * beta).  Errors: UCCSD_ERR_ARG for n < 3, M < 1, fewer than 3 distinct M,
+ * non-finite E or null arrays. */
+uccsd_status uccsd_trotter_extrapolate(int n, const int *M, const double *E, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,8 @@ EXPORTS = [
     "uccsd_set_excitations", "uccsd_set_batch", "uccsd_energy", "uccsd_energy_grad",
     "uccsd_energy_grad_batch", "uccsd_get_state", "uccsd_info", "uccsd_hamiltonian_stats",
     "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile", "uccsd_expectation_noalloc",
-    "uccsd_capture", "uccsd_replay",
+    "uccsd_capture", "uccsd_replay", "uccsd_mp1_amplitudes", "uccsd_magnitude_order",
+    "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -102,6 +103,11 @@ def lib():
         L.uccsd_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
                                         ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_mp1_amplitudes.argtypes = [vp, f64p, vp]
+        L.uccsd_energy_trotter_free.argtypes = [vp, dp, ip, dp, vp]
+        L.uccsd_energy_grad_trotter_free.argtypes = [vp, dp, ip, dp, dp, vp]
+        L.uccsd_magnitude_order.argtypes = [ip, i32p, f64p, i32p, i32p]
+        L.uccsd_trotter_extrapolate.argtypes = [ip, ctypes.POINTER(ctypes.c_int), f64p, f64p]
         _lib = L
     return _lib
 
@@ -164,6 +170,31 @@ def pauli_terms(n_orb, h, eri, e_core=0.0):
     if st:
         raise UCCSDError(st, "pauli_terms")
     return x, z, c
+
+
+def magnitude_order(ijab, t):
+    """Rows of ijab by decreasing |t| (stable); returns (rows, perm) with
+    rows = ijab[perm]."""
+    ijab = np.ascontiguousarray(ijab, dtype=np.int32).reshape(-1, 4)
+    t = _c64(t).reshape(ijab.shape[0])
+    out = np.zeros_like(ijab)
+    perm = np.zeros(ijab.shape[0], dtype=np.int32)
+    st = lib().uccsd_magnitude_order(ijab.shape[0], _i32p(ijab), _f64p(t), _i32p(out), _i32p(perm))
+    if st:
+        raise UCCSDError(st, "magnitude_order")
+    return out, perm
+
+
+def trotter_extrapolate(Ms, Es):
+    """Fit E(M) = alpha (1/M)^beta + gamma; returns (alpha, beta, gamma)."""
+    M = np.ascontiguousarray(Ms, dtype=np.int32)
+    E = _c64(Es).reshape(M.shape[0])
+    out = np.zeros(3)
+    st = lib().uccsd_trotter_extrapolate(M.shape[0], M.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                         _f64p(E), _f64p(out))
+    if st:
+        raise UCCSDError(st, "trotter_extrapolate")
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 # ---------------------------------------------------------------------------
@@ -297,6 +328,33 @@ class Context:
         self._check(self._L.uccsd_energy_grad_batch(self._c, B, theta_ptr, 1 if on_device else 0,
                                                     E_ptr, grad_ptr, _stream_ptr(stream)),
                     "energy_grad_batch(ptr)")
+
+    def energy_trotter_free(self, theta, stream=None):
+        """E of exp(sum_k theta_k G_k)|HF> (no Trotterisation)."""
+        th = _c64(theta).reshape(self.K)
+        E = np.zeros(1)
+        self._check(self._L.uccsd_energy_trotter_free(self._c, th.ctypes.data, 0, E.ctypes.data,
+                                                      _stream_ptr(stream)), "energy_trotter_free")
+        return float(E[0])
+
+    def energy_grad_trotter_free(self, theta, stream=None):
+        """E and dE/dtheta of exp(sum_k theta_k G_k)|HF>."""
+        th = _c64(theta).reshape(self.K)
+        E = np.zeros(1)
+        g = np.zeros(max(self.K, 1))
+        self._check(self._L.uccsd_energy_grad_trotter_free(self._c, th.ctypes.data, 0,
+                                                           E.ctypes.data, g.ctypes.data,
+                                                           _stream_ptr(stream)),
+                    "energy_grad_trotter_free")
+        return float(E[0]), g[:self.K].copy()
+
+    def mp1_amplitudes(self, stream=None):
+        """First-order amplitudes of the context's list (one device
+        evaluation at theta = 0)."""
+        t = np.zeros(max(self.K, 1))
+        self._check(self._L.uccsd_mp1_amplitudes(self._c, _f64p(t), _stream_ptr(stream)),
+                    "mp1_amplitudes")
+        return t[:self.K].copy()
 
     def info(self):
         inf = Info()

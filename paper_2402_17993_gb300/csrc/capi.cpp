@@ -472,6 +472,281 @@ uccsd_status eval(uccsd_ctx *c, int B, const double *theta, int on_dev, double *
     return run_eval<double>(c, B, theta, on_dev, E, grad, s);
 }
 
+// Plan of the Trotter-free ansatz: every excitation once, two vectors (u
+// read, w accumulated) per shared-memory tile.
+uccsd_status prepare_trotter_free(uccsd_ctx *c) {
+    if (c->tf_ready) return UCCSD_OK;
+    const int n = c->n;
+    const size_t A = amp_bytes(c);
+    std::vector<int32_t> ident(c->K);
+    for (int k = 0; k < c->K; ++k) ident[k] = k;
+    c->tf = plan_sweep(n, c->n_alpha, c->n_beta, A, 2, kSweepBudget, c->exc, ident);
+    for (const CRunDev &r : c->tf.runs)
+        if ((size_t)r.max_entries * A * 2 > kSweepBudget)
+            return fail(c, UCCSD_ERR_ARG, "an excitation does not fit one shared-memory tile");
+    uccsd_status st;
+    COpDev *p1;
+    uint32_t *p4;
+    void *p;
+    if ((st = upload(c, "tf_ops", c->tf.ops, &p1))) return st;
+    if ((st = upload(c, "tf_spread", c->tf.spread, &p4))) return st;
+    c->tf_args = c->fwd_args;
+    c->tf_args.spread = p4;
+    if ((st = dalloc(c, "tf_coef", sizeof(double) * std::max(c->K, 1), &p))) return st;
+    for (const char *name : {"tf_u", "tf_w"}) {
+        if ((st = dalloc(c, name, state_bytes(c) * amp_bytes(c), &p))) return st;
+        // only electron-sector entries are ever written; the rest stays zero
+        cudaError_t e = cudaMemset(p, 0, state_bytes(c) * amp_bytes(c));
+        if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+    }
+    if ((st = dalloc(c, "tf_grad", sizeof(double) * std::max(c->K, 1), &p))) return st;
+    if ((st = dalloc(c, "tf_gpart", sizeof(double) * std::max(c->K, 1) * c->tf.max_tiles, &p)))
+        return st;
+    int32_t *p2;
+    if ((st = upload(c, "tf_op_tiles", c->tf.op_tiles, &p2))) return st;
+    c->tf_ready = true;
+    return UCCSD_OK;
+}
+
+// Truncated Taylor series of exp(A) v in s steps of m terms each.  A is real
+// antisymmetric with ||A||_2 <= b = sum_k |theta_k| (every G_k has norm 1),
+// so the remainder of one step of length h = b/s is at most
+// sum_{j>m} h^j/j! <= h^(m+1)/(m+1)! / (1 - h/(m+2)), and each exact step is
+// orthogonal, so s steps stay within s times that.  Steps are limited to
+// h <= 1 so that the partial sums never exceed e^h times the vector's norm
+// (rounding).  Returns the (s, m) of fewest products s*m within tol.
+void taylor_schedule(double b, double tol, int *s_out, int *m_out) {
+    *s_out = 1;
+    *m_out = 0;
+    if (!(b > 0.0)) return;
+    long long best = -1;
+    // log of the bound on s steps; decreasing in s for m >= 1
+    auto lbound = [&](long long s, int m) {
+        const double h = b / double(s);
+        return std::log(double(s)) + (m + 1) * std::log(h) - std::lgamma(m + 2.0) -
+               std::log1p(-h / (m + 2.0));
+    };
+    const long long s_lo = std::max<long long>(1, (long long)std::ceil(b));
+    for (int m = 1; m <= 60; ++m) {
+        long long lo = s_lo, hi = s_lo << 20;
+        if (lbound(hi, m) > std::log(tol)) continue;
+        while (lo < hi) {  // smallest s in [s_lo, hi] within tol
+            const long long mid = lo + (hi - lo) / 2;
+            if (lbound(mid, m) <= std::log(tol)) hi = mid;
+            else lo = mid + 1;
+        }
+        const long long s = lo;
+        if (best < 0 || s * m < best) {
+            best = s * m;
+            *s_out = int(s);
+            *m_out = m;
+        }
+    }
+}
+
+// Gauss-Legendre rule of q nodes on [0, 1] (Newton iteration on the
+// three-term recurrence of the Legendre polynomials).
+void gauss_legendre01(int q, std::vector<double> *x, std::vector<double> *w) {
+    x->assign(q, 0.0);
+    w->assign(q, 0.0);
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(3.14159265358979323846 * (i + 0.75) / (q + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 2; j <= q; ++j) {
+                const double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (q == 1) p0 = 1.0, p1 = z;
+            dp = q * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        (*x)[q - 1 - i] = 0.5 * (1.0 + z);
+        (*w)[q - 1 - i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Nodes of the gradient integral: |f^(r)| <= (2b)^r C for the integrand
+// f(tau) = <lambda(tau)|G_k|phi(tau)>, so the q-node Gauss-Legendre error on
+// [0, 1], (q!)^4 / ((2q + 1) ((2q)!)^3) max|f^(2q)|, is bounded; the
+// smallest q whose doubled bound stays within tol is used.
+int gauss_nodes(double b, double C, double tol) {
+    for (int q = 1; q < 400; ++q) {
+        const double lb = std::log(2.0 * std::max(C, 1e-300)) + 4.0 * std::lgamma(q + 1.0) +
+                          2.0 * q * std::log(std::max(2.0 * b, 1e-300)) - std::log(2.0 * q + 1.0) -
+                          3.0 * std::lgamma(2.0 * q + 1.0);
+        if (lb <= std::log(tol)) return q;
+    }
+    return 400;
+}
+
+// acc <- exp(sign * length * A) acc on the sector, A = sum_k coef_k G_k with
+// b = sum_k |coef_k|; t0, t1 are scratch vectors.
+template <typename R>
+uccsd_status taylor_apply(uccsd_ctx *c, const LaunchCfg &cfg, void *acc, void *t0, void *t1,
+                          const double *coef, double sign, double length, double b) {
+    int s = 1, m = 0;
+    taylor_schedule(b * length, sizeof(R) == 4 ? 0x1p-24 : 0x1p-53, &s, &m);
+    if (m == 0) return UCCSD_OK;
+    cudaError_t e;
+    if ((e = launch_sector_copy<R>(cfg, t0, acc, c->hsec)) != cudaSuccess)
+        return cuda_fail(c, e, "sector copy kernel");
+    ++c->launches;
+    void *bufs[2] = {t0, t1};
+    const COpDev *ops = static_cast<const COpDev *>(dptr(c, "tf_ops"));
+    // bufs[cur] holds the current term; the last term of a step is replaced
+    // by the step's result, which is the first term of the next step
+    int cur = 0;
+    for (int step = 0; step < s; ++step) {
+        for (int j = 1; j <= m; ++j) {
+            // u_j = sign * length * A u_{j-1} / (s j); acc += u_j
+            const double scale = sign * length / (double(s) * j);
+            for (size_t r = 0; r < c->tf.runs.size(); ++r) {
+                if ((e = launch_gen_apply<R>(cfg, bufs[cur], bufs[cur ^ 1], c->tf.runs[r], ops, coef,
+                                             scale, c->tf_args, r == 0 ? 1 : 0)) != cudaSuccess)
+                    return cuda_fail(c, e, "generator-sum kernel");
+                ++c->launches;
+            }
+            if ((e = launch_sector_axpy<R>(cfg, acc, bufs[cur ^ 1], j == m ? bufs[cur] : nullptr,
+                                           c->hsec)) != cudaSuccess)
+                return cuda_fail(c, e, "sector axpy kernel");
+            ++c->launches;
+            if (j < m) cur ^= 1;
+        }
+    }
+    return UCCSD_OK;
+}
+
+// E (and, with grad_host, dE/dtheta) of exp(A)|HF>, A = sum_k theta_k G_k.
+// Gradient (Duhamel): dE/dtheta_k = 2 int_0^1 Re <lambda(tau)|G_k|phi(tau)> dtau
+// with phi(tau) = exp(tau A)|HF> and lambda(tau) = exp(tau A) exp(-A) (H - s) psi.
+template <typename R>
+uccsd_status run_trotter_free(uccsd_ctx *c, const double *theta, double *E, double *grad_host,
+                              cudaStream_t stream) {
+    LaunchCfg cfg;
+    cfg.n = c->n;
+    cfg.N = state_bytes(c);
+    cfg.B = 1;
+    cfg.n_ops = c->K;
+    cfg.stream = stream;
+    cudaError_t e;
+    uccsd_status st;
+    double *coef = static_cast<double *>(dptr(c, "tf_coef"));
+    if (c->K > 0) {
+        e = cudaMemcpyAsync(coef, theta, sizeof(double) * c->K, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "theta upload");
+    }
+    double b = 0.0;
+    for (int k = 0; k < c->K; ++k) b += std::fabs(theta[k]);
+    void *psi = dptr(c, "psi"), *sig = dptr(c, "sig");
+    void *t0 = dptr(c, "tf_u"), *t1 = dptr(c, "tf_w");
+    if ((e = launch_sector_init<R>(cfg, psi, t0, c->hsec, c->hf)) != cudaSuccess)
+        return cuda_fail(c, e, "sector init kernel");
+    ++c->launches;
+    if ((st = taylor_apply<R>(c, cfg, psi, t0, t1, coef, 1.0, 1.0, b))) return st;
+    const DevHam<R> &H = *reinterpret_cast<const DevHam<R> *>(sizeof(R) == 4 ? (const void *)&c->hf32
+                                                                             : (const void *)&c->hf64);
+    double *Epart = static_cast<double *>(dptr(c, "Epart"));
+    if ((e = launch_happly<R>(cfg, psi, sig, c->LH, H, c->hsec, Epart, grad_host ? 1 : 0)) !=
+        cudaSuccess)
+        return cuda_fail(c, e, "H-apply kernel");
+    ++c->launches;
+    double *dE = static_cast<double *>(dptr(c, "E"));
+    if ((e = launch_reduce(cfg, Epart, n_tiles_h(c), static_cast<const double *>(dptr(c, "gpart")),
+                           n_tiles_a(c), static_cast<const int32_t *>(dptr(c, "op_tiles")), 0,
+                           static_cast<const int32_t *>(dptr(c, "k_ptr")),
+                           static_cast<const int32_t *>(dptr(c, "k_ops")),
+                           static_cast<const double *>(dptr(c, "op_scale")), c->shift,
+                           c->prec ? 1 : 0, dE, nullptr)) != cudaSuccess)
+        return cuda_fail(c, e, "reduce kernel");
+    ++c->launches;
+    double *dG = static_cast<double *>(dptr(c, "tf_grad"));
+    if (grad_host && c->K > 0) {
+        // lambda(0) = exp(-A) sigma, phi(0) = |HF>
+        if ((st = taylor_apply<R>(c, cfg, sig, t0, t1, coef, -1.0, 1.0, b))) return st;
+        if ((e = launch_sector_init<R>(cfg, psi, t0, c->hsec, c->hf)) != cudaSuccess)
+            return cuda_fail(c, e, "sector init kernel");
+        ++c->launches;
+        double C = std::fabs(c->shift);
+        for (const XZTerm &t : c->H.terms) C += std::fabs(t.c);
+        const int q = gauss_nodes(b, C, (sizeof(R) == 4 ? 1e-7 : 1e-14) * std::max(1.0, C));
+        std::vector<double> xq, wq;
+        gauss_legendre01(q, &xq, &wq);
+        const COpDev *ops = static_cast<const COpDev *>(dptr(c, "tf_ops"));
+        double *gp = static_cast<double *>(dptr(c, "tf_gpart"));
+        const int32_t *ot = static_cast<const int32_t *>(dptr(c, "tf_op_tiles"));
+        double tau = 0.0;
+        for (int i = 0; i < q; ++i) {
+            const double dt = xq[i] - tau;
+            tau = xq[i];
+            if ((st = taylor_apply<R>(c, cfg, psi, t0, t1, coef, 1.0, dt, b))) return st;
+            if ((st = taylor_apply<R>(c, cfg, sig, t0, t1, coef, 1.0, dt, b))) return st;
+            for (size_t r = 0; r < c->tf.runs.size(); ++r) {
+                if ((e = launch_gen_dot<R>(cfg, psi, sig, c->tf.runs[r], ops, c->tf_args, gp,
+                                           c->tf.max_tiles)) != cudaSuccess)
+                    return cuda_fail(c, e, "gradient-integrand kernel");
+                ++c->launches;
+            }
+            if ((e = launch_tf_grad_accum(cfg, gp, c->tf.max_tiles, ot, c->K, wq[i], dG, i == 0)) !=
+                cudaSuccess)
+                return cuda_fail(c, e, "gradient accumulation kernel");
+            ++c->launches;
+        }
+    }
+    e = cudaMemcpyAsync(E, dE, sizeof(double), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess && grad_host && c->K > 0)
+        e = cudaMemcpyAsync(grad_host, dG, sizeof(double) * c->K, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "result download");
+    c->state_valid = (grad_host == nullptr);
+    c->last_stream = stream;
+    return UCCSD_OK;
+}
+
+uccsd_status trotter_free(uccsd_ctx *c, const double *theta, int on_dev, double *E, double *grad,
+                          void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
+    if ((!theta && c->K > 0) || !E) return fail(c, UCCSD_ERR_ARG, "null theta or E");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<double> th(c->K);
+    if (c->K > 0) {
+        if (on_dev) {
+            e = cudaMemcpyAsync(th.data(), theta, sizeof(double) * c->K, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(c, e, "theta download");
+        } else {
+            std::memcpy(th.data(), theta, sizeof(double) * c->K);
+        }
+    }
+    if (!finite_all(th.data(), th.size())) return fail(c, UCCSD_ERR_ARG, "non-finite theta");
+    uccsd_status st = prepare_trotter_free(c);
+    if (st) return st;
+    double Eh = 0.0;
+    std::vector<double> gh(grad ? std::max(c->K, 1) : 0);
+    double *gp = grad ? gh.data() : nullptr;
+    st = c->prec ? run_trotter_free<float>(c, th.data(), &Eh, gp, s)
+                 : run_trotter_free<double>(c, th.data(), &Eh, gp, s);
+    if (st) return st;
+    if (on_dev) {
+        e = cudaMemcpyAsync(E, &Eh, sizeof(double), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && grad && c->K > 0)
+            e = cudaMemcpyAsync(grad, gh.data(), sizeof(double) * c->K, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(c, e, "result copy");
+    } else {
+        *E = Eh;
+        if (grad && c->K > 0) std::memcpy(grad, gh.data(), sizeof(double) * c->K);
+    }
+    return UCCSD_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -619,6 +894,8 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->order = trotter_order;
     c->M = n_slices;
     c->ijab.assign(ijab, ijab + 4 * size_t(K));
+    c->exc = exc;
+    c->tf_ready = false;
     build_schedule(K, trotter_order, n_slices, &c->op_k, &c->op_scale);
     const size_t A = c->prec ? 8 : 16;
     c->fwd = plan_sweep(n, c->n_alpha, c->n_beta, A, 1, kSweepBudget, exc, c->op_k);
@@ -800,6 +1077,57 @@ uccsd_status uccsd_get_profile(const uccsd_ctx *c, uccsd_profile_t *out) {
     if (!c || !out) return UCCSD_ERR_ARG;
     *out = c->prof;
     return UCCSD_OK;
+}
+
+uccsd_status uccsd_mp1_amplitudes(uccsd_ctx *c, double *t, void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
+    const int K = c->K;
+    if (K == 0) return UCCSD_OK;
+    if (!t) return fail(c, UCCSD_ERR_ARG, "null amplitude output");
+    // Numerators: at theta = 0 every factor is the identity, so
+    // dE/dtheta_k = 2 <HF|H tau_k|HF> (tau_k^dag annihilates |HF>).
+    std::vector<double> zero(K, 0.0), g(K, 0.0);
+    double E = 0.0;
+    uccsd_status st = eval(c, 1, zero.data(), 0, &E, g.data(), stream);
+    if (st) return st;
+    // Orbital energies (Moller-Plesset partitioning): the Fock diagonal of the
+    // reference, read off the diagonal quadratic form of H,
+    // eps_P = d_P + sum_{I in HF, I != P} d_{PI}.
+    const int n = c->n;
+    std::vector<double> eps(n, 0.0);
+    if (c->H.has_diag) {
+        for (int P = 0; P < n; ++P) {
+            double v = c->H.diag_a[P];
+            for (int I = 0; I < n; ++I) {
+                if (I == P || !((c->hf >> I) & 1u)) continue;
+                v += c->H.diag_b[size_t(std::min(P, I)) * n + std::max(P, I)];
+            }
+            eps[P] = v;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        const int32_t *r = &c->ijab[4 * size_t(k)];
+        double den = eps[r[0]] - eps[r[2]];
+        if (r[1] >= 0) den += eps[r[1]] - eps[r[3]];
+        if (!(std::fabs(den) > 1e-12))
+            return fail(c, UCCSD_ERR_ARG, "excitation row " + std::to_string(k) +
+                                              " has a vanishing orbital-energy denominator");
+        t[k] = 0.5 * g[k] / den;
+    }
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_energy_trotter_free(uccsd_ctx *c, const double *theta, int on_dev, double *E,
+                                       void *stream) {
+    return trotter_free(c, theta, on_dev, E, nullptr, stream);
+}
+
+uccsd_status uccsd_energy_grad_trotter_free(uccsd_ctx *c, const double *theta, int on_dev, double *E,
+                                            double *grad, void *stream) {
+    if (c && c->K > 0 && !grad) return fail(c, UCCSD_ERR_ARG, "null grad");
+    return trotter_free(c, theta, on_dev, E, grad, stream);
 }
 
 uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *eri, double e_core,

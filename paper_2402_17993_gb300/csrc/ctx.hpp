@@ -41,6 +41,11 @@ struct uccsd_ctx {
     std::vector<double> op_scale;
     uccsd::SweepPlan fwd, adj;
     uccsd::SweepArgs fwd_args, adj_args;
+    std::vector<uccsd::CompiledExc> exc;  // list order
+    // Trotter-free ansatz: plan with every excitation once (built on first use)
+    uccsd::SweepPlan tf;
+    uccsd::SweepArgs tf_args;
+    bool tf_ready = false;
     int LH = uccsd::kHL;
     int B = 1;          // reserved slots
     bool state_valid = false;

@@ -84,6 +84,35 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
 template <typename R>
 cudaError_t launch_set_hf(const LaunchCfg &cfg, void *psi, uint32_t hf);
 
+// Trotter-free ansatz (Eq. 3): w (+)= scale * sum_k coef[k] G_k u over one
+// run of a plan holding each excitation once (first_run: w starts at zero).
+template <typename R>
+cudaError_t launch_gen_apply(const LaunchCfg &cfg, const void *u, void *w, const CRunDev &run,
+                             const COpDev *ops, const double *coef, double scale,
+                             const SweepArgs &sa, int first_run);
+// acc = u = |HF> on the electron sector (slot 0).
+template <typename R>
+cudaError_t launch_sector_init(const LaunchCfg &cfg, void *acc, void *u, const HSector &hs,
+                               uint32_t hf);
+// acc += w on the electron sector; u_out (may be null) = the new acc.
+template <typename R>
+cudaError_t launch_sector_axpy(const LaunchCfg &cfg, void *acc, const void *w, void *u_out,
+                               const HSector &hs);
+
+// Trotter-free gradient integrand: gpart[k][t] = tile-t partial of
+// Re <lam|G_k|phi> for the factors of one run (plan holding each excitation once).
+template <typename R>
+cudaError_t launch_gen_dot(const LaunchCfg &cfg, const void *phi, const void *lam,
+                           const CRunDev &run, const COpDev *ops, const SweepArgs &sa,
+                           double *gpart, int tile_stride);
+// g[k] = (init ? 0 : g[k]) + 2 weight sum_t gpart[k][t], t < op_tiles[k].
+cudaError_t launch_tf_grad_accum(const LaunchCfg &cfg, const double *gpart, int tile_stride,
+                                 const int32_t *op_tiles, int K, double weight, double *g,
+                                 int init);
+// dst = src on the electron sector.
+template <typename R>
+cudaError_t launch_sector_copy(const LaunchCfg &cfg, void *dst, const void *src, const HSector &hs);
+
 // Dynamic shared memory opt-in of the sweep kernels.
 cudaError_t configure_sweep_kernels(size_t max_smem);
 

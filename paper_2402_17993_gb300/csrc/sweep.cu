@@ -10,6 +10,7 @@
 // vectors (phi, lambda) and produces per-factor gradient partials.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "kernels.cuh"
@@ -371,6 +372,225 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     }
 }
 
+// Trotter-free ansatz (Eq. 3): w = scale * sum_k coef_k G_k u over the
+// factors of one run of a plan that holds every excitation once.  u is read
+// only; w is accumulated across the runs of the plan (the first run starts
+// from zero).  Per pair (x occupied side, x' partner) with G|x> = s|x'>:
+// w_x -= s c u_x', w_x' += s c u_x.
+template <typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS) gen_apply_kernel(
+    const V2<R> *__restrict__ u, V2<R> *__restrict__ w, size_t N, CRunDev run,
+    const COpDev *__restrict__ ops, const double *__restrict__ coef, double scale, SweepArgs sa,
+    int first_run) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileView v;
+    if (!make_view(run, sa, &v)) return;
+    V2<R> *tu = reinterpret_cast<V2<R> *>(smem_raw);
+    V2<R> *tw = tu + run.max_entries;
+    int2 *lists = reinterpret_cast<int2 *>(tw + run.max_entries);
+    const int lstride = run.max_da + run.max_db;
+    COpDev *sops;
+    const SweepArgs la = stage_tables(run, sa, ops, reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops);
+    __syncthreads();
+    make_view(run, la, &v);
+    const int D = v.Da * v.Db;
+    for (int e = threadIdx.x; e < D; e += blockDim.x) {
+        const uint32_t x = entry_index(v, e);
+        tu[e] = u[x];
+        V2<R> z;
+        z.x = (R)0;
+        z.y = (R)0;
+        tw[e] = first_run ? z : w[x];
+    }
+    const int nops = run.op_end - run.op_begin;
+    if (nops > 0) {
+        const PairSet p0 = pair_set(run, la, v, sops[0]);
+        build_sides(p0, v, sops[0], lists, lists + p0.Va);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int o = 0; o < nops; ++o) {
+        const COpDev &op = sops[o];
+        const PairSet p = pair_set(run, la, v, op);
+        int2 *A = lists + buf * lstride;
+        int2 *B = A + p.Va;
+        if (o + 1 < nops) {
+            const PairSet pn = pair_set(run, la, v, sops[o + 1]);
+            int2 *An = lists + (buf ^ 1) * lstride;
+            build_sides(pn, v, sops[o + 1], An, An + pn.Va);
+        }
+        const int P = p.Va * p.Vb;
+        if (P > 0) {
+            const double c0 = scale * coef[op.op_s0 & 0x7FFFFFFFu];
+            const R cc = (R)((op.op_s0 >> 31) ? -c0 : c0);
+            const int rpar = __popc(v.rest & op.par_rest) & 1;
+            const float inv = 1.0f / (float)p.Vb;
+            for (int j = threadIdx.x; j < P; j += blockDim.x) {
+                int ja, jb;
+                split_index(j, p.Vb, inv, &ja, &jb);
+                const int2 a2 = A[ja], b2 = B[jb];
+                const int e = (a2.x & 0x7FFFFFFF) + (b2.x & 0x7FFFFFFF);
+                const int e2 = a2.y + b2.y;
+                const int neg = ((((unsigned)(a2.x ^ b2.x)) >> 31) ^ rpar) & 1;
+                const R ss = neg ? -cc : cc;
+                const V2<R> u0 = tu[e], u1 = tu[e2];
+                V2<R> w0 = tw[e], w1 = tw[e2];
+                w0.x -= ss * u1.x;
+                w0.y -= ss * u1.y;
+                w1.x += ss * u0.x;
+                w1.y += ss * u0.y;
+                tw[e] = w0;
+                tw[e2] = w1;
+            }
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    for (int e = threadIdx.x; e < D; e += blockDim.x) w[entry_index(v, e)] = tw[e];
+}
+
+// Gradient integrand of the Trotter-free ansatz: per factor of one run and
+// per tile, the partial of Re <lambda|G_k|phi> (same pair formula as the
+// adjoint sweep, no rotation); tiles without sector entries write zero.
+template <typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS) gen_dot_kernel(
+    const V2<R> *__restrict__ phi, const V2<R> *__restrict__ lam, size_t N, CRunDev run,
+    const COpDev *__restrict__ ops, SweepArgs sa, double *__restrict__ gpart, int tile_stride) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double wring[2][32];
+    TileView v;
+    if (!make_view(run, sa, &v)) {
+        for (int o = run.op_begin + threadIdx.x; o < run.op_end; o += blockDim.x)
+            gpart[(size_t)(ops[o].op_s0 & 0x7FFFFFFFu) * tile_stride + blockIdx.x] = 0.0;
+        return;
+    }
+    V2<R> *tp = reinterpret_cast<V2<R> *>(smem_raw);
+    V2<R> *tl = tp + run.max_entries;
+    int2 *lists = reinterpret_cast<int2 *>(tl + run.max_entries);
+    const int lstride = run.max_da + run.max_db;
+    COpDev *sops;
+    const SweepArgs la = stage_tables(run, sa, ops, reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops);
+    __syncthreads();
+    make_view(run, la, &v);
+    const int D = v.Da * v.Db;
+    const int nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < D; e += blockDim.x) {
+        const uint32_t x = entry_index(v, e);
+        tp[e] = phi[x];
+        tl[e] = lam[x];
+    }
+    const int nops = run.op_end - run.op_begin;
+    if (nops > 0) {
+        const PairSet p0 = pair_set(run, la, v, sops[0]);
+        build_sides(p0, v, sops[0], lists, lists + p0.Va);
+    }
+    __syncthreads();
+    int buf = 0;
+    for (int o = 0; o < nops; ++o) {
+        const COpDev &op = sops[o];
+        const PairSet p = pair_set(run, la, v, op);
+        int2 *A = lists + buf * lstride;
+        int2 *B = A + p.Va;
+        if (o + 1 < nops) {
+            const PairSet pn = pair_set(run, la, v, sops[o + 1]);
+            int2 *An = lists + (buf ^ 1) * lstride;
+            build_sides(pn, v, sops[o + 1], An, An + pn.Va);
+        }
+        const int P = p.Va * p.Vb;
+        const int opi = (int)(op.op_s0 & 0x7FFFFFFFu);
+        R part = (R)0;
+        if (P > 0) {
+            const int rpar = __popc(v.rest & op.par_rest) & 1;
+            const float inv = 1.0f / (float)p.Vb;
+            for (int j = threadIdx.x; j < P; j += blockDim.x) {
+                int ja, jb;
+                split_index(j, p.Vb, inv, &ja, &jb);
+                const int2 a2 = A[ja], b2 = B[jb];
+                const int e = (a2.x & 0x7FFFFFFF) + (b2.x & 0x7FFFFFFF);
+                const int e2 = a2.y + b2.y;
+                const bool neg = ((((unsigned)(a2.x ^ b2.x)) >> 31) ^ rpar) & 1;
+                const V2<R> fa = tp[e], fb = tp[e2];
+                const V2<R> lx = tl[e], ly = tl[e2];
+                // (G phi)_x = -s phi_x', (G phi)_x' = s phi_x
+                const R d = (ly.x * fa.x + ly.y * fa.y) - (lx.x * fb.x + lx.y * fb.y);
+                part += neg ? -d : d;
+            }
+        }
+        const double dp = (op.op_s0 >> 31) ? -(double)warp_sum(part) : (double)warp_sum(part);
+        const int rb = o & 1;
+        if (lane == 0) wring[rb][warp] = dp;
+        __syncthreads();
+        if (warp == 0) {
+            double s2 = (lane < nw) ? wring[rb][lane] : 0.0;
+            s2 = warp_sum<double>(s2);
+            if (lane == 0) gpart[(size_t)opi * tile_stride + blockIdx.x] = s2;
+        }
+        buf ^= 1;
+    }
+}
+
+// g[k] (+)= 2 weight sum_t gpart[k][t] over the op_tiles[k] tiles of factor
+// k, one warp per factor in a fixed order (deterministic).
+__global__ void tf_grad_accum_kernel(const double *__restrict__ gpart, int tile_stride,
+                                     const int32_t *__restrict__ op_tiles, int K, double weight,
+                                     double *__restrict__ g, int init) {
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= K) return;
+    double sum = 0.0;
+    for (int t = lane; t < op_tiles[k]; t += 32) sum += gpart[(size_t)k * tile_stride + t];
+    sum = warp_sum<double>(sum);
+    if (lane == 0) g[k] = (init ? 0.0 : g[k]) + 2.0 * weight * sum;
+}
+
+// Electron-sector element-wise steps of the Taylor series: x runs over the
+// sector entries (alpha string rows x beta string columns).
+__device__ __forceinline__ uint32_t sector_index(const HSector &hs, int e) {
+    const int ia = e / hs.Db;
+    const int ib = e - ia * hs.Db;
+    return hs.aspread[hs.astr[ia]] | hs.bspread[hs.bstr[ib]];
+}
+
+// acc = u = |HF> on the sector.
+template <typename R>
+__global__ void sector_init_kernel(V2<R> *acc, V2<R> *u, HSector hs, uint32_t hf) {
+    const int D = hs.Da * hs.Db;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += gridDim.x * blockDim.x) {
+        const uint32_t x = sector_index(hs, e);
+        V2<R> val;
+        val.x = (R)(x == hf ? 1 : 0);
+        val.y = (R)0;
+        acc[x] = val;
+        u[x] = val;
+    }
+}
+
+// dst = src on the sector.
+template <typename R>
+__global__ void sector_copy_kernel(V2<R> *dst, const V2<R> *src, HSector hs) {
+    const int D = hs.Da * hs.Db;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += gridDim.x * blockDim.x) {
+        const uint32_t x = sector_index(hs, e);
+        dst[x] = src[x];
+    }
+}
+
+// acc += w; if u_out, u_out = acc (the next Taylor step's first term).
+template <typename R>
+__global__ void sector_axpy_kernel(V2<R> *acc, const V2<R> *w, V2<R> *u_out, HSector hs) {
+    const int D = hs.Da * hs.Db;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < D; e += gridDim.x * blockDim.x) {
+        const uint32_t x = sector_index(hs, e);
+        V2<R> a = acc[x];
+        const V2<R> d = w[x];
+        a.x += d.x;
+        a.y += d.y;
+        acc[x] = a;
+        if (u_out) u_out[x] = a;
+    }
+}
+
 // |HF> in slot b when the schedule is empty.
 template <typename R>
 __global__ void set_hf_kernel(V2<R> *psi, size_t N, uint32_t hf) {
@@ -425,6 +645,81 @@ cudaError_t launch_set_hf(const LaunchCfg &cfg, void *psi, uint32_t hf) {
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_gen_apply(const LaunchCfg &cfg, const void *u, void *w, const CRunDev &run,
+                             const COpDev *ops, const double *coef, double scale,
+                             const SweepArgs &sa, int first_run) {
+    dim3 grid(run.n_tiles, 1);
+    const size_t smem = sweep_smem_bytes(run.max_entries, run.max_da, run.max_db, sizeof(V2<R>), 2,
+                                         run.op_end - run.op_begin, max(run.La, run.Lb));
+    const V2<R> *pu = static_cast<const V2<R> *>(u);
+    V2<R> *pw = static_cast<V2<R> *>(w);
+    if (run.max_entries >= kLargeTile)
+        gen_apply_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
+            pu, pw, cfg.N, run, ops, coef, scale, sa, first_run);
+    else
+        gen_apply_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
+            pu, pw, cfg.N, run, ops, coef, scale, sa, first_run);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_sector_init(const LaunchCfg &cfg, void *acc, void *u, const HSector &hs,
+                               uint32_t hf) {
+    const int D = hs.Da * hs.Db;
+    const int blocks = std::min((D + 255) / 256, 152 * 8);
+    sector_init_kernel<R><<<blocks, 256, 0, cfg.stream>>>(static_cast<V2<R> *>(acc),
+                                                          static_cast<V2<R> *>(u), hs, hf);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_sector_axpy(const LaunchCfg &cfg, void *acc, const void *w, void *u_out,
+                               const HSector &hs) {
+    const int D = hs.Da * hs.Db;
+    const int blocks = std::min((D + 255) / 256, 152 * 8);
+    sector_axpy_kernel<R><<<blocks, 256, 0, cfg.stream>>>(
+        static_cast<V2<R> *>(acc), static_cast<const V2<R> *>(w), static_cast<V2<R> *>(u_out), hs);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_gen_dot(const LaunchCfg &cfg, const void *phi, const void *lam,
+                           const CRunDev &run, const COpDev *ops, const SweepArgs &sa,
+                           double *gpart, int tile_stride) {
+    dim3 grid(run.n_tiles, 1);
+    const size_t smem = sweep_smem_bytes(run.max_entries, run.max_da, run.max_db, sizeof(V2<R>), 2,
+                                         run.op_end - run.op_begin, max(run.La, run.Lb));
+    const V2<R> *f = static_cast<const V2<R> *>(phi);
+    const V2<R> *l = static_cast<const V2<R> *>(lam);
+    if (run.max_entries >= kLargeTile)
+        gen_dot_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
+            f, l, cfg.N, run, ops, sa, gpart, tile_stride);
+    else
+        gen_dot_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
+            f, l, cfg.N, run, ops, sa, gpart, tile_stride);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tf_grad_accum(const LaunchCfg &cfg, const double *gpart, int tile_stride,
+                                 const int32_t *op_tiles, int K, double weight, double *g,
+                                 int init) {
+    if (K <= 0) return cudaSuccess;
+    const int warps = 8;
+    tf_grad_accum_kernel<<<(K + warps - 1) / warps, warps * 32, 0, cfg.stream>>>(
+        gpart, tile_stride, op_tiles, K, weight, g, init);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_sector_copy(const LaunchCfg &cfg, void *dst, const void *src, const HSector &hs) {
+    const int D = hs.Da * hs.Db;
+    const int blocks = std::min((D + 255) / 256, 152 * 8);
+    sector_copy_kernel<R><<<blocks, 256, 0, cfg.stream>>>(static_cast<V2<R> *>(dst),
+                                                          static_cast<const V2<R> *>(src), hs);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_sweep_kernels(size_t max_smem) {
     const int bytes = (int)max_smem;
     cudaError_t e = cudaSuccess;
@@ -438,6 +733,14 @@ cudaError_t configure_sweep_kernels(size_t max_smem) {
     UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<float, kSweepThreadsSmall>))
     UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<double, kSweepThreadsLarge>))
     UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<double, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((gen_apply_kernel<float, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((gen_apply_kernel<float, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((gen_apply_kernel<double, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((gen_apply_kernel<double, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((gen_dot_kernel<float, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((gen_dot_kernel<float, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((gen_dot_kernel<double, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((gen_dot_kernel<double, kSweepThreadsSmall>))
 #undef UCCSD_SWEEP_ATTR
     return e;
 }
@@ -449,7 +752,19 @@ cudaError_t configure_sweep_kernels(size_t max_smem) {
     template cudaError_t launch_adjoint_sweep<R>(const LaunchCfg &, void *, void *,            \
                                                  const CRunDev &, const COpDev *, const void *, \
                                                  const SweepArgs &, double *, int);            \
-    template cudaError_t launch_set_hf<R>(const LaunchCfg &, void *, uint32_t);
+    template cudaError_t launch_set_hf<R>(const LaunchCfg &, void *, uint32_t);                \
+    template cudaError_t launch_gen_apply<R>(const LaunchCfg &, const void *, void *,          \
+                                             const CRunDev &, const COpDev *, const double *,   \
+                                             double, const SweepArgs &, int);                   \
+    template cudaError_t launch_sector_init<R>(const LaunchCfg &, void *, void *,              \
+                                               const HSector &, uint32_t);                      \
+    template cudaError_t launch_sector_axpy<R>(const LaunchCfg &, void *, const void *, void *, \
+                                               const HSector &);                                \
+    template cudaError_t launch_gen_dot<R>(const LaunchCfg &, const void *, const void *,      \
+                                           const CRunDev &, const COpDev *, const SweepArgs &,  \
+                                           double *, int);                                      \
+    template cudaError_t launch_sector_copy<R>(const LaunchCfg &, void *, const void *,        \
+                                               const HSector &);
 UCCSD_SWEEP_INST(float)
 UCCSD_SWEEP_INST(double)
 #undef UCCSD_SWEEP_INST

@@ -108,3 +108,57 @@ def test_status_strings(uc):
     L = uc.lib()
     for code in range(7):
         assert L.uccsd_status_string(code)
+
+
+def test_magnitude_order_equals_oracle(uc, oracle_mod):
+    # Section 2.3 ordering: same permutation as the oracle, ties included
+    ex = oracle_mod.excitations(6, 3, 3)
+    rng = np.random.default_rng(3)
+    t = np.round(rng.normal(size=len(ex)), 1)  # rounding creates many ties, of both signs
+    rows, perm = uc.magnitude_order(ex, t)
+    want_rows, want_perm = oracle_mod.magnitude_order(ex, t)
+    assert np.array_equal(perm, want_perm)
+    assert np.array_equal(rows, want_rows)
+    # aliasing output and input is allowed
+    ex2 = np.ascontiguousarray(ex.copy())
+    st = uc.lib().uccsd_magnitude_order(len(ex2), uc._i32p(ex2), uc._f64p(t), uc._i32p(ex2), None)
+    assert st == 0 and np.array_equal(ex2, want_rows)
+
+
+def test_magnitude_order_rejects_bad_input(uc):
+    with pytest.raises(uc.UCCSDError):
+        uc.magnitude_order(np.zeros((2, 4), np.int32), np.array([1.0, np.nan]))
+    assert uc.lib().uccsd_magnitude_order(-1, None, None, None, None) == 1
+    rows, perm = uc.magnitude_order(np.zeros((0, 4), np.int32), np.zeros(0))
+    assert rows.shape == (0, 4) and perm.shape == (0,)
+
+
+def test_trotter_extrapolation_equals_oracle_on_table_s3(uc, oracle_mod):
+    import json
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "table_s3_trotter_fit.json")))
+    got = uc.trotter_extrapolate(g["M"], g["dE_kcal"])
+    want = oracle_mod.trotter_extrapolate(g["M"], g["dE_kcal"])
+    assert abs(got[0] - want[0]) < 1e-6 * abs(want[0])
+    assert abs(got[1] - want[1]) < 1e-6 * abs(want[1])
+    assert abs(got[2] - want[2]) < 1e-8
+    kc = g["kcal_per_hartree"]
+    assert abs(got[0] / kc - g["paper_fit"]["alpha_hartree"]) < 2e-6
+    assert abs(got[1] - g["paper_fit"]["beta"]) < 1e-3
+
+
+@pytest.mark.parametrize("alpha,beta,gamma", [(0.3, 1.0, -2.0), (-0.01, 2.0, 5.0),
+                                              (0.005396, 3.6466, -3.876244), (1e-6, 0.5, -75.0)])
+def test_trotter_extrapolation_recovers_exact_power_laws(uc, alpha, beta, gamma):
+    M = np.array([1, 2, 3, 4, 5, 6])
+    E = alpha * (1.0 / M) ** beta + gamma
+    a, b, c = uc.trotter_extrapolate(M, E)
+    assert abs(b - beta) < 1e-5 * beta
+    assert abs(a - alpha) < 1e-5 * abs(alpha)
+    assert abs(c - gamma) < 1e-9 * max(1.0, abs(alpha))
+
+
+def test_trotter_extrapolation_rejects_bad_input(uc):
+    for M, E in [([1, 2], [0.0, 1.0]), ([1, 1, 2], [0.0, 1.0, 2.0]), ([0, 1, 2], [1.0, 2.0, 3.0]),
+                 ([1, 2, 3], [1.0, np.inf, 3.0])]:
+        with pytest.raises(uc.UCCSDError):
+            uc.trotter_extrapolate(M, E)
