@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--layout", default="full", choices=["full", "sector"],
+                    help="state layout of the timed path (the sector layout is also timed "
+                         "beside the full one as a comparison)")
+    ap.add_argument("--no-layout-compare", action="store_true")
     ap.add_argument("--no-scaleup", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -277,8 +281,9 @@ def run_ours(args):
     amp_bytes = 8 if prec == uc.FP32_STATE else 16
     w = synth.workload("18q")
     B = args.batch
+    layout = uc.LAYOUT_SECTOR if args.layout == "sector" else uc.LAYOUT_FULL
     ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
-                          precision=prec, device=local, batch=B)
+                          precision=prec, device=local, batch=B, layout=layout)
     K = ctx.K
     th_host = np.stack([synth.theta_normal(K, 0.05, 1002 + b + 1000 * rank) for b in range(B)])
     theta = torch.tensor(th_host, device=dev, dtype=torch.float64)
@@ -344,6 +349,8 @@ def run_ours(args):
         "config": {"workload": "18q/10e UCCSD K=560 (seed 2, 16 Cholesky), batch 64 theta "
                                "~N(0,0.05), energy+adjoint gradient, M=1 first-order Trotter",
                    "state": "complex64 + FP64 reductions" if prec else "complex128",
+                   "layout": args.layout + (" (2^n vector per slot)" if args.layout == "full"
+                                            else " (electron-sector array per slot)"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "fwd_runs": info["n_fwd_runs"], "adj_runs": info["n_adj_runs"],
                    "groups": info["n_groups"], "terms": info["n_terms"]},
@@ -360,6 +367,8 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"12 of the 64 theta vectors ({dt:.1f} s, sector-restricted "
                                           "FP64 oracle, OpenMP)"}
+    if rank == 0 and not args.no_layout_compare and args.layout == "full":
+        line["sector_layout"] = layout_compare(uc, local, w, prec, B, th_host, args, flush)
     if rank == 0 and not args.no_scaleup:
         line["scaleup"] = scaleup_26q(uc, local)
     if rank == 0 and not args.no_serving:
@@ -371,15 +380,51 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def layout_compare(uc, device, w, prec, B, th_host, args, flush):
+    """The same timed loop with the electron-sector state layout (bitwise the
+    same results; a comparison beside the headline, which times the full
+    2^n layout)."""
+    import torch
+    ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
+                          precision=prec, device=device, batch=B, layout=uc.LAYOUT_SECTOR)
+    theta = torch.tensor(th_host, device="cuda", dtype=torch.float64)
+    E = torch.empty(B, device="cuda", dtype=torch.float64)
+    G = torch.empty(B, ctx.K, device="cuda", dtype=torch.float64)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ctx.energy_grad_device(theta, E, G, stream)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        evs[s][0].record(stream)
+        ctx.energy_grad_device(theta, E, G, stream)
+        evs[s][1].record(stream)
+    torch.cuda.synchronize()
+    total = sum(a.elapsed_time(b) for a, b in evs)
+    prof = ctx.profile()
+    out = {"value": B * args.steps / (total / 1e3), "unit": UNIT,
+           "ms_per_step": total / args.steps,
+           "family_ms": {f: prof["ms"][f] / max(1, prof["calls"]) for f in prof["ms"]},
+           "device_bytes": ctx.info()["device_bytes"]}
+    ctx.close()
+    return out
+
+
 def scaleup_26q(uc, device):
     import torch
     w = synth.workload("26q")
     gold_path = os.path.join(ROOT, "tests", "golden", "golden_26q.json")
     gold = json.load(open(gold_path)) if os.path.exists(gold_path) else None
     out = {}
-    for name, prec in (("fp32", uc.FP32_STATE), ("fp64", uc.FP64)):
+    for name, prec, layout in (("fp32", uc.FP32_STATE, uc.LAYOUT_FULL),
+                               ("fp64", uc.FP64, uc.LAYOUT_FULL),
+                               ("fp32_sector_layout", uc.FP32_STATE, uc.LAYOUT_SECTOR),
+                               ("fp64_sector_layout", uc.FP64, uc.LAYOUT_SECTOR)):
         ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"],
-                              w["n_beta"], precision=prec, device=device)
+                              w["n_beta"], precision=prec, device=device, layout=layout)
         th = torch.tensor(synth.theta_normal(ctx.K, 0.02, 1004), device="cuda",
                           dtype=torch.float64).unsqueeze(0)
         E = torch.empty(1, device="cuda", dtype=torch.float64)

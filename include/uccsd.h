@@ -70,6 +70,12 @@ typedef enum {
     UCCSD_FP32_STATE = 1  /* complex64 state and rotations; FP64 energy/gradient reductions */
 } uccsd_prec;
 
+typedef enum {
+    UCCSD_LAYOUT_FULL = 0,   /* each slot is the full 2^n amplitude vector (index = occupation bits) */
+    UCCSD_LAYOUT_SECTOR = 1  /* each slot holds only the (n_alpha, n_beta) sector: C(n_orb, n_alpha) x
+                                C(n_orb, n_beta) amplitudes, alpha-string rank major, strings ascending */
+} uccsd_layout;
+
 typedef struct {
     int n_qubits;         /* 2 * n_orb */
     int n_orb, n_alpha, n_beta;
@@ -81,6 +87,7 @@ typedef struct {
     int n_adj_runs;       /* shared-memory passes of the adjoint sweep */
     int batch;            /* state slots reserved */
     int precision;        /* uccsd_prec */
+    int layout;           /* uccsd_layout */
     size_t device_bytes;  /* device memory held by the context */
     uint64_t launches;    /* kernels launched by this context so far */
 } uccsd_info_t;
@@ -110,6 +117,19 @@ const char *uccsd_status_string(uccsd_status st);
  * asymmetric input -> UCCSD_ERR_ARG.  Invalidates excitations and state. */
 uccsd_status uccsd_set_hamiltonian(uccsd_ctx *ctx, int n_orb, const double *h,
                                    const double *eri, double e_core);
+
+/* State layout in device memory (default UCCSD_LAYOUT_FULL).  The
+ * Hamiltonian and the ansatz conserve the alpha and beta electron counts, so
+ * only the amplitudes of the (n_alpha, n_beta) sector are ever nonzero; every
+ * kernel touches only those.  UCCSD_LAYOUT_FULL keeps them at their place in
+ * the 2^n vector (the rest stays zero); UCCSD_LAYOUT_SECTOR stores them as a
+ * dense C(n_orb, n_alpha) x C(n_orb, n_beta) array (4.4% of 2^n at 26
+ * qubits), with identical arithmetic in the same order, so energies and
+ * gradients are bitwise the same in both layouts.  uccsd_get_state returns
+ * the 2^n vector in both.  Must come before uccsd_set_reference (after
+ * uccsd_set_hamiltonian, which clears the reference, it may be called again);
+ * otherwise UCCSD_ERR_STATE.  Unknown layout: UCCSD_ERR_ARG. */
+uccsd_status uccsd_set_layout(uccsd_ctx *ctx, int layout);
 
 /* Reference determinant |Psi_HF> (Eq. 3): n_alpha, n_beta electrons in the
  * lowest spin orbitals of each spin.  Needs the Hamiltonian first. */

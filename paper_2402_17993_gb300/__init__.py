@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libuccsd_gb300.so")
 
 FP64 = 0
 FP32_STATE = 1
+LAYOUT_FULL = 0
+LAYOUT_SECTOR = 1
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "device out of memory", 3: "CUDA error",
           4: "invalid call order or failed context", 5: "device wait timed out",
@@ -33,6 +35,7 @@ EXPORTS = [
     "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile", "uccsd_expectation_noalloc",
     "uccsd_capture", "uccsd_replay", "uccsd_mp1_amplitudes", "uccsd_magnitude_order",
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
+    "uccsd_set_layout",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -49,7 +52,7 @@ class Info(ctypes.Structure):
                 ("n_beta", ctypes.c_int), ("K", ctypes.c_int), ("n_ops", ctypes.c_int),
                 ("n_groups", ctypes.c_int), ("n_terms", ctypes.c_int),
                 ("n_fwd_runs", ctypes.c_int), ("n_adj_runs", ctypes.c_int),
-                ("batch", ctypes.c_int), ("precision", ctypes.c_int),
+                ("batch", ctypes.c_int), ("precision", ctypes.c_int), ("layout", ctypes.c_int),
                 ("device_bytes", ctypes.c_size_t), ("launches", ctypes.c_uint64)]
 
     def as_dict(self):
@@ -85,6 +88,7 @@ def lib():
         L.uccsd_status_string.restype = ctypes.c_char_p
         L.uccsd_set_hamiltonian.argtypes = [vp, ip, f64p, f64p, ctypes.c_double]
         L.uccsd_set_reference.argtypes = [vp, ip, ip]
+        L.uccsd_set_layout.argtypes = [vp, ip]
         L.uccsd_build_uccsd_list.argtypes = [ip, ip, ip, i32p, ip, ctypes.POINTER(ctypes.c_int)]
         L.uccsd_set_excitations.argtypes = [vp, ip, i32p, ip, ip]
         L.uccsd_set_batch.argtypes = [vp, ip]
@@ -246,6 +250,10 @@ class Context:
         self.n_qubits = 2 * n_orb
         return self
 
+    def set_layout(self, layout):
+        self._check(self._L.uccsd_set_layout(self._c, layout), "set_layout")
+        return self
+
     def set_reference(self, n_alpha, n_beta):
         self._check(self._L.uccsd_set_reference(self._c, n_alpha, n_beta), "set_reference")
         return self
@@ -363,9 +371,12 @@ class Context:
 
 
 def make_context(n_orb, h, eri, e_core, n_alpha, n_beta, ijab=None, precision=FP64, device=0,
-                 batch=1, trotter_order=1, n_slices=1, hbm_budget_bytes=0):
+                 batch=1, trotter_order=1, n_slices=1, hbm_budget_bytes=0, layout=0):
     ctx = Context(device, precision, hbm_budget_bytes)
-    ctx.set_hamiltonian(n_orb, h, eri, e_core).set_reference(n_alpha, n_beta)
+    ctx.set_hamiltonian(n_orb, h, eri, e_core)
+    if layout:
+        ctx.set_layout(layout)
+    ctx.set_reference(n_alpha, n_beta)
     if ijab is None:
         ijab = build_uccsd_list(n_orb, n_alpha, n_beta)
     ctx.set_excitations(ijab, trotter_order, n_slices)

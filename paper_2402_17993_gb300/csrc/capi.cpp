@@ -266,8 +266,9 @@ uccsd_status upload_tile_tables(uccsd_ctx *c) {
     return UCCSD_OK;
 }
 
-// Row/column layout of the sector for the reference's electron counts.
-void set_row_layout(uccsd_ctx *c) {
+// Row/column layout of the sector for the reference's electron counts and
+// the state addressing of the context's layout.
+uccsd_status set_row_layout(uccsd_ctx *c) {
     const int no = c->n_orb;
     const size_t base = (size_t(1) << no) - 1;
     c->hsec.astr = c->comb_combos + base + c->comb_offs_host[no * 17 + c->n_alpha];
@@ -278,9 +279,36 @@ void set_row_layout(uccsd_ctx *c) {
     c->hsec.ncb = (c->hsec.Db + c->hsec.colblock - 1) / c->hsec.colblock;
     c->hsec.n_alpha = c->n_alpha;
     c->hsec.n_beta = c->n_beta;
+    c->hsec.aoff = c->hsec.aspread;
+    c->hsec.boff = c->hsec.bspread;
+    c->hsec_full = c->hsec;
+    const uint32_t hfa = uint32_t((1u << c->n_alpha) - 1u), hfb = uint32_t((1u << c->n_beta) - 1u);
+    c->hf_addr = c->hf;
+    if (c->layout) {
+        // rank of a string among the n_orb-bit strings of its popcount, in
+        // ascending order (the order of astr / bstr)
+        std::vector<uint32_t> off(size_t(2) << no, 0u);
+        std::vector<int> cnt(no + 2, 0);
+        for (uint32_t sv = 0; sv < (1u << no); ++sv) {
+            const int pc = __builtin_popcount(sv);
+            const uint32_t rank = uint32_t(cnt[pc]++);
+            if (pc == c->n_alpha) off[sv] = rank * uint32_t(c->hsec.Db);
+            if (pc == c->n_beta) off[(size_t(1) << no) + sv] = rank;
+        }
+        uint32_t *p4;
+        uccsd_status st = upload(c, "hoff", off, &p4);
+        if (st) return st;
+        c->hsec.aoff = p4;
+        c->hsec.boff = p4 + (size_t(1) << no);
+        c->hf_addr = off[hfa] + off[(size_t(1) << no) + hfb];
+    }
+    return UCCSD_OK;
 }
 
-size_t state_bytes(const uccsd_ctx *c) { return size_t(1) << c->n; }
+// Amplitudes per slot: 2^n in the full layout, Da * Db in the sector layout.
+size_t state_elems(const uccsd_ctx *c) {
+    return c->layout ? size_t(c->hsec.Da) * size_t(c->hsec.Db) : size_t(1) << c->n;
+}
 size_t amp_bytes(const uccsd_ctx *c) { return c->prec ? 8 : 16; }
 int n_tiles_h(const uccsd_ctx *c) { return c->hsec.Da * c->hsec.ncb; }
 int n_tiles_a(const uccsd_ctx *c) { return c->adj.max_tiles; }
@@ -292,13 +320,13 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     uccsd_status st;
     const size_t B = c->B;
     const size_t n_ops = std::max<size_t>(c->op_k.size(), 1);
-    if ((st = dalloc(c, "psi", B * state_bytes(c) * amp_bytes(c), &p))) return st;
+    if ((st = dalloc(c, "psi", B * state_elems(c) * amp_bytes(c), &p))) return st;
     // the sweeps touch only electron-sector amplitudes; the rest stays zero
-    cudaError_t e0 = cudaMemset(p, 0, B * state_bytes(c) * amp_bytes(c));
+    cudaError_t e0 = cudaMemset(p, 0, B * state_elems(c) * amp_bytes(c));
     if (e0 != cudaSuccess) return cuda_fail(c, e0, "memset");
-    if ((st = dalloc(c, "sig", B * state_bytes(c) * amp_bytes(c), &p))) return st;
+    if ((st = dalloc(c, "sig", B * state_elems(c) * amp_bytes(c), &p))) return st;
     // sigma is written only inside the electron sector; the rest stays zero
-    cudaError_t e = cudaMemset(p, 0, B * state_bytes(c) * amp_bytes(c));
+    cudaError_t e = cudaMemset(p, 0, B * state_elems(c) * amp_bytes(c));
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
     if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
@@ -372,7 +400,7 @@ struct Marks {
 template <typename R>
 uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, double *E, double *grad,
                       cudaStream_t stream) {
-    const size_t N = state_bytes(c);
+    const size_t N = state_elems(c);
     LaunchCfg cfg;
     cfg.n = c->n;
     cfg.N = N;
@@ -405,13 +433,13 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     mk.begin(UCCSD_K_FORWARD);
     for (size_t r = 0; r < c->fwd.runs.size(); ++r) {
         if ((e = launch_forward_sweep<R>(cfg, psi, c->fwd.runs[r], fops, cs, c->fwd_args,
-                                         r == 0 ? 1 : 0, c->hf)) != cudaSuccess)
+                                         r == 0 ? 1 : 0, c->hf_addr)) != cudaSuccess)
             return cuda_fail(c, e, "forward kernel");
         ++c->launches;
         c->prof.launches[UCCSD_K_FORWARD]++;
     }
     if (c->fwd.runs.empty()) {
-        if ((e = launch_set_hf<R>(cfg, psi, c->hf)) != cudaSuccess) return cuda_fail(c, e, "hf kernel");
+        if ((e = launch_set_hf<R>(cfg, psi, c->hf_addr)) != cudaSuccess) return cuda_fail(c, e, "hf kernel");
         ++c->launches;
         c->prof.launches[UCCSD_K_FORWARD]++;
     }
@@ -494,9 +522,9 @@ uccsd_status prepare_trotter_free(uccsd_ctx *c) {
     c->tf_args.spread = p4;
     if ((st = dalloc(c, "tf_coef", sizeof(double) * std::max(c->K, 1), &p))) return st;
     for (const char *name : {"tf_u", "tf_w"}) {
-        if ((st = dalloc(c, name, state_bytes(c) * amp_bytes(c), &p))) return st;
+        if ((st = dalloc(c, name, state_elems(c) * amp_bytes(c), &p))) return st;
         // only electron-sector entries are ever written; the rest stays zero
-        cudaError_t e = cudaMemset(p, 0, state_bytes(c) * amp_bytes(c));
+        cudaError_t e = cudaMemset(p, 0, state_elems(c) * amp_bytes(c));
         if (e != cudaSuccess) return cuda_fail(c, e, "memset");
     }
     if ((st = dalloc(c, "tf_grad", sizeof(double) * std::max(c->K, 1), &p))) return st;
@@ -629,7 +657,7 @@ uccsd_status run_trotter_free(uccsd_ctx *c, const double *theta, double *E, doub
                               cudaStream_t stream) {
     LaunchCfg cfg;
     cfg.n = c->n;
-    cfg.N = state_bytes(c);
+    cfg.N = state_elems(c);
     cfg.B = 1;
     cfg.n_ops = c->K;
     cfg.stream = stream;
@@ -644,7 +672,7 @@ uccsd_status run_trotter_free(uccsd_ctx *c, const double *theta, double *E, doub
     for (int k = 0; k < c->K; ++k) b += std::fabs(theta[k]);
     void *psi = dptr(c, "psi"), *sig = dptr(c, "sig");
     void *t0 = dptr(c, "tf_u"), *t1 = dptr(c, "tf_w");
-    if ((e = launch_sector_init<R>(cfg, psi, t0, c->hsec, c->hf)) != cudaSuccess)
+    if ((e = launch_sector_init<R>(cfg, psi, t0, c->hsec, c->hf_addr)) != cudaSuccess)
         return cuda_fail(c, e, "sector init kernel");
     ++c->launches;
     if ((st = taylor_apply<R>(c, cfg, psi, t0, t1, coef, 1.0, 1.0, b))) return st;
@@ -668,7 +696,7 @@ uccsd_status run_trotter_free(uccsd_ctx *c, const double *theta, double *E, doub
     if (grad_host && c->K > 0) {
         // lambda(0) = exp(-A) sigma, phi(0) = |HF>
         if ((st = taylor_apply<R>(c, cfg, sig, t0, t1, coef, -1.0, 1.0, b))) return st;
-        if ((e = launch_sector_init<R>(cfg, psi, t0, c->hsec, c->hf)) != cudaSuccess)
+        if ((e = launch_sector_init<R>(cfg, psi, t0, c->hsec, c->hf_addr)) != cudaSuccess)
             return cuda_fail(c, e, "sector init kernel");
         ++c->launches;
         double C = std::fabs(c->shift);
@@ -822,6 +850,15 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, con
     return UCCSD_OK;
 }
 
+uccsd_status uccsd_set_layout(uccsd_ctx *c, int layout) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (layout != UCCSD_LAYOUT_FULL && layout != UCCSD_LAYOUT_SECTOR)
+        return fail(c, UCCSD_ERR_ARG, "layout must be UCCSD_LAYOUT_FULL or UCCSD_LAYOUT_SECTOR");
+    if (c->have_ref) return fail(c, UCCSD_ERR_STATE, "set_layout must come before set_reference");
+    c->layout = layout;
+    return UCCSD_OK;
+}
+
 uccsd_status uccsd_set_reference(uccsd_ctx *c, int n_alpha, int n_beta) {
     if (!c) return UCCSD_ERR_ARG;
     if (!c->have_h) return fail(c, UCCSD_ERR_STATE, "set_hamiltonian must come first");
@@ -841,7 +878,8 @@ uccsd_status uccsd_set_reference(uccsd_ctx *c, int n_alpha, int n_beta) {
     c->shift = c->H.has_diag ? sft : c->H.c0;
     c->hf32.diag_q0 = shifted_q0(c);
     c->hf64.diag_q0 = shifted_q0(c);
-    set_row_layout(c);
+    uccsd_status st = set_row_layout(c);
+    if (st) return st;
     c->have_ref = true;
     c->have_exc = false;
     c->state_valid = false;
@@ -931,6 +969,8 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     for (int q = 0; q < n; q += 2) base.amask |= 1u << q;
     base.n_alpha = c->n_alpha;
     base.n_beta = c->n_beta;
+    base.aoff = c->hsec.aoff;
+    base.boff = c->hsec.boff;
     c->fwd_args = base;
     c->adj_args = base;
     if ((st = upload(c, "fwd_spread", c->fwd.spread, &p4))) return st;
@@ -1029,20 +1069,46 @@ uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {
     if (!c) return UCCSD_ERR_ARG;
     if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "no state yet");
     if (slot < 0 || slot >= c->B) return fail(c, UCCSD_ERR_ARG, "slot out of range");
-    const size_t N = state_bytes(c);
-    if (!out || len < 2 * N) return fail(c, UCCSD_ERR_ARG, "output buffer too small");
+    const size_t N = state_elems(c);
+    const size_t Nfull = size_t(1) << c->n;
+    if (!out || len < 2 * Nfull) return fail(c, UCCSD_ERR_ARG, "output buffer too small");
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "synchronise");
     const char *src = static_cast<const char *>(dptr(c, "psi")) + size_t(slot) * N * amp_bytes(c);
+    std::vector<double> dense(c->layout ? 2 * N : 0);
+    double *dst = c->layout ? dense.data() : out;
     if (c->prec) {
         std::vector<float> tmp(2 * N);
         e = cudaMemcpy(tmp.data(), src, N * 8, cudaMemcpyDeviceToHost);
-        for (size_t i = 0; i < 2 * N; ++i) out[i] = tmp[i];
+        for (size_t i = 0; i < 2 * N; ++i) dst[i] = tmp[i];
     } else {
-        e = cudaMemcpy(out, src, N * 16, cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(dst, src, N * 16, cudaMemcpyDeviceToHost);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "state download");
+    if (c->layout) {
+        // scatter the sector array (alpha rank major, strings ascending) to 2^n
+        std::memset(out, 0, sizeof(double) * 2 * Nfull);
+        std::vector<uint32_t> sa, sb;
+        for (uint32_t sv = 0; sv < (1u << c->n_orb); ++sv) {
+            if (__builtin_popcount(sv) == c->n_alpha) sa.push_back(sv);
+            if (__builtin_popcount(sv) == c->n_beta) sb.push_back(sv);
+        }
+        auto spread = [](uint32_t sv, int shift) {
+            uint32_t x = 0;
+            for (int t = 0; sv; ++t, sv >>= 1)
+                if (sv & 1u) x |= 1u << (2 * t + shift);
+            return x;
+        };
+        for (size_t ia = 0; ia < sa.size(); ++ia) {
+            const uint32_t xa = spread(sa[ia], 0);
+            for (size_t ib = 0; ib < sb.size(); ++ib) {
+                const size_t x = xa | spread(sb[ib], 1), i = ia * sb.size() + ib;
+                out[2 * x] = dense[2 * i];
+                out[2 * x + 1] = dense[2 * i + 1];
+            }
+        }
+    }
     return UCCSD_OK;
 }
 
@@ -1061,6 +1127,7 @@ uccsd_status uccsd_info(const uccsd_ctx *c, uccsd_info_t *info) {
     info->n_adj_runs = int(c->adj.runs.size());
     info->batch = c->B;
     info->precision = c->prec;
+    info->layout = c->layout;
     info->device_bytes = c->bytes;
     info->launches = c->launches;
     return UCCSD_OK;

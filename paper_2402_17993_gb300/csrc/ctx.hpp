@@ -34,7 +34,9 @@ struct uccsd_ctx {
     int n_orb = 0, n = 0;
     bool have_h = false, have_ref = false, have_exc = false;
     int n_alpha = 0, n_beta = 0;
-    uint32_t hf = 0;
+    uint32_t hf = 0;       // reference determinant (qubit bits)
+    int layout = 0;        // 0 full 2^n vector, 1 electron-sector array (UCCSD_LAYOUT_*)
+    uint32_t hf_addr = 0;  // address of the reference amplitude in a slot
     uccsd::CompiledH H;
     int K = 0, order = 1, M = 1;
     std::vector<int32_t> ijab, op_k;
@@ -57,6 +59,7 @@ struct uccsd_ctx {
     uccsd::DevHam<float> hf32;
     uccsd::DevHam<double> hf64;
     uccsd::HSector hsec;
+    uccsd::HSector hsec_full;  // hsec with full-layout addressing (caller states)
     // combinatorial rank tables (shared by the sweeps and the H-apply)
     const uint16_t *comb_combos = nullptr, *comb_ranks = nullptr;
     const int32_t *comb_offs = nullptr;

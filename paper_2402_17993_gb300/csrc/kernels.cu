@@ -149,9 +149,9 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     for (int t = threadIdx.x; t < (1 << n_orb); t += blockDim.x) brk[t] = hs.brank[t];
     for (int t = threadIdx.x; t < 16 * 5; t += blockDim.x) nb4[t] = hs.binom[t];
     {
-        const uint32_t xR = hs.aspread[sR];
+        const uint32_t xR = hs.aoff[sR];
         for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
-            src[c] = st[xR | hs.bspread[hs.bstr[c]]];
+            src[c] = st[xR + hs.boff[hs.bstr[c]]];
     }
     __syncthreads();
 
@@ -252,10 +252,10 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         for (uint32_t vq = virA; vq; vq &= vq - 1u) {
             const int q = __ffs(vq) - 1;
             const uint32_t sRp = sR ^ (1u << p) ^ (1u << q);
-            const uint32_t xRp = hs.aspread[sRp];
+            const uint32_t xRp = hs.aoff[sRp];
             __syncthreads();
             for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
-                src[c] = st[xRp | hs.bspread[hs.bstr[c]]];
+                src[c] = st[xRp + hs.boff[hs.bstr[c]]];
             __syncthreads();
             const int pa = pair_index(min(p, q), max(p, q));
             const int asel = q > p;
@@ -318,13 +318,13 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                     const int rq2 = __popc(m & ((1u << q2) - 1u));
                     const DblT<R> &Dq = H.d2a[qi];
                     const uint32_t sRp = sR ^ m;
-                    const uint32_t xRp = hs.aspread[sRp];
+                    const uint32_t xRp = hs.aoff[sRp];
                     const R base = Dq.lut[(1 << rq1) | (1 << rq2)];
 #pragma unroll
                     for (int i = 0; i < EPT; ++i) {
                         if (cix[i] < 0) continue;
                         R val = jw_parity(sRp, sc[i], Dq.j) ? -base : base;
-                        accumulate<R>(acc[i], comp[i], val, st[xRp | hs.bspread[sc[i]]]);
+                        accumulate<R>(acc[i], comp[i], val, st[xRp + hs.boff[sc[i]]]);
                     }
                 }
             }
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
         nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
         if (store_sigma)
-            sig[(size_t)b * N + (hs.aspread[sR] | hs.bspread[sc[i]])] = acc[i];
+            sig[(size_t)b * N + (hs.aoff[sR] + hs.boff[sc[i]])] = acc[i];
     }
     e = block_sum(e, red);
     nrm = block_sum(nrm, red);

@@ -38,8 +38,14 @@ struct HSector {
     const uint16_t *astr = nullptr;    // Da alpha strings
     const uint16_t *bstr = nullptr;    // Db beta strings
     const uint16_t *brank = nullptr;   // rank of any n_orb-bit string in its popcount class
-    const uint32_t *aspread = nullptr; // alpha string -> global bits (2^n_orb)
-    const uint32_t *bspread = nullptr; // beta string -> global bits (2^n_orb)
+    const uint32_t *aspread = nullptr; // alpha string -> qubit bits (2^n_orb)
+    const uint32_t *bspread = nullptr; // beta string -> qubit bits (2^n_orb)
+    // State addressing: the amplitude of determinant (alpha string sa, beta
+    // string sb) of a slot is at aoff[sa] + boff[sb].  Full 2^n layout: the
+    // qubit bits (aoff = aspread, boff = bspread); sector layout: rank(sa) * Db
+    // and rank(sb).
+    const uint32_t *aoff = nullptr;
+    const uint32_t *boff = nullptr;
     const int32_t *binom = nullptr;    // binom[t * 5 + k], t < 16, k <= 4
     int n_alpha = 0, n_beta = 0;
     int Da = 0, Db = 0;
@@ -48,7 +54,7 @@ struct HSector {
 
 struct LaunchCfg {
     int n = 0;           // qubits
-    size_t N = 0;        // 2^n
+    size_t N = 0;        // amplitudes per slot: 2^n (full layout) or Da * Db (sector layout)
     int B = 1;           // slots in this call
     int n_ops = 0;
     cudaStream_t stream = nullptr;
@@ -65,7 +71,9 @@ struct SweepArgs {
     const uint16_t *combos = nullptr;    // strings sorted by (popcount, value), per bit count
     const uint16_t *ranks = nullptr;     // rank of a string within its popcount class
     const int32_t *comb_offs = nullptr;  // class offsets, 17 per bit count
-    const uint32_t *spread = nullptr;    // per run: tile string -> global bits
+    const uint32_t *spread = nullptr;    // per run: tile string -> orbital string
+    const uint32_t *aoff = nullptr;      // state addressing (see HSector)
+    const uint32_t *boff = nullptr;
     uint32_t amask = 0;                  // alpha qubits (even positions)
     int n_alpha = 0, n_beta = 0;
 };

@@ -89,9 +89,9 @@ extern "C" uccsd_status uccsd_expectation_noalloc(uccsd_ctx *c, const void *psi,
     // The H-apply writes both partials of every tile before the reduction
     // reads them, so nothing in the scratch has to start at zero.
     if (c->prec)
-        e = uccsd::launch_happly<float>(cfg, psi, nullptr, c->LH, c->hf32, c->hsec, partials, 0);
+        e = uccsd::launch_happly<float>(cfg, psi, nullptr, c->LH, c->hf32, c->hsec_full, partials, 0);
     else
-        e = uccsd::launch_happly<double>(cfg, psi, nullptr, c->LH, c->hf64, c->hsec, partials, 0);
+        e = uccsd::launch_happly<double>(cfg, psi, nullptr, c->LH, c->hf64, c->hsec_full, partials, 0);
     if (e == cudaSuccess)
         e = uccsd::launch_reduce(cfg, partials, tiles, nullptr, 1, nullptr, 0, nullptr, nullptr,
                                  nullptr, c->shift, c->prec ? 1 : 0, E, nullptr);

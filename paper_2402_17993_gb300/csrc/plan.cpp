@@ -168,8 +168,11 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
             r.max_db = int(db);
         }
         r.spread_off = int(plan.spread.size());
-        for (uint32_t sidx = 0; sidx < (1u << r.La); ++sidx) plan.spread.push_back(deposit_bits(sidx, Ta));
-        for (uint32_t sidx = 0; sidx < (1u << r.Lb); ++sidx) plan.spread.push_back(deposit_bits(sidx, Tb));
+        // tile string -> orbital string (alpha: orbital t for qubit 2t; beta: qubit 2t + 1)
+        for (uint32_t sidx = 0; sidx < (1u << r.La); ++sidx)
+            plan.spread.push_back(gather_bits(deposit_bits(sidx, Ta), amask));
+        for (uint32_t sidx = 0; sidx < (1u << r.Lb); ++sidx)
+            plan.spread.push_back(gather_bits(deposit_bits(sidx, Tb), bmask));
         r.op_begin = int(plan.ops.size());
         for (size_t u = o; u < e; ++u) {
             const CompiledExc &x = exc[op_k[u]];

@@ -24,7 +24,7 @@ void build_schedule(int K, int order, int M, std::vector<int32_t> *op_k,
 struct SweepPlan {
     std::vector<CRunDev> runs;
     std::vector<COpDev> ops;       // ops of run r at [runs[r].op_begin, runs[r].op_end)
-    std::vector<uint32_t> spread;  // per run: deposit tables of alpha and beta strings
+    std::vector<uint32_t> spread;  // per run: tile alpha / beta string -> orbital string
     std::vector<int32_t> op_tiles; // per schedule factor: tiles of its run
     int max_tiles = 1;
     int max_entries = 1;

@@ -70,14 +70,16 @@ __device__ __forceinline__ T warp_sum(T v) {
 // Per-CTA view of its compact tile.
 struct TileView {
     uint32_t rest;
+    uint32_t restA, restB;  // orbital strings of the rest bits
     int a, b;            // electrons left for the tile's alpha / beta bits
     int Da, Db;          // C(La, a), C(Lb, b)
     const uint16_t *ca;  // alpha strings of popcount a
     const uint16_t *cb;  // beta strings of popcount b
     const uint16_t *ra;  // rank of an La-bit string in its popcount class
     const uint16_t *rb;
-    const uint32_t *spa; // alpha string -> global bits
+    const uint32_t *spa; // tile alpha string -> orbital string
     const uint32_t *spb;
+    const uint32_t *aoff, *boff;  // state addressing
 };
 
 __device__ __forceinline__ bool make_view(const CRunDev &run, const SweepArgs &sa, TileView *v) {
@@ -93,13 +95,24 @@ __device__ __forceinline__ bool make_view(const CRunDev &run, const SweepArgs &s
     v->rb = sa.ranks + ((1 << run.Lb) - 1);
     v->spa = sa.spread + run.spread_off;
     v->spb = v->spa + (1 << run.La);
+    v->aoff = sa.aoff;
+    v->boff = sa.boff;
+    uint32_t ra = 0, rb = 0;
+    for (uint32_t m = v->rest; m; m &= m - 1u) {
+        const int q = __ffs(m) - 1;
+        if (q & 1) rb |= 1u << (q >> 1);
+        else ra |= 1u << (q >> 1);
+    }
+    v->restA = ra;
+    v->restB = rb;
     return true;
 }
 
+// Address of tile entry e in a slot of the state.
 __device__ __forceinline__ uint32_t entry_index(const TileView &v, int e) {
     const int ia = e / v.Db;
     const int ib = e - ia * v.Db;
-    return v.rest | v.spa[v.ca[ia]] | v.spb[v.cb[ib]];
+    return v.aoff[v.restA | v.spa[v.ca[ia]]] + v.boff[v.restB | v.spb[v.cb[ib]]];
 }
 
 // Pairs of factor `op` inside the tile: occupied-side strings have the op's
@@ -549,7 +562,7 @@ __global__ void tf_grad_accum_kernel(const double *__restrict__ gpart, int tile_
 __device__ __forceinline__ uint32_t sector_index(const HSector &hs, int e) {
     const int ia = e / hs.Db;
     const int ib = e - ia * hs.Db;
-    return hs.aspread[hs.astr[ia]] | hs.bspread[hs.bstr[ib]];
+    return hs.aoff[hs.astr[ia]] + hs.boff[hs.bstr[ib]];
 }
 
 // acc = u = |HF> on the sector.

@@ -71,9 +71,11 @@ class LBFGS:
         return theta + d
 
 
-def minimize(ctx, theta0=None, gtol: float = 1e-6, maxiter: int = 1000):
+def minimize(ctx, theta0=None, gtol: float = 1e-6, maxiter: int = 1000, trotter_free: bool = False):
     """VQE by scipy L-BFGS-B with the adjoint gradient until the gradient
-    2-norm is below gtol.  Returns (E, theta, n_evals, grad_norm)."""
+    2-norm is below gtol.  trotter_free: optimise exp(sum theta G)|HF>
+    (Eq. 3 without Trotterisation) instead of the context's Trotter product.
+    Returns (E, theta, n_evals, grad_norm)."""
     import scipy.optimize
 
     K = ctx.K
@@ -81,8 +83,10 @@ def minimize(ctx, theta0=None, gtol: float = 1e-6, maxiter: int = 1000):
     n_eval = [0]
     last = {}
 
+    eg = ctx.energy_grad_trotter_free if trotter_free else ctx.energy_grad
+
     def fun(th):
-        E, g = ctx.energy_grad(th)
+        E, g = eg(th)
         n_eval[0] += 1
         last["g"] = g
         return E, g
@@ -90,5 +94,5 @@ def minimize(ctx, theta0=None, gtol: float = 1e-6, maxiter: int = 1000):
     res = scipy.optimize.minimize(fun, theta0, jac=True, method="L-BFGS-B",
                                   options={"maxiter": maxiter, "gtol": gtol / np.sqrt(max(K, 1)),
                                            "ftol": 1e-15, "maxcor": 10})
-    E, g = ctx.energy_grad(res.x)
+    E, g = eg(res.x)
     return float(E), res.x, n_eval[0] + 1, float(np.linalg.norm(g))

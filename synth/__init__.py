@@ -91,9 +91,13 @@ class Xoshiro256StarStar:
         return z0
 
 
-def make_integrals(n_orb: int, n_chol: int, seed: int):
+def make_integrals(n_orb: int, n_chol: int, seed: int, offdiag: float = 1.0,
+                   chol: float = 1.0):
     """Synthetic one- and two-electron integrals (recipe in the module doc).
 
+    offdiag and chol scale the off-diagonal h_pq and the Cholesky-like
+    vectors (1.0: the recipe above; smaller values give weakly correlated
+    fragments dominated by their reference determinant).
     Returns (h, eri, e_core): h is (n_orb, n_orb) float64 symmetric,
     eri is (n_orb,)*4 float64 chemist-notation (pq|rs), e_core = 0.0.
     """
@@ -101,14 +105,14 @@ def make_integrals(n_orb: int, n_chol: int, seed: int):
     h = np.zeros((n_orb, n_orb), dtype=np.float64)
     for p in range(n_orb):
         for q in range(p + 1, n_orb):
-            v = rng.normal()
+            v = rng.normal() * offdiag
             h[p, q] = v
             h[q, p] = v
     diag = np.linspace(-2.0, -0.5, n_orb) if n_orb > 1 else np.array([-2.0])
     for p in range(n_orb):
         h[p, p] = diag[p]
     L = np.zeros((n_chol, n_orb, n_orb), dtype=np.float64)
-    scale = 1.0 / math.sqrt(n_chol)
+    scale = chol / math.sqrt(n_chol)
     for k in range(n_chol):
         for p in range(n_orb):
             for q in range(p, n_orb):
@@ -166,6 +170,59 @@ def workload(name: str):
     h, eri, e_core = make_integrals(w["n_orb"], w["n_chol"], w["seed"])
     return dict(w, h=h, eri=eri, e_core=e_core,
                 n_alpha=w["n_elec"] // 2, n_beta=w["n_elec"] // 2)
+
+
+def non_interacting_dimer(h_a, eri_a, n_occ_a, h_b, eri_b, n_occ_b):
+    """Integrals of two fragments with no integral between them (a dimer at
+    infinite separation, the size-consistency setting of the paper's
+    Section 3.2) in localised orbitals, ordered [A occupied, B occupied,
+    A virtual, B virtual] so that the lowest orbitals form the product
+    reference determinant.  Returns (h, eri, perm) with perm[new] = old index
+    in the block-diagonal order [A orbitals, B orbitals]."""
+    na, nb = h_a.shape[0], h_b.shape[0]
+    n = na + nb
+    h = np.zeros((n, n))
+    eri = np.zeros((n, n, n, n))
+    h[:na, :na] = h_a
+    h[na:, na:] = h_b
+    eri[:na, :na, :na, :na] = eri_a
+    eri[na:, na:, na:, na:] = eri_b
+    perm = (list(range(n_occ_a)) + [na + i for i in range(n_occ_b)] +
+            list(range(n_occ_a, na)) + [na + i for i in range(n_occ_b, nb)])
+    perm = np.array(perm)
+    h = h[np.ix_(perm, perm)]
+    eri = eri[np.ix_(perm, perm, perm, perm)]
+    return np.ascontiguousarray(h), np.ascontiguousarray(eri), perm
+
+
+def rotate_orbitals(h, eri, U):
+    """Integrals in the rotated orbitals phi'_p = sum_q U[q, p] phi_q
+    (U orthogonal): h' = U^T h U, (pq|rs)' = sum U_ap U_bq U_cr U_ds (ab|cd)."""
+    h2 = U.T @ h @ U
+    e2 = np.einsum("abcd,ap,bq,cr,ds->pqrs", eri, U, U, U, U, optimize=True)
+    # restore exact 8-fold symmetry against summation-order rounding
+    e2 = 0.5 * (e2 + e2.transpose(2, 3, 0, 1))
+    e2 = 0.5 * (e2 + e2.transpose(1, 0, 2, 3))
+    e2 = 0.5 * (e2 + e2.transpose(0, 1, 3, 2))
+    return np.ascontiguousarray(0.5 * (h2 + h2.T)), np.ascontiguousarray(e2)
+
+
+def pair_mixing(n_occ, n_virt, angle=math.pi / 4):
+    """Orthogonal U for a dimer ordered [A occ, B occ, A virt, B virt] with
+    n_occ occupied and n_virt virtual orbitals per fragment: orbital i of A
+    and orbital i of B (occupied with occupied, virtual with virtual) are
+    rotated into each other by `angle`.  At pi/4 these are the
+    symmetric/antisymmetric combinations, the canonical orbitals of two
+    identical non-interacting fragments (delocalised over the dimer)."""
+    n = 2 * (n_occ + n_virt)
+    U = np.eye(n)
+    c, s = math.cos(angle), math.sin(angle)
+    pairs = [(i, n_occ + i) for i in range(n_occ)]
+    pairs += [(2 * n_occ + a, 2 * n_occ + n_virt + a) for a in range(n_virt)]
+    for p, q in pairs:
+        U[p, p], U[q, p] = c, s
+        U[p, q], U[q, q] = -s, c
+    return U
 
 
 def stream_fragments(n_req: int, seed: int = 7):
