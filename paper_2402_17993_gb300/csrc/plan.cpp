@@ -108,7 +108,7 @@ void max_tile_sides(int n_qubits, int n_alpha, int n_beta, uint32_t tmask, long 
 size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
                         int nvec, int n_ops_run, int lmax) {
     size_t b = size_t(entries) * amp_bytes * nvec + 2 * size_t(da + db) * 8 +
-               size_t(n_ops_run) * sizeof(COpDev);
+               size_t(n_ops_run) * (sizeof(COpDev) + amp_bytes);
     if (lmax <= kStageLmax) b += sweep_table_bytes(lmax);
     return b;
 }

@@ -43,7 +43,8 @@ constexpr int kStageLmax = 10;
 size_t sweep_table_bytes(int lmax);
 // Shared memory of one sweep CTA: nvec tiles, the two double-buffered
 // alpha/beta pair-side lists (8 bytes per string), the run's factor
-// descriptors and (lmax <= kStageLmax) the staged tables.
+// descriptors and cos/sin values (one amplitude each) and (lmax <=
+// kStageLmax) the staged tables.
 size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
                         int nvec, int n_ops_run, int lmax);
 

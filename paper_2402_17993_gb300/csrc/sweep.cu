@@ -19,7 +19,7 @@
 namespace uccsd {
 namespace {
 
-constexpr int kSweepThreadsLarge = 1024;  // tiles of >= kLargeTile entries
+constexpr int kSweepThreadsLarge = 512;  // tiles of >= kLargeTile entries
 constexpr int kSweepThreadsSmall = 256;
 constexpr int kLargeTile = 4096;
 
@@ -189,6 +189,42 @@ __device__ __forceinline__ SweepArgs stage_tables(const CRunDev &run, const Swee
     return la;
 }
 
+// As stage_tables, with the run's cos/sin values (of slot csb, gathered by
+// factor) staged right after the factor descriptors.
+template <typename R>
+__device__ __forceinline__ SweepArgs stage_run(const CRunDev &run, const SweepArgs &sa,
+                                               const COpDev *ops, const V2<R> *csb,
+                                               unsigned char *base, COpDev **sops, V2<R> **scs) {
+    const int nops = run.op_end - run.op_begin;
+    COpDev *so = reinterpret_cast<COpDev *>(base);
+    const uint32_t *gsrc = reinterpret_cast<const uint32_t *>(ops + run.op_begin);
+    uint32_t *gdst = reinterpret_cast<uint32_t *>(so);
+    for (int t = threadIdx.x; t < nops * 8; t += blockDim.x) gdst[t] = gsrc[t];
+    V2<R> *c = reinterpret_cast<V2<R> *>(so + nops);
+    for (int t = threadIdx.x; t < nops; t += blockDim.x)
+        c[t] = csb[ops[run.op_begin + t].op_s0 & 0x7FFFFFFFu];
+    *sops = so;
+    *scs = c;
+    SweepArgs la = sa;
+    const int lmax = max(run.La, run.Lb);
+    if (lmax <= kStageLmax) {
+        int32_t *offs = reinterpret_cast<int32_t *>(c + nops);
+        const int n_offs = (lmax + 1) * 17;
+        uint16_t *cmb = reinterpret_cast<uint16_t *>(offs + n_offs);
+        const int n_str = (1 << (lmax + 1)) - 1;
+        uint16_t *rnk = cmb + n_str;
+        for (int t = threadIdx.x; t < n_offs; t += blockDim.x) offs[t] = sa.comb_offs[t];
+        for (int t = threadIdx.x; t < n_str; t += blockDim.x) {
+            cmb[t] = sa.combos[t];
+            rnk[t] = sa.ranks[t];
+        }
+        la.comb_offs = offs;
+        la.combos = cmb;
+        la.ranks = rnk;
+    }
+    return la;
+}
+
 // j -> (ja, jb) = (j / Vb, j % Vb) by a float reciprocal with an exact fix-up
 // (j < 2^24).
 __device__ __forceinline__ void split_index(int j, int Vb, float inv, int *ja, int *jb) {
@@ -199,24 +235,149 @@ __device__ __forceinline__ void split_index(int j, int Vb, float inv, int *ja, i
     *jb = j - q * Vb;
 }
 
+// x with its sign bit flipped when bit 31 of neg is set.
+__device__ __forceinline__ float flip_sign(float x, uint32_t neg) {
+    return __int_as_float(__float_as_int(x) ^ (int)(neg & 0x80000000u));
+}
+__device__ __forceinline__ double flip_sign(double x, uint32_t neg) {
+    return __hiloint2double(__double2hiint(x) ^ (int)(neg & 0x80000000u), __double2loint(x));
+}
+
+// Walk over the pair set j = ja * Vb + jb in steps of THREADS: the step in
+// (ja, jb) coordinates is (sq, sr) with THREADS = sq * Vb + sr.
+struct PairWalk {
+    int ja, jb, sq, sr, Vb;
+    __device__ __forceinline__ void init(int j0, int threads, int vb) {
+        Vb = vb;
+        const float inv = 1.0f / (float)vb;
+        split_index(j0, vb, inv, &ja, &jb);
+        split_index(threads, vb, inv, &sq, &sr);
+    }
+    __device__ __forceinline__ void next(int *a, int *b) const {
+        int na = *a + sq, nb = *b + sr;
+        if (nb >= Vb) {
+            nb -= Vb;
+            ++na;
+        }
+        *a = na;
+        *b = nb;
+    }
+};
+
+// Offsets of a pair from its side-list entries: the low 31 bits of the sums
+// are the tile entries of the occupied side and its partner; bit 31 of the
+// first sum is the XOR of the two strings' Jordan-Wigner parities.
+__device__ __forceinline__ void pair_offsets(int2 a2, int2 b2, int *e, int *e2, uint32_t *par) {
+    const uint32_t sum = (uint32_t)a2.x + (uint32_t)b2.x;
+    *e = (int)(sum & 0x7FFFFFFFu);
+    *e2 = a2.y + b2.y;
+    *par = sum;
+}
+
+// Rounding of the rotations and dot products fixed by explicit intrinsics,
+// so every instantiation of a kernel gives the same bits.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+// (c x - s y, c y + s x) for the pair (x occupied side, y partner).
+template <typename R>
+__device__ __forceinline__ void rotate_pair(R c, R s, V2<R> &x, V2<R> &y) {
+    const V2<R> x0 = x, y0 = y;
+    x.x = fma_rn(c, x0.x, -mul_rn(s, y0.x));
+    x.y = fma_rn(c, x0.y, -mul_rn(s, y0.y));
+    y.x = fma_rn(c, y0.x, mul_rn(s, x0.x));
+    y.y = fma_rn(c, y0.y, mul_rn(s, x0.y));
+}
+
+// Re(conj(l_x) (G phi)_x + conj(l_x') (G phi)_x') / s for the pair, with
+// (G phi)_x = -s phi_x', (G phi)_x' = s phi_x.
+template <typename R>
+__device__ __forceinline__ R pair_dot(V2<R> fx, V2<R> fy, V2<R> lx, V2<R> ly) {
+    return fma_rn(ly.x, fx.x, fma_rn(ly.y, fx.y, -fma_rn(lx.x, fy.x, mul_rn(lx.y, fy.y))));
+}
+
+// Per-factor header written by the builder warp: pair-set sizes, cos, the
+// sin with the factor's sign and the tile's rest-bit parity folded in, and
+// (adjoint) the two sign bits separately for the gradient partial.
+template <typename R>
+struct OpHdr {
+    int Va, Vb;
+    R ct, st;
+    uint32_t opneg, rneg;
+};
+
+// The builder warps prepare factor `op` in one buffer: side lists (NB
+// builder lanes) and the header (builder lane 0, from its cos/sin value csv).
+template <typename R, int NB>
+__device__ __forceinline__ void build_factor(const CRunDev &run, const SweepArgs &la,
+                                             const TileView &v, const COpDev &op, V2<R> csv,
+                                             int2 *lists, OpHdr<R> *hdr, int lane) {
+    const PairSet p = pair_set(run, la, v, op);
+    int2 *A = lists, *B = lists + p.Va;
+    for (int t = lane; t < p.Va + p.Vb; t += NB) {
+        if (t < p.Va) {
+            const uint32_t s = insert_zeros(p.fa[t], op.fa) | op.oa;
+            const int par = __popc(s & op.pa) & 1;
+            A[t] = make_int2((int)(v.ra[s] * v.Db) | (par << 31), (int)(v.ra[s ^ op.fa] * v.Db));
+        } else {
+            const int u = t - p.Va;
+            const uint32_t s = insert_zeros(p.fb[u], op.fb) | op.ob;
+            const int par = __popc(s & op.pb) & 1;
+            B[u] = make_int2((int)v.rb[s] | (par << 31), (int)v.rb[s ^ op.fb]);
+        }
+    }
+    if (lane == 0) {
+        OpHdr<R> h;
+        h.Va = p.Va;
+        h.Vb = p.Vb;
+        h.opneg = op.op_s0 & 0x80000000u;
+        h.rneg = (uint32_t)(__popc(v.rest & op.par_rest) & 1) << 31;
+        h.ct = csv.x;
+        h.st = flip_sign(csv.y, h.opneg ^ h.rneg);
+        *hdr = h;
+    }
+}
+
+// Builder warps per CTA of THREADS threads (the last warps of the CTA).
+template <int THREADS>
+struct Roles {
+    static constexpr int kBuildWarps = THREADS >= 512 ? 4 : 2;
+    static constexpr int kBuildLanes = 32 * kBuildWarps;
+    static constexpr int kCompute = THREADS - kBuildLanes;   // compute threads 0 .. kCompute-1
+    static constexpr int kComputeWarps = kCompute / 32;
+};
+
+// Forward sweep of one run over one tile.  Warp specialisation: the last
+// warps build factor o + 1 (side lists and header) while the other warps
+// rotate the pairs of factor o; one barrier per factor separates the two
+// buffers.  All cos/sin values of the run are staged in shared memory.
 template <typename R, int THREADS>
 __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
     V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
     const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf) {
+    using RL = Roles<THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ OpHdr<R> hdr[2];
     V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
     int2 *lists = reinterpret_cast<int2 *>(tile + run.max_entries);  // [2][max_da + max_db]
     const int lstride = run.max_da + run.max_db;
     TileView v;
     if (!make_view(run, sa, &v)) return;  // no sector entries in this tile
+    const int b = blockIdx.y;
     COpDev *sops;
-    const SweepArgs la = stage_tables(run, sa, ops, reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops);
+    V2<R> *scs;
+    const SweepArgs la = stage_run<R>(run, sa, ops, cs + (size_t)b * n_ops,
+                                      reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops, &scs);
     __syncthreads();
     make_view(run, la, &v);
-    const int b = blockIdx.y;
+    const bool builder = (int)threadIdx.x >= RL::kCompute;
+    const int bl = (int)threadIdx.x - RL::kCompute;  // builder lane
     V2<R> *st = psi + (size_t)b * N;
     const int D = v.Da * v.Db;
-    for (int e = threadIdx.x; e < D; e += blockDim.x) {
+    const int nops = run.op_end - run.op_begin;
+    for (int e = threadIdx.x; e < D; e += THREADS) {
         const uint32_t x = entry_index(v, e);
         V2<R> val;
         if (init_hf) {
@@ -227,67 +388,78 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
         }
         tile[e] = val;
     }
-    if (run.op_begin < run.op_end) {
-        const PairSet p0 = pair_set(run, la, v, sops[0]);
-        build_sides(p0, v, sops[0], lists, lists + p0.Va);
-    }
+    if (builder && nops > 0)
+        build_factor<R, RL::kBuildLanes>(run, la, v, sops[0], scs[0], lists, &hdr[0], bl);
     __syncthreads();
-    int buf = 0;
-    const int nops = run.op_end - run.op_begin;
     for (int o = 0; o < nops; ++o) {
-        const COpDev &op = sops[o];
-        const PairSet p = pair_set(run, la, v, op);
-        int2 *A = lists + buf * lstride;
-        int2 *B = A + p.Va;
-        // next factor's side lists go to the other buffer (independent of psi)
-        if (o + 1 < nops) {
-            const PairSet pn = pair_set(run, la, v, sops[o + 1]);
-            int2 *An = lists + (buf ^ 1) * lstride;
-            build_sides(pn, v, sops[o + 1], An, An + pn.Va);
-        }
-        const int P = p.Va * p.Vb;
-        if (P > 0) {
-            const V2<R> csv = cs[(size_t)b * n_ops + (op.op_s0 & 0x7FFFFFFFu)];
-            const R ct = csv.x;
-            const R st0 = (op.op_s0 >> 31) ? -csv.y : csv.y;
-            const int rpar = __popc(v.rest & op.par_rest) & 1;
-            const float inv = 1.0f / (float)p.Vb;
-            for (int j = threadIdx.x; j < P; j += blockDim.x) {
-                int ja, jb;
-                split_index(j, p.Vb, inv, &ja, &jb);
-                const int2 a2 = A[ja], b2 = B[jb];
-                const int e = (a2.x & 0x7FFFFFFF) + (b2.x & 0x7FFFFFFF);
-                const int e2 = a2.y + b2.y;
-                const int neg = ((((unsigned)(a2.x ^ b2.x)) >> 31) ^ rpar) & 1;
-                const R ss = neg ? -st0 : st0;
-                const V2<R> x0 = tile[e], x1 = tile[e2];
-                V2<R> y0, y1;
-                y0.x = ct * x0.x - ss * x1.x;
-                y0.y = ct * x0.y - ss * x1.y;
-                y1.x = ct * x1.x + ss * x0.x;
-                y1.y = ct * x1.y + ss * x0.y;
-                tile[e] = y0;
-                tile[e2] = y1;
+        const int buf = o & 1;
+        if (builder) {
+            if (o + 1 < nops)
+                build_factor<R, RL::kBuildLanes>(run, la, v, sops[o + 1], scs[o + 1],
+                                                 lists + (buf ^ 1) * lstride, &hdr[buf ^ 1], bl);
+        } else {
+            const OpHdr<R> h = hdr[buf];
+            const int P = h.Va * h.Vb;
+            const int2 *A = lists + buf * lstride;
+            const int2 *B = A + h.Va;
+            if ((int)threadIdx.x < P) {
+                PairWalk w;
+                w.init(threadIdx.x, RL::kCompute, h.Vb);
+                int ja = w.ja, jb = w.jb;
+                int j = threadIdx.x;
+                // two disjoint pairs per iteration: all loads before any store
+                for (; j + RL::kCompute < P; j += 2 * RL::kCompute) {
+                    int ja1 = ja, jb1 = jb;
+                    w.next(&ja1, &jb1);
+                    int e0, f0, e1, f1;
+                    uint32_t q0, q1;
+                    pair_offsets(A[ja], B[jb], &e0, &f0, &q0);
+                    pair_offsets(A[ja1], B[jb1], &e1, &f1, &q1);
+                    V2<R> x0 = tile[e0], x1 = tile[f0], u0 = tile[e1], u1 = tile[f1];
+                    rotate_pair<R>(h.ct, flip_sign(h.st, q0), x0, x1);
+                    rotate_pair<R>(h.ct, flip_sign(h.st, q1), u0, u1);
+                    tile[e0] = x0;
+                    tile[f0] = x1;
+                    tile[e1] = u0;
+                    tile[f1] = u1;
+                    ja = ja1;
+                    jb = jb1;
+                    w.next(&ja, &jb);
+                }
+                if (j < P) {
+                    int e0, f0;
+                    uint32_t q0;
+                    pair_offsets(A[ja], B[jb], &e0, &f0, &q0);
+                    V2<R> x0 = tile[e0], x1 = tile[f0];
+                    rotate_pair<R>(h.ct, flip_sign(h.st, q0), x0, x1);
+                    tile[e0] = x0;
+                    tile[f0] = x1;
+                }
             }
         }
         __syncthreads();
-        buf ^= 1;
     }
-    for (int e = threadIdx.x; e < D; e += blockDim.x) st[entry_index(v, e)] = tile[e];
+    for (int e = threadIdx.x; e < D; e += THREADS) st[entry_index(v, e)] = tile[e];
 }
 
+// Adjoint sweep of one run over one tile, factors in reverse: the compute
+// warps form the gradient partial of factor o and un-rotate phi and lambda
+// while the builder warps prepare factor o - 1 and write the partial of
+// factor o + 1.
 template <typename R, int THREADS>
 __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
     double *__restrict__ gpart, int tile_stride) {
+    using RL = Roles<THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ OpHdr<R> hdr[2];
     __shared__ double wring[2][32];
     const int b = blockIdx.y;
     TileView v;
     if (!make_view(run, sa, &v)) {
         // all-zero tile: its gradient partials are zero
-        for (int o = run.op_begin + threadIdx.x; o < run.op_end; o += blockDim.x)
+        for (int o = run.op_begin + threadIdx.x; o < run.op_end; o += THREADS)
             gpart[((size_t)b * n_ops + (ops[o].op_s0 & 0x7FFFFFFFu)) * tile_stride + blockIdx.x] = 0.0;
         return;
     }
@@ -296,89 +468,109 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     int2 *lists = reinterpret_cast<int2 *>(tl + run.max_entries);
     const int lstride = run.max_da + run.max_db;
     COpDev *sops;
-    const SweepArgs la = stage_tables(run, sa, ops, reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops);
+    V2<R> *scs;
+    const SweepArgs la = stage_run<R>(run, sa, ops, cs + (size_t)b * n_ops,
+                                      reinterpret_cast<unsigned char *>(lists + 2 * lstride), &sops, &scs);
     __syncthreads();
     make_view(run, la, &v);
     const int D = v.Da * v.Db;
     V2<R> *sp = phi + (size_t)b * N;
     V2<R> *sl = lam + (size_t)b * N;
-    const int nw = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool builder = (int)threadIdx.x >= RL::kCompute;
+    const int bl = (int)threadIdx.x - RL::kCompute;  // builder lane
     const int nops = run.op_end - run.op_begin;
-    for (int e = threadIdx.x; e < D; e += blockDim.x) {
+    for (int e = threadIdx.x; e < D; e += THREADS) {
         const uint32_t x = entry_index(v, e);
         tp[e] = sp[x];
         tl[e] = sl[x];
     }
-    if (nops > 0) {
-        const PairSet p0 = pair_set(run, la, v, sops[nops - 1]);
-        build_sides(p0, v, sops[nops - 1], lists, lists + p0.Va);
-    }
+    if (builder && nops > 0)
+        build_factor<R, RL::kBuildLanes>(run, la, v, sops[nops - 1], scs[nops - 1], lists, &hdr[0], bl);
     __syncthreads();
-    int it = 0, buf = 0;
-    for (int o = nops - 1; o >= 0; --o) {
-        const COpDev &op = sops[o];
-        const PairSet p = pair_set(run, la, v, op);
-        int2 *A = lists + buf * lstride;
-        int2 *B = A + p.Va;
-        if (o - 1 >= 0) {
-            const PairSet pn = pair_set(run, la, v, sops[o - 1]);
-            int2 *An = lists + (buf ^ 1) * lstride;
-            build_sides(pn, v, sops[o - 1], An, An + pn.Va);
-        }
-        const int P = p.Va * p.Vb;
-        const int opi = (int)(op.op_s0 & 0x7FFFFFFFu);
-        const size_t gidx = ((size_t)b * n_ops + opi) * tile_stride + blockIdx.x;
-        R part = (R)0;
-        if (P > 0) {
-            const V2<R> csv = cs[(size_t)b * n_ops + opi];
-            const R ct = csv.x;
-            const R st0 = (op.op_s0 >> 31) ? -csv.y : csv.y;
-            const int rpar = __popc(v.rest & op.par_rest) & 1;
-            const float inv = 1.0f / (float)p.Vb;
-            for (int j = threadIdx.x; j < P; j += blockDim.x) {
-                int ja, jb;
-                split_index(j, p.Vb, inv, &ja, &jb);
-                const int2 a2 = A[ja], b2 = B[jb];
-                const int e = (a2.x & 0x7FFFFFFF) + (b2.x & 0x7FFFFFFF);
-                const int e2 = a2.y + b2.y;
-                const bool neg = ((((unsigned)(a2.x ^ b2.x)) >> 31) ^ rpar) & 1;
-                const V2<R> fa = tp[e], fb = tp[e2];
-                const V2<R> la = tl[e], lb = tl[e2];
-                // (G phi)_x = -s phi_x', (G phi)_x' = s phi_x
-                const R d = (lb.x * fa.x + lb.y * fa.y) - (la.x * fb.x + la.y * fb.y);
-                part += neg ? -d : d;
-                const R ss = neg ? -st0 : st0;
-                V2<R> w;
-                w.x = ct * fa.x + ss * fb.x;
-                w.y = ct * fa.y + ss * fb.y;
-                tp[e] = w;
-                w.x = ct * fb.x - ss * fa.x;
-                w.y = ct * fb.y - ss * fa.y;
-                tp[e2] = w;
-                w.x = ct * la.x + ss * lb.x;
-                w.y = ct * la.y + ss * lb.y;
-                tl[e] = w;
-                w.x = ct * lb.x - ss * la.x;
-                w.y = ct * lb.y - ss * la.y;
-                tl[e2] = w;
+    // the first builder warp writes the partial of the previous iteration's
+    // factor, summed over the compute warps in a fixed order
+    auto flush_partial = [&](int it, int o) {
+        double s2 = (lane < RL::kComputeWarps) ? wring[it & 1][lane] : 0.0;
+        s2 = warp_sum<double>(s2);
+        if (lane == 0)
+            gpart[((size_t)b * n_ops + (sops[o].op_s0 & 0x7FFFFFFFu)) * tile_stride + blockIdx.x] = s2;
+    };
+    int it = 0;
+    for (int o = nops - 1; o >= 0; --o, ++it) {
+        const int buf = it & 1;
+        if (builder) {
+            if (it > 0 && bl < 32) flush_partial(it - 1, o + 1);
+            if (o - 1 >= 0)
+                build_factor<R, RL::kBuildLanes>(run, la, v, sops[o - 1], scs[o - 1],
+                                                 lists + (buf ^ 1) * lstride, &hdr[buf ^ 1], bl);
+        } else {
+            const OpHdr<R> h = hdr[buf];
+            const int P = h.Va * h.Vb;
+            const int2 *A = lists + buf * lstride;
+            const int2 *B = A + h.Va;
+            R part = (R)0;
+            if ((int)threadIdx.x < P) {
+                PairWalk wk;
+                wk.init(threadIdx.x, RL::kCompute, h.Vb);
+                int ja = wk.ja, jb = wk.jb;
+                int j = threadIdx.x;
+                // two disjoint pairs per iteration: all loads before any store;
+                // the partial carries the string and rest parities, the
+                // factor's own sign is applied to the warp sum
+                for (; j + RL::kCompute < P; j += 2 * RL::kCompute) {
+                    int ja1 = ja, jb1 = jb;
+                    wk.next(&ja1, &jb1);
+                    int e0, f0, e1, f1;
+                    uint32_t q0, q1;
+                    pair_offsets(A[ja], B[jb], &e0, &f0, &q0);
+                    pair_offsets(A[ja1], B[jb1], &e1, &f1, &q1);
+                    V2<R> fa = tp[e0], fb = tp[f0], la0 = tl[e0], lb0 = tl[f0];
+                    V2<R> ga = tp[e1], gb = tp[f1], ma = tl[e1], mb = tl[f1];
+                    part += flip_sign(pair_dot<R>(fa, fb, la0, lb0), q0 ^ h.rneg);
+                    part += flip_sign(pair_dot<R>(ga, gb, ma, mb), q1 ^ h.rneg);
+                    const R s0 = flip_sign(h.st, q0), s1 = flip_sign(h.st, q1);
+                    // U(-theta): rotate with -s
+                    rotate_pair<R>(h.ct, -s0, fa, fb);
+                    rotate_pair<R>(h.ct, -s0, la0, lb0);
+                    rotate_pair<R>(h.ct, -s1, ga, gb);
+                    rotate_pair<R>(h.ct, -s1, ma, mb);
+                    tp[e0] = fa;
+                    tp[f0] = fb;
+                    tl[e0] = la0;
+                    tl[f0] = lb0;
+                    tp[e1] = ga;
+                    tp[f1] = gb;
+                    tl[e1] = ma;
+                    tl[f1] = mb;
+                    ja = ja1;
+                    jb = jb1;
+                    wk.next(&ja, &jb);
+                }
+                if (j < P) {
+                    int e0, f0;
+                    uint32_t q0;
+                    pair_offsets(A[ja], B[jb], &e0, &f0, &q0);
+                    V2<R> fa = tp[e0], fb = tp[f0], la0 = tl[e0], lb0 = tl[f0];
+                    part += flip_sign(pair_dot<R>(fa, fb, la0, lb0), q0 ^ h.rneg);
+                    const R s0 = flip_sign(h.st, q0);
+                    rotate_pair<R>(h.ct, -s0, fa, fb);
+                    rotate_pair<R>(h.ct, -s0, la0, lb0);
+                    tp[e0] = fa;
+                    tp[f0] = fb;
+                    tl[e0] = la0;
+                    tl[f0] = lb0;
+                }
             }
+            // per-warp partial in the state precision (a few products per
+            // thread), then FP64 across the compute warps
+            const R ws = warp_sum(part);
+            if (lane == 0) wring[buf][warp] = flip_sign((double)ws, h.opneg);
         }
-        // per-warp partial in the state precision (<= 32 thread partials of a
-        // few products each), then FP64 across warps, tiles and factors
-        const double dp = (op.op_s0 >> 31) ? -(double)warp_sum(part) : (double)warp_sum(part);
-        const int rb = it & 1;
-        ++it;
-        if (lane == 0) wring[rb][warp] = dp;
         __syncthreads();
-        if (warp == 0) {
-            double s2 = (lane < nw) ? wring[rb][lane] : 0.0;
-            s2 = warp_sum<double>(s2);
-            if (lane == 0) gpart[gidx] = s2;
-        }
-        buf ^= 1;
     }
-    for (int e = threadIdx.x; e < D; e += blockDim.x) {
+    if (builder && bl < 32 && nops > 0) flush_partial(it - 1, 0);
+    for (int e = threadIdx.x; e < D; e += THREADS) {
         const uint32_t x = entry_index(v, e);
         sp[x] = tp[e];
         sl[x] = tl[e];
