@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -500,6 +502,94 @@ uccsd_status eval(uccsd_ctx *c, int B, const double *theta, int on_dev, double *
     return run_eval<double>(c, B, theta, on_dev, E, grad, s);
 }
 
+// Precomputed pair lists of a plan (sweeps over lists instead of building
+// side lists per factor): at most kMaxListPairs pairs (8 bytes each) per
+// plan, larger plans keep the builder kernels.  Lists depend only on the
+// plan, so a process-wide cache keyed by a hash of the plan serves repeated
+// contexts of the same shape.
+constexpr size_t kMaxListPairs = size_t(16) << 20;
+
+uint64_t plan_hash(const uccsd_ctx *c, const SweepPlan &pl) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    };
+    const int hdr[4] = {c->n, c->n_alpha, c->n_beta, c->prec};
+    mix(hdr, sizeof(hdr));
+    for (CRunDev r : pl.runs) {
+        r.pl_base = 0;
+        mix(&r, sizeof(r));
+    }
+    mix(pl.ops.data(), pl.ops.size() * sizeof(COpDev));
+    return h;
+}
+
+struct CachedLists {
+    std::shared_ptr<PairLists> lists;  // null: over the size limit
+    std::vector<int32_t> pl_base;
+};
+
+std::mutex g_list_mu;
+std::vector<std::pair<uint64_t, CachedLists>> g_list_cache;  // most recent last, at most 8
+
+CachedLists cached_lists(const uccsd_ctx *c, SweepPlan *pl, uint64_t key) {
+    {
+        std::lock_guard<std::mutex> lk(g_list_mu);
+        for (auto &kv : g_list_cache)
+            if (kv.first == key) return kv.second;
+    }
+    CachedLists cl;
+    auto L = std::make_shared<PairLists>();
+    // 8-byte amplitudes: 16 lanes per shared-memory wavefront; 16-byte: 8
+    if (build_pair_lists(c->n, c->n_alpha, c->n_beta, kMaxListPairs, pl, L.get(), c->prec ? 16 : 8))
+        cl.lists = L;
+    for (const CRunDev &r : pl->runs) cl.pl_base.push_back(r.pl_base);
+    std::lock_guard<std::mutex> lk(g_list_mu);
+    g_list_cache.emplace_back(key, cl);
+    if (g_list_cache.size() > 8) g_list_cache.erase(g_list_cache.begin());
+    return cl;
+}
+
+// Attach pair lists to a plan and its sweep arguments (tag "fwd" / "adj").
+// Without lists (too large, or over the HBM budget) the plan keeps the
+// builder kernels.
+uccsd_status attach_lists(uccsd_ctx *c, SweepPlan *pl, SweepArgs *args, const std::string &tag) {
+    args->op_pl = nullptr;
+    args->pairs = nullptr;
+    const uint64_t key = plan_hash(c, *pl);
+    CachedLists cl = cached_lists(c, pl, key);
+    for (size_t r = 0; r < pl->runs.size(); ++r) pl->runs[r].pl_base = cl.lists ? cl.pl_base[r] : -1;
+    uint64_t &held = c->list_key[tag == "fwd" ? 0 : 1];
+    if (!cl.lists) {
+        release(c, tag + "_pl");
+        release(c, tag + "_pairs");
+        held = 0;
+        return UCCSD_OK;
+    }
+    if (held != key || !dptr(c, tag + "_pl") || !dptr(c, tag + "_pairs")) {
+        // (re)upload unless this context already holds the lists of the same plan
+        const PairLists &L = *cl.lists;
+        int32_t *p2;
+        uint32_t *p4;
+        held = 0;
+        uccsd_status st = upload(c, tag + "_pl", L.op_pl, &p2);
+        if (st == UCCSD_OK) st = upload(c, tag + "_pairs", L.pairs, &p4);
+        if (st == UCCSD_ERR_BUDGET) {
+            release(c, tag + "_pl");
+            release(c, tag + "_pairs");
+            for (CRunDev &r : pl->runs) r.pl_base = -1;
+            c->err.clear();
+            return UCCSD_OK;
+        }
+        if (st) return st;
+        held = key;
+    }
+    args->op_pl = static_cast<const int2 *>(dptr(c, tag + "_pl"));
+    args->pairs = static_cast<const uint2 *>(dptr(c, tag + "_pairs"));
+    return UCCSD_OK;
+}
+
 // Plan of the Trotter-free ansatz: every excitation once, two vectors (u
 // read, w accumulated) per shared-memory tile.
 uccsd_status prepare_trotter_free(uccsd_ctx *c) {
@@ -520,6 +610,8 @@ uccsd_status prepare_trotter_free(uccsd_ctx *c) {
     if ((st = upload(c, "tf_spread", c->tf.spread, &p4))) return st;
     c->tf_args = c->fwd_args;
     c->tf_args.spread = p4;
+    c->tf_args.op_pl = nullptr;
+    c->tf_args.pairs = nullptr;
     if ((st = dalloc(c, "tf_coef", sizeof(double) * std::max(c->K, 1), &p))) return st;
     for (const char *name : {"tf_u", "tf_w"}) {
         if ((st = dalloc(c, name, state_elems(c) * amp_bytes(c), &p))) return st;
@@ -977,6 +1069,8 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->fwd_args.spread = p4;
     if ((st = upload(c, "adj_spread", c->adj.spread, &p4))) return st;
     c->adj_args.spread = p4;
+    if ((st = attach_lists(c, &c->fwd, &c->fwd_args, "fwd"))) return st;
+    if ((st = attach_lists(c, &c->adj, &c->adj_args, "adj"))) return st;
     c->have_exc = true;
     c->state_valid = false;
     return alloc_slots(c);

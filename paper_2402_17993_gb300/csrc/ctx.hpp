@@ -43,6 +43,7 @@ struct uccsd_ctx {
     std::vector<double> op_scale;
     uccsd::SweepPlan fwd, adj;
     uccsd::SweepArgs fwd_args, adj_args;
+    uint64_t list_key[2] = {0, 0};  // plan hashes of the pair lists held (forward, adjoint)
     std::vector<uccsd::CompiledExc> exc;  // list order
     // Trotter-free ansatz: plan with every excitation once (built on first use)
     uccsd::SweepPlan tf;

@@ -74,6 +74,9 @@ struct SweepArgs {
     const uint32_t *spread = nullptr;    // per run: tile string -> orbital string
     const uint32_t *aoff = nullptr;      // state addressing (see HSector)
     const uint32_t *boff = nullptr;
+    // precomputed pair lists (PairLists of plan.hpp), null when the plan has none
+    const int2 *op_pl = nullptr;
+    const uint2 *pairs = nullptr;
     uint32_t amask = 0;                  // alpha qubits (even positions)
     int n_alpha = 0, n_beta = 0;
 };

@@ -107,8 +107,8 @@ void max_tile_sides(int n_qubits, int n_alpha, int n_beta, uint32_t tmask, long 
 
 size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
                         int nvec, int n_ops_run, int lmax) {
-    size_t b = size_t(entries) * amp_bytes * nvec + 2 * size_t(da + db) * 8 +
-               size_t(n_ops_run) * (sizeof(COpDev) + amp_bytes);
+    size_t b = size_t(tile_alloc(entries)) * amp_bytes * nvec + 2 * size_t(da + db) * 8 +
+               size_t(n_ops_run) * (sizeof(COpDev) + amp_bytes + 8);
     if (lmax <= kStageLmax) b += sweep_table_bytes(lmax);
     return b;
 }
@@ -154,6 +154,7 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
             ++e;
         }
         CRunDev r{};
+        r.pl_base = -1;
         r.tmask = U;
         r.rmask = all & ~U;
         const uint32_t Ta = U & amask, Tb = U & bmask;
@@ -195,6 +196,192 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
         o = e;
     }
     return plan;
+}
+
+namespace {
+// Insert a zero bit at each set bit position of mask, lowest first.
+uint32_t insert_zeros_host(uint32_t j, uint32_t mask) {
+    for (; mask; mask &= mask - 1u) {
+        const uint32_t lowm = (mask & (0u - mask)) - 1u;
+        j = ((j & ~lowm) << 1) | (j & lowm);
+    }
+    return j;
+}
+}  // namespace
+
+namespace {
+// Conflict-free grouping of one factor's pairs.  With G lanes served by one
+// shared-memory wavefront, pair (e, e') is an edge between residue e mod G
+// (left) and e' mod G (right) of a bipartite multigraph; a proper edge
+// colouring puts at most one pair of each left and each right residue in a
+// colour, so every colour class is a conflict-free group.  A bipartite
+// multigraph of maximum degree D has a proper D-colouring (Konig); it is
+// built edge by edge, swapping two colours along an alternating path when
+// the endpoints have no common free colour.  Each class is padded to G
+// pairs with dummy pairs on zeroed scratch entries scratch + r (e side) and
+// scratch + G + r (e' side) for residues r unused by the class.  Returns the
+// padded list (2 words per pair).
+std::vector<uint32_t> bank_groups(const uint32_t *pairs, int P, int G, uint32_t scratch) {
+    std::vector<uint32_t> out;
+    if (P <= 0) return out;
+    std::vector<int> deg(2 * G, 0);
+    for (int i = 0; i < P; ++i) {
+        deg[(pairs[2 * i] & 0x7FFFFFFFu) % G]++;
+        deg[G + pairs[2 * i + 1] % G]++;
+    }
+    const int D = *std::max_element(deg.begin(), deg.end());
+    // at[node * D + c] = edge of colour c at node, or -1
+    std::vector<int> at(size_t(2 * G) * D, -1), col(P, -1), eu(P), ev(P);
+    for (int i = 0; i < P; ++i) {
+        eu[i] = int((pairs[2 * i] & 0x7FFFFFFFu) % G);
+        ev[i] = G + int(pairs[2 * i + 1] % G);
+    }
+    auto free_col = [&](int node) {
+        for (int c = 0; c < D; ++c)
+            if (at[size_t(node) * D + c] < 0) return c;
+        return -1;
+    };
+    for (int i = 0; i < P; ++i) {
+        const int u = eu[i], v = ev[i];
+        const int a = free_col(u), b = free_col(v);
+        if (at[size_t(v) * D + a] >= 0) {
+            // a is used at v: swap a and b along the path from v that starts
+            // with its a-edge (it cannot reach u, so a becomes free at v)
+            std::vector<int> path;
+            int node = v, c = a;
+            for (;;) {
+                const int ed = at[size_t(node) * D + c];
+                if (ed < 0) break;
+                path.push_back(ed);
+                node = (node == eu[ed]) ? ev[ed] : eu[ed];
+                c = (c == a) ? b : a;
+            }
+            for (int ed : path) {
+                at[size_t(eu[ed]) * D + col[ed]] = -1;
+                at[size_t(ev[ed]) * D + col[ed]] = -1;
+            }
+            for (int ed : path) {
+                col[ed] = (col[ed] == a) ? b : a;
+                at[size_t(eu[ed]) * D + col[ed]] = ed;
+                at[size_t(ev[ed]) * D + col[ed]] = ed;
+            }
+        }
+        col[i] = a;
+        at[size_t(u) * D + a] = i;
+        at[size_t(v) * D + a] = i;
+    }
+    out.reserve(size_t(2) * D * G);
+    for (int c = 0; c < D; ++c) {
+        uint32_t used_e = 0, used_f = 0;
+        int m = 0;
+        for (int r = 0; r < G; ++r) {
+            const int ed = at[size_t(r) * D + c];
+            if (ed < 0) continue;
+            out.push_back(pairs[2 * ed]);
+            out.push_back(pairs[2 * ed + 1]);
+            used_e |= 1u << eu[ed];
+            used_f |= 1u << (ev[ed] - G);
+            ++m;
+        }
+        for (int re = 0, rf = 0; m < G; ++m) {
+            while (used_e >> re & 1u) ++re;
+            while (used_f >> rf & 1u) ++rf;
+            out.push_back(scratch + uint32_t(re++));
+            out.push_back(scratch + uint32_t(G + rf++));
+        }
+    }
+    return out;
+}
+}  // namespace
+
+bool build_pair_lists(int n_qubits, int n_alpha, int n_beta, size_t max_pairs, SweepPlan *plan,
+                      PairLists *out, int bank_group) {
+    std::vector<uint16_t> combos, rank;
+    std::vector<int32_t> offs;
+    build_comb_tables(&combos, &rank, &offs);
+    auto cnt = [&](int m, int k) { return (k < 0 || k > m) ? 0 : offs[m * 17 + k + 1] - offs[m * 17 + k]; };
+    auto strings = [&](int m, int k) { return &combos[((size_t(1) << m) - 1) + offs[m * 17 + k]]; };
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
+    // size first
+    size_t total = 0, n_pl = 0;
+    for (const CRunDev &r : plan->runs) {
+        const int nops = r.op_end - r.op_begin;
+        const int ra = popc(r.rmask & amask), rb = popc(r.rmask & ~amask);
+        n_pl += size_t(r.La + 1) * (r.Lb + 1) * nops;
+        for (int a = 0; a <= r.La; ++a)
+            for (int b = 0; b <= r.Lb; ++b) {
+                if (n_alpha - a < 0 || n_alpha - a > ra || n_beta - b < 0 || n_beta - b > rb) continue;
+                for (int o = r.op_begin; o < r.op_end; ++o) {
+                    const COpDev &op = plan->ops[o];
+                    total += size_t(cnt(r.La - popc(op.fa), a - popc(op.oa))) *
+                             size_t(cnt(r.Lb - popc(op.fb), b - popc(op.ob)));
+                }
+            }
+    }
+    if (total > max_pairs) {
+        for (CRunDev &r : plan->runs) r.pl_base = -1;
+        return false;
+    }
+    out->pairs.clear();
+    out->pairs.reserve(2 * total + 2 * total / 4);
+    out->op_pl.assign(2 * n_pl, 0);
+    size_t pos = 0, plb = 0;
+    std::vector<uint32_t> raw;
+    std::vector<uint32_t> ea, ea2, eb, eb2;
+    std::vector<uint8_t> pa_, pb_;
+    for (CRunDev &r : plan->runs) {
+        const int nops = r.op_end - r.op_begin;
+        const int ra = popc(r.rmask & amask), rb = popc(r.rmask & ~amask);
+        r.pl_base = int32_t(plb);
+        const uint16_t *rka = &rank[(size_t(1) << r.La) - 1];
+        const uint16_t *rkb = &rank[(size_t(1) << r.Lb) - 1];
+        for (int a = 0; a <= r.La; ++a)
+            for (int b = 0; b <= r.Lb; ++b) {
+                const size_t cbase = plb + (size_t(a) * (r.Lb + 1) + b) * nops;
+                if (n_alpha - a < 0 || n_alpha - a > ra || n_beta - b < 0 || n_beta - b > rb) continue;
+                const uint32_t Db = uint32_t(cnt(r.Lb, b));
+                for (int o = 0; o < nops; ++o) {
+                    const COpDev &op = plan->ops[r.op_begin + o];
+                    const int ma = r.La - popc(op.fa), ka = a - popc(op.oa);
+                    const int mb = r.Lb - popc(op.fb), kb = b - popc(op.ob);
+                    const int Va = cnt(ma, ka), Vb = cnt(mb, kb);
+                    out->op_pl[2 * (cbase + o)] = int32_t(pos);
+                    out->op_pl[2 * (cbase + o) + 1] = 0;
+                    if (!Va || !Vb) continue;
+                    ea.resize(Va); ea2.resize(Va); pa_.resize(Va);
+                    eb.resize(Vb); eb2.resize(Vb); pb_.resize(Vb);
+                    const uint16_t *fa = strings(ma, ka), *fb = strings(mb, kb);
+                    for (int i = 0; i < Va; ++i) {
+                        const uint32_t sv = insert_zeros_host(fa[i], op.fa) | op.oa;
+                        ea[i] = uint32_t(rka[sv]) * Db;
+                        ea2[i] = uint32_t(rka[sv ^ op.fa]) * Db;
+                        pa_[i] = uint8_t(popc(sv & op.pa) & 1);
+                    }
+                    for (int i = 0; i < Vb; ++i) {
+                        const uint32_t sv = insert_zeros_host(fb[i], op.fb) | op.ob;
+                        eb[i] = rkb[sv];
+                        eb2[i] = rkb[sv ^ op.fb];
+                        pb_[i] = uint8_t(popc(sv & op.pb) & 1);
+                    }
+                    raw.resize(2 * size_t(Va) * Vb);
+                    size_t q = 0;
+                    for (int i = 0; i < Va; ++i)
+                        for (int j = 0; j < Vb; ++j) {
+                            raw[q++] = (ea[i] + eb[j]) | (uint32_t(pa_[i] ^ pb_[j]) << 31);
+                            raw[q++] = ea2[i] + eb2[j];
+                        }
+                    const std::vector<uint32_t> g =
+                        bank_groups(raw.data(), Va * Vb, bank_group, tile_scratch(r.max_entries));
+                    out->pairs.insert(out->pairs.end(), g.begin(), g.end());
+                    out->op_pl[2 * (cbase + o) + 1] = int32_t(g.size() / 2);
+                    pos += g.size() / 2;
+                }
+            }
+        plb += size_t(r.La + 1) * (r.Lb + 1) * nops;
+    }
+    out->n_pairs = pos;
+    return true;
 }
 
 void build_comb_tables(std::vector<uint16_t> *combos, std::vector<uint16_t> *rank,

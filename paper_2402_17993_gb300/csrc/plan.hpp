@@ -21,6 +21,18 @@ std::vector<int32_t> build_uccsd_list(int n_orb, int n_alpha, int n_beta);
 void build_schedule(int K, int order, int M, std::vector<int32_t> *op_k,
                     std::vector<double> *op_scale);
 
+// Shared-memory tile of a run: the largest compact tile rounded up to 16
+// entries, then 32 zeroed scratch entries that the padding pairs of the
+// precomputed lists rotate (no effect: they stay zero).
+constexpr int kTileScratch = 32;
+#ifdef __CUDACC__
+#define UCCSD_HD __host__ __device__
+#else
+#define UCCSD_HD
+#endif
+UCCSD_HD inline int tile_scratch(int max_entries) { return (max_entries + 15) & ~15; }
+UCCSD_HD inline int tile_alloc(long long max_entries) { return tile_scratch(int(max_entries)) + kTileScratch; }
+
 struct SweepPlan {
     std::vector<CRunDev> runs;
     std::vector<COpDev> ops;       // ops of run r at [runs[r].op_begin, runs[r].op_end)
@@ -43,8 +55,8 @@ constexpr int kStageLmax = 10;
 size_t sweep_table_bytes(int lmax);
 // Shared memory of one sweep CTA: nvec tiles, the two double-buffered
 // alpha/beta pair-side lists (8 bytes per string), the run's factor
-// descriptors and cos/sin values (one amplitude each) and (lmax <=
-// kStageLmax) the staged tables.
+// descriptors, cos/sin values (one amplitude each) and pair-list entries
+// (8 bytes each) and (lmax <= kStageLmax) the staged tables.
 size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t amp_bytes,
                         int nvec, int n_ops_run, int lmax);
 
@@ -54,6 +66,29 @@ size_t sweep_smem_bytes(long long entries, long long da, long long db, size_t am
 SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, int nvec,
                      size_t budget, const std::vector<CompiledExc> &exc,
                      const std::vector<int32_t> &op_k);
+
+// Precomputed pair lists of a sweep plan.  For every run, every electron
+// count class (a, b) of its tiles (class index a * (Lb + 1) + b) and every
+// factor of the run, the factor's pairs in tile-entry coordinates: pair word
+// 2i = e | (string parity << 31) with e the occupied-side entry, word 2i + 1
+// = the partner entry e'.  The pairs of (run r, class c, factor o) start at
+// pair op_pl[2 * (runs[r].pl_base + c * n_ops_r + o)] and number
+// op_pl[2 * (...) + 1].  Within a factor the pairs come in aligned groups of
+// bank_group pairs (the lanes of one shared-memory wavefront: 16 for 8-byte,
+// 8 for 16-byte amplitudes) whose e and e' are distinct modulo bank_group,
+// so no group has a bank conflict; groups are completed with padding pairs
+// on the tile's scratch entries (tile_scratch(max_entries) + r), which hold
+// zeros, so the counts include the padding.
+struct PairLists {
+    std::vector<uint32_t> pairs;
+    std::vector<int32_t> op_pl;
+    size_t n_pairs = 0;
+};
+
+// Fill `out` and set runs[r].pl_base for every run; false (plan untouched,
+// pl_base = -1) when the lists would hold more than max_pairs pairs.
+bool build_pair_lists(int n_qubits, int n_alpha, int n_beta, size_t max_pairs, SweepPlan *plan,
+                      PairLists *out, int bank_group);
 
 // Combinatorial tables for bit strings of m <= kCombMax bits: for each m,
 // the 2^m strings sorted by (popcount, value) at combos[2^m - 1 ...], the

@@ -190,11 +190,13 @@ __device__ __forceinline__ SweepArgs stage_tables(const CRunDev &run, const Swee
 }
 
 // As stage_tables, with the run's cos/sin values (of slot csb, gathered by
-// factor) staged right after the factor descriptors.
+// factor) staged right after the factor descriptors and, when cls_pl is
+// given, the tile class's pair-list entries (offset, count) after them.
 template <typename R>
 __device__ __forceinline__ SweepArgs stage_run(const CRunDev &run, const SweepArgs &sa,
                                                const COpDev *ops, const V2<R> *csb,
-                                               unsigned char *base, COpDev **sops, V2<R> **scs) {
+                                               unsigned char *base, COpDev **sops, V2<R> **scs,
+                                               const int2 *cls_pl = nullptr, int2 **spl = nullptr) {
     const int nops = run.op_end - run.op_begin;
     COpDev *so = reinterpret_cast<COpDev *>(base);
     const uint32_t *gsrc = reinterpret_cast<const uint32_t *>(ops + run.op_begin);
@@ -205,10 +207,15 @@ __device__ __forceinline__ SweepArgs stage_run(const CRunDev &run, const SweepAr
         c[t] = csb[ops[run.op_begin + t].op_s0 & 0x7FFFFFFFu];
     *sops = so;
     *scs = c;
+    int2 *pl = reinterpret_cast<int2 *>(c + nops);
+    if (spl) {
+        for (int t = threadIdx.x; t < nops; t += blockDim.x) pl[t] = cls_pl[t];
+        *spl = pl;
+    }
     SweepArgs la = sa;
     const int lmax = max(run.La, run.Lb);
     if (lmax <= kStageLmax) {
-        int32_t *offs = reinterpret_cast<int32_t *>(c + nops);
+        int32_t *offs = reinterpret_cast<int32_t *>(pl + nops);
         const int n_offs = (lmax + 1) * 17;
         uint16_t *cmb = reinterpret_cast<uint16_t *>(offs + n_offs);
         const int n_str = (1 << (lmax + 1)) - 1;
@@ -577,6 +584,268 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sweeps over precomputed pair lists (plans whose lists fit the budget).
+// Every warp rotates pairs; each thread holds its first pairs of the next
+// two factors in registers (loaded two factors ahead), so a factor's
+// critical path is the barrier, two shared-memory loads per pair, the
+// rotation and the stores.
+// ---------------------------------------------------------------------------
+// Pairs per thread held in registers, loaded two factors ahead.
+template <typename R>
+struct ListPre {
+    static constexpr int kFwd = sizeof(R) == 4 ? 8 : 4;
+    static constexpr int kAdj = sizeof(R) == 4 ? 4 : 2;
+};
+
+template <int KP>
+__device__ __forceinline__ void fetch_pairs(uint2 (&dst)[KP], const uint2 *__restrict__ pairs,
+                                            int2 pl, int t, int threads) {
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        const int j = t + k * threads;
+        dst[k] = j < pl.y ? __ldg(pairs + pl.x + j) : make_uint2(0u, 0u);
+    }
+}
+
+template <typename R, int THREADS, int KP>
+__device__ __forceinline__ void forward_list_step(int o, int nops, V2<R> *tile, const COpDev *sops,
+                                                  const V2<R> *scs, const int2 *spl,
+                                                  const uint2 *__restrict__ pairs, uint32_t rest,
+                                                  uint2 (&cur)[KP], uint2 (&nxt)[KP]) {
+    const int t = threadIdx.x;
+    if (o + 2 < nops) fetch_pairs<KP>(nxt, pairs, spl[o + 2], t, THREADS);
+    const int2 pl = spl[o];
+    const COpDev &op = sops[o];
+    const V2<R> csv = scs[o];
+    const uint32_t rneg = (uint32_t)(__popc(rest & op.par_rest) & 1) << 31;
+    const R ct = csv.x, st = flip_sign(csv.y, (op.op_s0 & 0x80000000u) ^ rneg);
+    // the prefetched pairs in chunks of two: loads of a chunk before its stores
+#pragma unroll
+    for (int k0 = 0; k0 < KP; k0 += 2) {
+        V2<R> x[2], y[2];
+#pragma unroll
+        for (int k = k0; k < k0 + 2 && k < KP; ++k)
+            if (t + k * THREADS < pl.y) {
+                x[k - k0] = tile[cur[k].x & 0x7FFFFFFFu];
+                y[k - k0] = tile[cur[k].y];
+            }
+#pragma unroll
+        for (int k = k0; k < k0 + 2 && k < KP; ++k)
+            if (t + k * THREADS < pl.y) {
+                rotate_pair<R>(ct, flip_sign(st, cur[k].x), x[k - k0], y[k - k0]);
+                tile[cur[k].x & 0x7FFFFFFFu] = x[k - k0];
+                tile[cur[k].y] = y[k - k0];
+            }
+    }
+    // further pairs: loads issued four at a time
+    for (int j0 = t + KP * THREADS; j0 < pl.y; j0 += 4 * THREADS) {
+        uint2 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            q[k] = j0 + k * THREADS < pl.y ? __ldg(pairs + pl.x + j0 + k * THREADS) : make_uint2(0u, 0u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (j0 + k * THREADS < pl.y) {
+                V2<R> a = tile[q[k].x & 0x7FFFFFFFu], c = tile[q[k].y];
+                rotate_pair<R>(ct, flip_sign(st, q[k].x), a, c);
+                tile[q[k].x & 0x7FFFFFFFu] = a;
+                tile[q[k].y] = c;
+            }
+    }
+    __syncthreads();
+}
+
+template <typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS) forward_list_kernel(
+    V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
+    const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf) {
+    constexpr int KP = ListPre<R>::kFwd;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
+    TileView v;
+    if (!make_view(run, sa, &v)) return;  // no sector entries in this tile
+    const int b = blockIdx.y;
+    const int nops = run.op_end - run.op_begin;
+    const int cls = v.a * (run.Lb + 1) + v.b;
+    COpDev *sops;
+    V2<R> *scs;
+    int2 *spl;
+    const SweepArgs la = stage_run<R>(run, sa, ops, cs + (size_t)b * n_ops,
+                                      reinterpret_cast<unsigned char *>(tile + tile_alloc(run.max_entries)),
+                                      &sops, &scs, sa.op_pl + run.pl_base + (size_t)cls * nops, &spl);
+    if (threadIdx.x < kTileScratch)  // padding pairs rotate these zeros
+        tile[tile_scratch(run.max_entries) + threadIdx.x] = V2<R>{(R)0, (R)0};
+    __syncthreads();
+    make_view(run, la, &v);
+    V2<R> *st = psi + (size_t)b * N;
+    const int D = v.Da * v.Db;
+    for (int e = threadIdx.x; e < D; e += THREADS) {
+        const uint32_t x = entry_index(v, e);
+        V2<R> val;
+        if (init_hf) {
+            val.x = (R)(x == hf ? 1 : 0);
+            val.y = (R)0;
+        } else {
+            val = st[x];
+        }
+        tile[e] = val;
+    }
+    uint2 p0[KP], p1[KP], p2[KP];
+    if (nops > 0) fetch_pairs<KP>(p0, sa.pairs, spl[0], threadIdx.x, THREADS);
+    if (nops > 1) fetch_pairs<KP>(p1, sa.pairs, spl[1], threadIdx.x, THREADS);
+    __syncthreads();
+    for (int o = 0; o < nops; o += 3) {
+        forward_list_step<R, THREADS, KP>(o, nops, tile, sops, scs, spl, sa.pairs, v.rest, p0, p2);
+        if (o + 1 < nops)
+            forward_list_step<R, THREADS, KP>(o + 1, nops, tile, sops, scs, spl, sa.pairs, v.rest, p1, p0);
+        if (o + 2 < nops)
+            forward_list_step<R, THREADS, KP>(o + 2, nops, tile, sops, scs, spl, sa.pairs, v.rest, p2, p1);
+    }
+    for (int e = threadIdx.x; e < D; e += THREADS) st[entry_index(v, e)] = tile[e];
+}
+
+// One adjoint factor over precomputed pairs: un-rotates phi and lambda and
+// leaves the warp partial of Re <lambda|G|phi> (string and rest parities and
+// the factor's sign applied) in wring[it & 1][warp]; warp 0 first writes the
+// previous factor's partial, summed over the warps in a fixed order.
+template <typename R, int THREADS, int KP>
+__device__ __forceinline__ void adjoint_list_step(int o, int it, int nops, V2<R> *tp, V2<R> *tl,
+                                                  const COpDev *sops, const V2<R> *scs,
+                                                  const int2 *spl, const uint2 *__restrict__ pairs,
+                                                  uint32_t rest, double (*wring)[32],
+                                                  uint2 (&cur)[KP], uint2 (&nxt)[KP],
+                                                  double *__restrict__ gp, int tile_stride) {
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (warp == 0 && it > 0) {
+        double s2 = (lane < THREADS / 32) ? wring[(it - 1) & 1][lane] : 0.0;
+        s2 = warp_sum<double>(s2);
+        if (lane == 0) gp[(size_t)(sops[o + 1].op_s0 & 0x7FFFFFFFu) * tile_stride] = s2;
+    }
+    if (o - 2 >= 0) fetch_pairs<KP>(nxt, pairs, spl[o - 2], t, THREADS);
+    const int2 pl = spl[o];
+    const COpDev &op = sops[o];
+    const V2<R> csv = scs[o];
+    const uint32_t rneg = (uint32_t)(__popc(rest & op.par_rest) & 1) << 31;
+    const R ct = csv.x, st = flip_sign(csv.y, (op.op_s0 & 0x80000000u) ^ rneg);
+    R part = (R)0;
+    auto one = [&](uint2 q, V2<R> &fa, V2<R> &fb, V2<R> &la0, V2<R> &lb0) {
+        const uint32_t e = q.x & 0x7FFFFFFFu, e2 = q.y;
+        part += flip_sign(pair_dot<R>(fa, fb, la0, lb0), q.x ^ rneg);
+        const R s = flip_sign(st, q.x);
+        rotate_pair<R>(ct, -s, fa, fb);
+        rotate_pair<R>(ct, -s, la0, lb0);
+        tp[e] = fa;
+        tp[e2] = fb;
+        tl[e] = la0;
+        tl[e2] = lb0;
+    };
+    // the prefetched pairs in chunks of two: loads of a chunk before its stores
+#pragma unroll
+    for (int k0 = 0; k0 < KP; k0 += 2) {
+        V2<R> f[2], g[2], l[2], m[2];
+#pragma unroll
+        for (int k = k0; k < k0 + 2 && k < KP; ++k)
+            if (t + k * THREADS < pl.y) {
+                const uint32_t e = cur[k].x & 0x7FFFFFFFu, e2 = cur[k].y;
+                f[k - k0] = tp[e];
+                g[k - k0] = tp[e2];
+                l[k - k0] = tl[e];
+                m[k - k0] = tl[e2];
+            }
+#pragma unroll
+        for (int k = k0; k < k0 + 2 && k < KP; ++k)
+            if (t + k * THREADS < pl.y) one(cur[k], f[k - k0], g[k - k0], l[k - k0], m[k - k0]);
+    }
+    // further pairs: loads issued four at a time
+    for (int j0 = t + KP * THREADS; j0 < pl.y; j0 += 4 * THREADS) {
+        uint2 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            q[k] = j0 + k * THREADS < pl.y ? __ldg(pairs + pl.x + j0 + k * THREADS) : make_uint2(0u, 0u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (j0 + k * THREADS < pl.y) {
+                const uint32_t e = q[k].x & 0x7FFFFFFFu, e2 = q[k].y;
+                V2<R> fa = tp[e], fb = tp[e2], la0 = tl[e], lb0 = tl[e2];
+                one(q[k], fa, fb, la0, lb0);
+            }
+    }
+    const R ws = warp_sum(part);
+    if (lane == 0) wring[it & 1][warp] = flip_sign((double)ws, op.op_s0 & 0x80000000u);
+    __syncthreads();
+}
+
+template <typename R, int THREADS>
+__global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
+    V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
+    const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
+    double *__restrict__ gpart, int tile_stride) {
+    constexpr int KP = ListPre<R>::kAdj;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double wring[2][32];
+    const int b = blockIdx.y;
+    TileView v;
+    if (!make_view(run, sa, &v)) {
+        // all-zero tile: its gradient partials are zero
+        for (int o = run.op_begin + threadIdx.x; o < run.op_end; o += THREADS)
+            gpart[((size_t)b * n_ops + (ops[o].op_s0 & 0x7FFFFFFFu)) * tile_stride + blockIdx.x] = 0.0;
+        return;
+    }
+    V2<R> *tp = reinterpret_cast<V2<R> *>(smem_raw);
+    V2<R> *tl = tp + tile_alloc(run.max_entries);
+    const int nops = run.op_end - run.op_begin;
+    const int cls = v.a * (run.Lb + 1) + v.b;
+    COpDev *sops;
+    V2<R> *scs;
+    int2 *spl;
+    const SweepArgs la = stage_run<R>(run, sa, ops, cs + (size_t)b * n_ops,
+                                      reinterpret_cast<unsigned char *>(tl + tile_alloc(run.max_entries)),
+                                      &sops, &scs, sa.op_pl + run.pl_base + (size_t)cls * nops, &spl);
+    if (threadIdx.x < kTileScratch) {  // padding pairs rotate these zeros
+        tp[tile_scratch(run.max_entries) + threadIdx.x] = V2<R>{(R)0, (R)0};
+        tl[tile_scratch(run.max_entries) + threadIdx.x] = V2<R>{(R)0, (R)0};
+    }
+    __syncthreads();
+    make_view(run, la, &v);
+    const int D = v.Da * v.Db;
+    V2<R> *sp = phi + (size_t)b * N;
+    V2<R> *sl = lam + (size_t)b * N;
+    for (int e = threadIdx.x; e < D; e += THREADS) {
+        const uint32_t x = entry_index(v, e);
+        tp[e] = sp[x];
+        tl[e] = sl[x];
+    }
+    // gradient partials of this slot and tile: gp[op_index * tile_stride]
+    double *gp = gpart + (size_t)b * n_ops * tile_stride + blockIdx.x;
+    uint2 p0[KP], p1[KP], p2[KP];
+    if (nops > 0) fetch_pairs<KP>(p0, sa.pairs, spl[nops - 1], threadIdx.x, THREADS);
+    if (nops > 1) fetch_pairs<KP>(p1, sa.pairs, spl[nops - 2], threadIdx.x, THREADS);
+    __syncthreads();
+    for (int it = 0; it < nops; it += 3) {
+        const int o = nops - 1 - it;
+        adjoint_list_step<R, THREADS, KP>(o, it, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
+                                          wring, p0, p2, gp, tile_stride);
+        if (it + 1 < nops)
+            adjoint_list_step<R, THREADS, KP>(o - 1, it + 1, nops, tp, tl, sops, scs, spl, sa.pairs,
+                                              v.rest, wring, p1, p0, gp, tile_stride);
+        if (it + 2 < nops)
+            adjoint_list_step<R, THREADS, KP>(o - 2, it + 2, nops, tp, tl, sops, scs, spl, sa.pairs,
+                                              v.rest, wring, p2, p1, gp, tile_stride);
+    }
+    if (nops > 0 && (threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        double s2 = (lane < THREADS / 32) ? wring[(nops - 1) & 1][lane] : 0.0;
+        s2 = warp_sum<double>(s2);
+        if (lane == 0) gp[(size_t)(sops[0].op_s0 & 0x7FFFFFFFu) * tile_stride] = s2;
+    }
+    for (int e = threadIdx.x; e < D; e += THREADS) {
+        const uint32_t x = entry_index(v, e);
+        sp[x] = tp[e];
+        sl[x] = tl[e];
+    }
+}
+
 // Trotter-free ansatz (Eq. 3): w = scale * sum_k coef_k G_k u over the
 // factors of one run of a plan that holds every excitation once.  u is read
 // only; w is accumulated across the runs of the plan (the first run starts
@@ -816,6 +1085,15 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
                                          run.op_end - run.op_begin, max(run.La, run.Lb));
     V2<R> *p = static_cast<V2<R> *>(psi);
     const V2<R> *c = static_cast<const V2<R> *>(cs);
+    if (run.pl_base >= 0 && sa.pairs) {
+        if (run.max_entries >= kLargeTile)
+            forward_list_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
+                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+        else
+            forward_list_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
+                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+        return cudaGetLastError();
+    }
     if (run.max_entries >= kLargeTile)
         forward_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
             p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
@@ -835,6 +1113,15 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
     V2<R> *f = static_cast<V2<R> *>(phi);
     V2<R> *l = static_cast<V2<R> *>(lam);
     const V2<R> *c = static_cast<const V2<R> *>(cs);
+    if (run.pl_base >= 0 && sa.pairs) {
+        if (run.max_entries >= kLargeTile)
+            adjoint_list_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
+                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+        else
+            adjoint_list_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
+                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+        return cudaGetLastError();
+    }
     if (run.max_entries >= kLargeTile)
         adjoint_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
             f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
@@ -938,6 +1225,14 @@ cudaError_t configure_sweep_kernels(size_t max_smem) {
     UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<float, kSweepThreadsSmall>))
     UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<double, kSweepThreadsLarge>))
     UCCSD_SWEEP_ATTR((adjoint_sweep_kernel<double, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((forward_list_kernel<float, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((forward_list_kernel<float, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((forward_list_kernel<double, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((forward_list_kernel<double, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((adjoint_list_kernel<float, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((adjoint_list_kernel<float, kSweepThreadsSmall>))
+    UCCSD_SWEEP_ATTR((adjoint_list_kernel<double, kSweepThreadsLarge>))
+    UCCSD_SWEEP_ATTR((adjoint_list_kernel<double, kSweepThreadsSmall>))
     UCCSD_SWEEP_ATTR((gen_apply_kernel<float, kSweepThreadsLarge>))
     UCCSD_SWEEP_ATTR((gen_apply_kernel<float, kSweepThreadsSmall>))
     UCCSD_SWEEP_ATTR((gen_apply_kernel<double, kSweepThreadsLarge>))

@@ -70,10 +70,20 @@ def footprint_bytes(n_orb: int, n_alpha: int, n_beta: int, precision: int) -> in
     n = 2 * n_orb
     N = 1 << n
     A = 8 if precision == FP32_STATE else 16
-    K = len(build_uccsd_list(n_orb, n_alpha, n_beta))
+    ijab = build_uccsd_list(n_orb, n_alpha, n_beta)
+    K = len(ijab)
     tiles = max(1, N >> 10)
     tables = 200 * (n_orb ** 4) + (4 << 20)
-    return 2 * N * A + K * tiles * 8 + K * 256 + tables
+    # precomputed pair lists: the pairs of each excitation on the whole sector
+    # (exact for one-tile plans), for the forward plan and up to twice that
+    # for the adjoint plan, 8 bytes per pair
+    from math import comb
+    pairs = 0
+    for i, j, a, b in ijab.tolist():
+        na = sum(1 for q in (i, j, a, b) if q >= 0 and q % 2 == 0) // 2
+        nb = sum(1 for q in (i, j, a, b) if q >= 0 and q % 2 == 1) // 2
+        pairs += (comb(n_orb - 2 * na, n_alpha - na) * comb(n_orb - 2 * nb, n_beta - nb))
+    return 2 * N * A + K * tiles * 8 + K * 256 + tables + 3 * 8 * pairs
 
 
 class _Slot:
