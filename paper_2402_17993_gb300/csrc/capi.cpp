@@ -33,6 +33,7 @@ int pair_idx(int p, int q) { return q * (q - 1) / 2 + p; }  // p < q
 template <typename R>
 struct HamTables {
     std::vector<MixT<R>> mix;
+    std::vector<MixO<R>> mixo;
     std::vector<SglT<R>> s1a, s1b;
     std::vector<DblT<R>> d2a, d2b;
     std::vector<R> spec;
@@ -98,6 +99,20 @@ bool make_tables(const CompiledH &H, int n_orb, HamTables<R> *T, std::string *er
     }
     for (double v : H.spec) T->spec.push_back(R(v));
     if (T->spec.empty()) T->spec.push_back(R(0));
+    // ordered view of the mixed groups (target occupies p and j; the source
+    // occupies q and b: asel = q > p, bsel = b > j)
+    T->mixo.assign(size_t(n_orb) * n_orb * n_orb * n_orb, MixO<R>{});
+    for (int p = 0; p < n_orb; ++p)
+        for (int q = 0; q < n_orb; ++q)
+            for (int jj = 0; jj < n_orb; ++jj)
+                for (int b = 0; b < n_orb; ++b) {
+                    if (p == q || jj == b) continue;
+                    const MixT<R> &M = T->mix[size_t(pair_idx(std::min(p, q), std::max(p, q))) * np +
+                                              pair_idx(std::min(jj, b), std::max(jj, b))];
+                    MixO<R> &O = T->mixo[((size_t(p) * n_orb + q) * n_orb + jj) * n_orb + b];
+                    O.w = M.lut[(q > p ? 1 : 0) + 2 * (b > jj ? 1 : 0)];
+                    O.j = M.j;
+                }
     return true;
 }
 
@@ -196,12 +211,14 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     if (!make_tables<R>(c->H, c->n_orb, &T, &err)) return fail(c, UCCSD_ERR_ARG, err);
     std::string t(tag);
     MixT<R> *mx;
+    MixO<R> *mo;
     SglT<R> *sa, *sb;
     DblT<R> *da, *db;
     R *sp;
     long long *qa, *qb;
     uccsd_status st;
     if ((st = upload(c, t + "mix", T.mix, &mx))) return st;
+    if ((st = upload(c, t + "mixo", T.mixo, &mo))) return st;
     if ((st = upload(c, t + "s1a", T.s1a, &sa))) return st;
     if ((st = upload(c, t + "s1b", T.s1b, &sb))) return st;
     if ((st = upload(c, t + "d2a", T.d2a, &da))) return st;
@@ -210,6 +227,7 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     if ((st = upload(c, "diag_qa", c->diag_qa, &qa))) return st;
     if ((st = upload(c, "diag_qb", c->diag_qb, &qb))) return st;
     dh->mix = mx;
+    dh->mixo = mo;
     dh->s1a = sa;
     dh->s1b = sb;
     dh->d2a = da;

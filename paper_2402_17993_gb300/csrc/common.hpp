@@ -44,6 +44,15 @@ struct MixT {
     R lut[4];
     uint32_t j;
 };
+// The same mixed groups by ordered excitation: entry ((p n + q) n + j) n + b
+// of an n_orb^4 array holds, for a target with alpha p occupied and q empty
+// and beta j occupied and b empty (the source flips both pairs), the LUT
+// value of that source pattern and the group's Jordan-Wigner mask.
+template <typename R>
+struct alignas(sizeof(R) == 4 ? 8 : 16) MixO {
+    R w;
+    uint32_t j;
+};
 // Same-spin single (pair): lut[sel] at the source occupying the higher
 // (sel = 1) or lower orbital; spectator rows start at spec (rows of 4,
 // pattern 1 = lower occupied, 2 = higher occupied).

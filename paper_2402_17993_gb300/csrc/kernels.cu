@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             const int pa = pair_index(min(p, q), max(p, q));
             const int asel = q > p;
             const SglT<R> &S = H.s1a[pa];
-            const MixT<R> *Mrow = H.mix + (size_t)pa * H.n_pairs;
+            const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * n_orb * n_orb;
 #pragma unroll
             for (int i = 0; i < EPT; ++i) {
                 if (cix[i] < 0) continue;
@@ -282,12 +282,13 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                 V2<R> seg = V2<R>{(R)0, (R)0};
                 for (uint32_t o = cb_str; o; o &= o - 1u) {
                     const int j = __ffs(o) - 1;
+                    const MixO<R> *Mj = Mrow + j * n_orb;
+                    const uint32_t yj = cb_str ^ (1u << j);
                     for (uint32_t v = vir; v; v &= v - 1u) {
                         const int bb = __ffs(v) - 1;
-                        const MixT<R> &M = Mrow[pair_index(min(j, bb), max(j, bb))];
-                        const uint32_t yb = cb_str ^ (1u << j) ^ (1u << bb);
-                        R w = M.lut[asel + 2 * (bb > j)];
-                        if (jw_parity(sRp, yb, M.j)) w = -w;
+                        const MixO<R> M = Mj[bb];
+                        const uint32_t yb = yj ^ (1u << bb);
+                        const R w = jw_parity(sRp, yb, M.j) ? -M.w : M.w;
                         const V2<R> y = src[brk[yb]];
                         seg.x += w * y.x;
                         seg.y += w * y.y;

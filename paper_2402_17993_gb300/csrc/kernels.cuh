@@ -13,6 +13,7 @@ namespace uccsd {
 template <typename R>
 struct DevHam {
     const MixT<R> *mix = nullptr;  // [n_pairs * n_pairs], alpha pair major
+    const MixO<R> *mixo = nullptr; // [n_orb^4], ordered alpha and beta excitations
     const SglT<R> *s1a = nullptr;  // [n_pairs] alpha singles
     const SglT<R> *s1b = nullptr;  // [n_pairs] beta singles
     const DblT<R> *d2a = nullptr;  // [n_quads] alpha doubles
