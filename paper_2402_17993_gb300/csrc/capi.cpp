@@ -33,7 +33,7 @@ int pair_idx(int p, int q) { return q * (q - 1) / 2 + p; }  // p < q
 template <typename R>
 struct HamTables {
     std::vector<MixT<R>> mix;
-    std::vector<MixO<R>> mixo;
+    std::vector<MixO<R>> mixo, d2ao, d2bo;
     std::vector<SglT<R>> s1a, s1b;
     std::vector<DblT<R>> d2a, d2b;
     std::vector<R> spec;
@@ -113,6 +113,29 @@ bool make_tables(const CompiledH &H, int n_orb, HamTables<R> *T, std::string *er
                     O.w = M.lut[(q > p ? 1 : 0) + 2 * (b > jj ? 1 : 0)];
                     O.j = M.j;
                 }
+    // ordered view of the same-spin doubles
+    const size_t n4 = size_t(n_orb) * n_orb * n_orb * n_orb;
+    for (int spin = 0; spin < 2; ++spin) {
+        std::vector<MixO<R>> &dst = spin ? T->d2bo : T->d2ao;
+        const std::vector<DblT<R>> &src = spin ? T->d2b : T->d2a;
+        dst.assign(n4, MixO<R>{});
+        for (int o1 = 0; o1 < n_orb; ++o1)
+            for (int o2 = o1 + 1; o2 < n_orb; ++o2)
+                for (int v1 = 0; v1 < n_orb; ++v1)
+                    for (int v2 = v1 + 1; v2 < n_orb; ++v2) {
+                        if (v1 == o1 || v1 == o2 || v2 == o1 || v2 == o2) continue;
+                        int q[4] = {o1, o2, v1, v2};
+                        std::sort(q, q + 4);
+                        const DblT<R> &D = src[binom_int(q[3], 4) + binom_int(q[2], 3) +
+                                               binom_int(q[1], 2) + q[0]];
+                        int pat = 0;
+                        for (int k = 0; k < 4; ++k)
+                            if (q[k] == v1 || q[k] == v2) pat |= 1 << k;
+                        MixO<R> &O = dst[((size_t(o1) * n_orb + o2) * n_orb + v1) * n_orb + v2];
+                        O.w = D.lut[pat];
+                        O.j = D.j;
+                    }
+    }
     return true;
 }
 
@@ -211,7 +234,7 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     if (!make_tables<R>(c->H, c->n_orb, &T, &err)) return fail(c, UCCSD_ERR_ARG, err);
     std::string t(tag);
     MixT<R> *mx;
-    MixO<R> *mo;
+    MixO<R> *mo, *oa, *ob;
     SglT<R> *sa, *sb;
     DblT<R> *da, *db;
     R *sp;
@@ -219,6 +242,8 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     uccsd_status st;
     if ((st = upload(c, t + "mix", T.mix, &mx))) return st;
     if ((st = upload(c, t + "mixo", T.mixo, &mo))) return st;
+    if ((st = upload(c, t + "d2ao", T.d2ao, &oa))) return st;
+    if ((st = upload(c, t + "d2bo", T.d2bo, &ob))) return st;
     if ((st = upload(c, t + "s1a", T.s1a, &sa))) return st;
     if ((st = upload(c, t + "s1b", T.s1b, &sb))) return st;
     if ((st = upload(c, t + "d2a", T.d2a, &da))) return st;
@@ -228,6 +253,8 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     if ((st = upload(c, "diag_qb", c->diag_qb, &qb))) return st;
     dh->mix = mx;
     dh->mixo = mo;
+    dh->d2ao = oa;
+    dh->d2bo = ob;
     dh->s1a = sa;
     dh->s1b = sb;
     dh->d2a = da;

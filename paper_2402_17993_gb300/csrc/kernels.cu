@@ -216,25 +216,17 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             const int j1 = __ffs(o1) - 1;
             for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
                 const int j2 = __ffs(o2) - 1;
+                const MixO<R> *Dj = H.d2bo + (size_t)(j1 * n_orb + j2) * n_orb * n_orb;
+                const uint32_t yj = cb_str ^ (1u << j1) ^ (1u << j2);
                 V2<R> seg = V2<R>{(R)0, (R)0};  // plain partial per occupied pair
                 for (uint32_t v1 = vir; v1; v1 &= v1 - 1u) {
                     const int b1 = __ffs(v1) - 1;
+                    const MixO<R> *Db1 = Dj + b1 * n_orb;
                     for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
                         const int b2 = __ffs(v2) - 1;
-                        // sorted quad and the ranks of b1 < b2 in it
-                        const uint32_t m = (1u << j1) | (1u << j2) | (1u << b1) | (1u << b2);
-                        uint32_t t = m;
-                        const int q0 = __ffs(t) - 1; t &= t - 1u;
-                        const int q1 = __ffs(t) - 1; t &= t - 1u;
-                        const int q2 = __ffs(t) - 1; t &= t - 1u;
-                        const int q3 = __ffs(t) - 1;
-                        const int qi = nb4[q3 * 5 + 4] + nb4[q2 * 5 + 3] + nb4[q1 * 5 + 2] + q0;
-                        const int rb1 = __popc(m & ((1u << b1) - 1u));
-                        const int rb2 = __popc(m & ((1u << b2) - 1u));
-                        const DblT<R> &Dq = H.d2b[qi];
-                        const uint32_t yb = cb_str ^ m;
-                        R val = Dq.lut[(1 << rb1) | (1 << rb2)];
-                        if (jw_parity(sR, yb, Dq.j)) val = -val;
+                        const MixO<R> D = Db1[b2];
+                        const uint32_t yb = yj ^ (1u << b1) ^ (1u << b2);
+                        const R val = jw_parity(sR, yb, D.j) ? -D.w : D.w;
                         const V2<R> y = src[brk[yb]];
                         seg.x += val * y.x;
                         seg.y += val * y.y;
@@ -304,23 +296,16 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         const int p1 = __ffs(o1) - 1;
         for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
             const int p2 = __ffs(o2) - 1;
+            const MixO<R> *Dp = H.d2ao + (size_t)(p1 * n_orb + p2) * n_orb * n_orb;
             for (uint32_t v1 = virA; v1; v1 &= v1 - 1u) {
                 const int q1 = __ffs(v1) - 1;
                 for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
                     const int q2 = __ffs(v2) - 1;
                     const uint32_t m = (1u << p1) | (1u << p2) | (1u << q1) | (1u << q2);
-                    uint32_t t = m;
-                    const int k0 = __ffs(t) - 1; t &= t - 1u;
-                    const int k1 = __ffs(t) - 1; t &= t - 1u;
-                    const int k2 = __ffs(t) - 1; t &= t - 1u;
-                    const int k3 = __ffs(t) - 1;
-                    const int qi = nb4[k3 * 5 + 4] + nb4[k2 * 5 + 3] + nb4[k1 * 5 + 2] + k0;
-                    const int rq1 = __popc(m & ((1u << q1) - 1u));
-                    const int rq2 = __popc(m & ((1u << q2) - 1u));
-                    const DblT<R> &Dq = H.d2a[qi];
+                    const MixO<R> Dq = Dp[q1 * n_orb + q2];
                     const uint32_t sRp = sR ^ m;
                     const uint32_t xRp = hs.aoff[sRp];
-                    const R base = Dq.lut[(1 << rq1) | (1 << rq2)];
+                    const R base = Dq.w;
 #pragma unroll
                     for (int i = 0; i < EPT; ++i) {
                         if (cix[i] < 0) continue;

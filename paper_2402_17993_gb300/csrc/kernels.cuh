@@ -14,6 +14,11 @@ template <typename R>
 struct DevHam {
     const MixT<R> *mix = nullptr;  // [n_pairs * n_pairs], alpha pair major
     const MixO<R> *mixo = nullptr; // [n_orb^4], ordered alpha and beta excitations
+    // same-spin doubles by ordered target pattern: entry ((o1 n + o2) n + v1) n + v2
+    // (o1 < o2 occupied and v1 < v2 empty in the target) holds the LUT value of
+    // the source occupying v1, v2 and the group's Jordan-Wigner mask
+    const MixO<R> *d2ao = nullptr;
+    const MixO<R> *d2bo = nullptr;
     const SglT<R> *s1a = nullptr;  // [n_pairs] alpha singles
     const SglT<R> *s1b = nullptr;  // [n_pairs] beta singles
     const DblT<R> *d2a = nullptr;  // [n_quads] alpha doubles
