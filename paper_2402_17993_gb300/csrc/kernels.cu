@@ -120,6 +120,14 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 256;
 
+// Dynamic shared memory of the H-apply: one source row, the beta string
+// ranks, then (8-byte aligned) the per-row alpha-spectator sums.
+template <typename R>
+__host__ __device__ inline size_t happly_aspec_offset(int Db, int n_orb) {
+    const size_t o = sizeof(V2<R>) * (size_t)Db + sizeof(uint16_t) * ((size_t)1 << n_orb);
+    return (o + 7) & ~(size_t)7;
+}
+
 __device__ __forceinline__ int pair_index(int p, int q) {  // p < q
     return (q * (q - 1) >> 1) + p;
 }
@@ -137,8 +145,11 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *src = reinterpret_cast<V2<R> *>(smem_raw);                  // one source row
     uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
+    // alpha-spectator part of each beta single's value for this row, [pair][sel]
+    R *aspec = reinterpret_cast<R *>(smem_raw + happly_aspec_offset<R>(hs.Db, H.n_orb));
     __shared__ double red[32];
     __shared__ int nb4[16 * 5];
+    __shared__ R a_single;  // alpha part of the current alpha single's value
     const int b = blockIdx.y;
     const int row = blockIdx.x / hs.ncb;
     const int cb = blockIdx.x - row * hs.ncb;
@@ -148,6 +159,16 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     const V2<R> *st = psi + (size_t)b * N;
     for (int t = threadIdx.x; t < (1 << n_orb); t += blockDim.x) brk[t] = hs.brank[t];
     for (int t = threadIdx.x; t < 16 * 5; t += blockDim.x) nb4[t] = hs.binom[t];
+    for (int t = threadIdx.x; t < 2 * H.n_pairs; t += blockDim.x) {
+        const SglT<R> &S = H.s1b[t >> 1];
+        R val = (R)0;
+        if (S.spec >= 0) {
+            const int pat = (t & 1) ? 2 : 1;
+            for (uint32_t w = sR; w; w &= w - 1u)
+                val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + pat];
+        }
+        aspec[t] = val;
+    }
     {
         const uint32_t xR = hs.aoff[sR];
         for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
@@ -197,14 +218,13 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             for (uint32_t v = vir; v; v &= v - 1u) {
                 const int bb = __ffs(v) - 1;
                 const int lo = min(j, bb), hi = max(j, bb);
-                const SglT<R> &S = H.s1b[pair_index(lo, hi)];
+                const int pb = pair_index(lo, hi);
+                const SglT<R> &S = H.s1b[pb];
                 const int sel = bb > j;
                 const uint32_t yb = cb_str ^ (1u << j) ^ (1u << bb);
-                R val = S.lut[sel];
+                R val = S.lut[sel] + aspec[2 * pb + sel];
                 if (S.spec >= 0) {
                     const int pat = sel ? 2 : 1;
-                    for (uint32_t w = sR; w; w &= w - 1u)
-                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + pat];
                     for (uint32_t w = yb & ~(1u << bb); w; w &= w - 1u)
                         val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
                 }
@@ -245,24 +265,30 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             const int q = __ffs(vq) - 1;
             const uint32_t sRp = sR ^ (1u << p) ^ (1u << q);
             const uint32_t xRp = hs.aoff[sRp];
-            __syncthreads();
-            for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
-                src[c] = st[xRp + hs.boff[hs.bstr[c]]];
-            __syncthreads();
             const int pa = pair_index(min(p, q), max(p, q));
             const int asel = q > p;
             const SglT<R> &S = H.s1a[pa];
+            __syncthreads();
+            for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
+                src[c] = st[xRp + hs.boff[hs.bstr[c]]];
+            if (threadIdx.x == 0) {
+                // the value's alpha part: the same for every column
+                R va = S.lut[asel];
+                if (S.spec >= 0)
+                    for (uint32_t w = sRp & ~(1u << q); w; w &= w - 1u)
+                        va += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + (asel ? 2 : 1)];
+                a_single = va;
+            }
+            __syncthreads();
             const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * n_orb * n_orb;
 #pragma unroll
             for (int i = 0; i < EPT; ++i) {
                 if (cix[i] < 0) continue;
                 const uint32_t cb_str = sc[i];
                 // alpha-only pair group: same column
-                R val = S.lut[asel];
+                R val = a_single;
                 if (S.spec >= 0) {
                     const int pat = asel ? 2 : 1;
-                    for (uint32_t w = sRp & ~(1u << q); w; w &= w - 1u)
-                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + pat];
                     for (uint32_t w = cb_str; w; w &= w - 1u)
                         val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
                 }
@@ -297,6 +323,9 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
             const int p2 = __ffs(o2) - 1;
             const MixO<R> *Dp = H.d2ao + (size_t)(p1 * n_orb + p2) * n_orb * n_orb;
+            V2<R> dseg[EPT];  // plain partial per occupied pair
+#pragma unroll
+            for (int i = 0; i < EPT; ++i) dseg[i] = V2<R>{(R)0, (R)0};
             for (uint32_t v1 = virA; v1; v1 &= v1 - 1u) {
                 const int q1 = __ffs(v1) - 1;
                 for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
@@ -309,11 +338,16 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
 #pragma unroll
                     for (int i = 0; i < EPT; ++i) {
                         if (cix[i] < 0) continue;
-                        R val = jw_parity(sRp, sc[i], Dq.j) ? -base : base;
-                        accumulate<R>(acc[i], comp[i], val, st[xRp + hs.boff[sc[i]]]);
+                        const R val = jw_parity(sRp, sc[i], Dq.j) ? -base : base;
+                        const V2<R> y = st[xRp + hs.boff[sc[i]]];
+                        dseg[i].x += val * y.x;
+                        dseg[i].y += val * y.y;
                     }
                 }
             }
+#pragma unroll
+            for (int i = 0; i < EPT; ++i)
+                if (cix[i] >= 0) accumulate<R>(acc[i], comp[i], (R)1, dseg[i]);
         }
     }
 
@@ -392,7 +426,7 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
 // ---------------------------------------------------------------------------
 template <typename R>
 size_t happly_smem(const HSector &hs, int n_orb) {
-    return sizeof(V2<R>) * (size_t)hs.Db + sizeof(uint16_t) * ((size_t)1 << n_orb);
+    return happly_aspec_offset<R>(hs.Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1);
 }
 
 template <typename R>
