@@ -132,9 +132,18 @@ __device__ __forceinline__ int pair_index(int p, int q) {  // p < q
     return (q * (q - 1) >> 1) + p;
 }
 
-__device__ __forceinline__ int jw_parity(uint32_t ya, uint32_t yb, uint32_t j) {
-    return (__popc(ya & (j & 0xFFFFu)) + __popc(yb & (j >> 16))) & 1;
+// Sign bit (bit 31) of the Jordan-Wigner parity of a group with mask j (alpha
+// bits low, beta bits high) at the source strings packed as ya | yb << 16.
+__device__ __forceinline__ uint32_t jw_sign(uint32_t packed, uint32_t j) {
+    return (uint32_t)__popc(packed & j) << 31;
 }
+__device__ __forceinline__ float with_sign(float x, uint32_t s) {
+    return __int_as_float(__float_as_int(x) ^ (int)(s & 0x80000000u));
+}
+__device__ __forceinline__ double with_sign(double x, uint32_t s) {
+    return __hiloint2double(__double2hiint(x) ^ (int)(s & 0x80000000u), __double2loint(x));
+}
+
 
 template <typename R, int EPT>
 __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__restrict__ psi,
@@ -228,7 +237,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                     for (uint32_t w = yb & ~(1u << bb); w; w &= w - 1u)
                         val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
                 }
-                if (jw_parity(sR, yb, S.j)) val = -val;
+                val = with_sign(val, jw_sign(sR | (yb << 16), S.j));
                 accumulate<R>(acc[i], comp[i], val, src[brk[yb]]);
             }
         }
@@ -242,11 +251,12 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                 for (uint32_t v1 = vir; v1; v1 &= v1 - 1u) {
                     const int b1 = __ffs(v1) - 1;
                     const MixO<R> *Db1 = Dj + b1 * n_orb;
+                    const uint32_t y1 = yj ^ (1u << b1);
                     for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
                         const int b2 = __ffs(v2) - 1;
                         const MixO<R> D = Db1[b2];
-                        const uint32_t yb = yj ^ (1u << b1) ^ (1u << b2);
-                        const R val = jw_parity(sR, yb, D.j) ? -D.w : D.w;
+                        const uint32_t yb = y1 ^ (1u << b2);
+                        const R val = with_sign(D.w, jw_sign(sR | (yb << 16), D.j));
                         const V2<R> y = src[brk[yb]];
                         seg.x += val * y.x;
                         seg.y += val * y.y;
@@ -292,7 +302,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                     for (uint32_t w = cb_str; w; w &= w - 1u)
                         val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
                 }
-                if (jw_parity(sRp, cb_str, S.j)) val = -val;
+                val = with_sign(val, jw_sign(sRp | (cb_str << 16), S.j));
                 accumulate<R>(acc[i], comp[i], val, src[cix[i]]);
                 // mixed groups through the lane's beta single excitations:
                 // a plain partial sum per segment, added with compensation
@@ -302,11 +312,13 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                     const int j = __ffs(o) - 1;
                     const MixO<R> *Mj = Mrow + j * n_orb;
                     const uint32_t yj = cb_str ^ (1u << j);
+                    const uint32_t xj = sRp | (yj << 16);  // packed source strings
                     for (uint32_t v = vir; v; v &= v - 1u) {
                         const int bb = __ffs(v) - 1;
                         const MixO<R> M = Mj[bb];
-                        const uint32_t yb = yj ^ (1u << bb);
-                        const R w = jw_parity(sRp, yb, M.j) ? -M.w : M.w;
+                        const uint32_t bit = 1u << bb;
+                        const uint32_t yb = yj ^ bit;
+                        const R w = with_sign(M.w, jw_sign(xj ^ (bit << 16), M.j));
                         const V2<R> y = src[brk[yb]];
                         seg.x += w * y.x;
                         seg.y += w * y.y;
@@ -338,7 +350,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
 #pragma unroll
                     for (int i = 0; i < EPT; ++i) {
                         if (cix[i] < 0) continue;
-                        const R val = jw_parity(sRp, sc[i], Dq.j) ? -base : base;
+                        const R val = with_sign(base, jw_sign(sRp | (sc[i] << 16), Dq.j));
                         const V2<R> y = st[xRp + hs.boff[sc[i]]];
                         dseg[i].x += val * y.x;
                         dseg[i].y += val * y.y;
