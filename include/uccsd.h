@@ -326,6 +326,26 @@ uccsd_status uccsd_magnitude_order(int K, const int32_t *ijab, const double *t, 
  * non-finite E or null arrays. */
 uccsd_status uccsd_trotter_extrapolate(int n, const int *M, const double *E, double *out);
 
+/* Host-only: the Hamiltonian of Eq. 2 under the symmetry-conserving
+ * Bravyi-Kitaev encoding with two qubits tapered off (the SCBKT encoding of
+ * Section 2.3, giving n - 2 qubits).  Spin orbitals in up-then-down order
+ * (alpha p -> p, beta p -> n/2 + p); Bravyi-Kitaev tree by recursive halving,
+ * whose node n/2 - 1 holds the alpha-electron parity and root n - 1 the total
+ * parity; those two qubits are replaced by the eigenvalues (-1)^n_alpha and
+ * (-1)^(n_alpha + n_beta) and removed.  Output terms, in the convention of
+ * uccsd_pauli_terms: H = sum coef[t] X^{xmask[t]} Z^{zmask[t]} on
+ * *n_qubits_out = 2 n_orb - 2 qubits, merged and sorted; writes min(count,
+ * cap) terms, *n_out = count.  The spectrum of the result equals that of H on
+ * the states whose alpha and total electron numbers have the parities of
+ * n_alpha and n_alpha + n_beta.  Errors: UCCSD_ERR_ARG for n_orb outside
+ * [2, 15], electron counts outside [0, n_orb], non-finite integrals or null
+ * outputs with cap > 0.  The state-vector path does not use this encoding:
+ * its electron-sector layout removes the N_alpha and N_beta symmetries
+ * entirely. */
+uccsd_status uccsd_pauli_terms_scbk(int n_orb, const double *h, const double *eri, double e_core,
+                                    int n_alpha, int n_beta, uint32_t *xmask, uint32_t *zmask,
+                                    double *coef, int cap, int *n_out, int *n_qubits_out);
+
 #ifdef __cplusplus
 }
 #endif

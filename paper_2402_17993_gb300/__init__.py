@@ -35,7 +35,7 @@ EXPORTS = [
     "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile", "uccsd_expectation_noalloc",
     "uccsd_capture", "uccsd_replay", "uccsd_mp1_amplitudes", "uccsd_magnitude_order",
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
-    "uccsd_set_layout",
+    "uccsd_set_layout", "uccsd_pauli_terms_scbk",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -108,6 +108,9 @@ def lib():
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
                                         ctypes.POINTER(ctypes.c_int)]
         L.uccsd_mp1_amplitudes.argtypes = [vp, f64p, vp]
+        L.uccsd_pauli_terms_scbk.argtypes = [ip, f64p, f64p, ctypes.c_double, ip, ip, u32p, u32p,
+                                             f64p, ip, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int)]
         L.uccsd_energy_trotter_free.argtypes = [vp, dp, ip, dp, vp]
         L.uccsd_energy_grad_trotter_free.argtypes = [vp, dp, ip, dp, dp, vp]
         L.uccsd_magnitude_order.argtypes = [ip, i32p, f64p, i32p, i32p]
@@ -174,6 +177,28 @@ def pauli_terms(n_orb, h, eri, e_core=0.0):
     if st:
         raise UCCSDError(st, "pauli_terms")
     return x, z, c
+
+
+def pauli_terms_scbk(n_orb, h, eri, e_core, n_alpha, n_beta):
+    """Symmetry-conserving Bravyi-Kitaev terms with two qubits tapered:
+    (xmask, zmask, coef, n_qubits)."""
+    L = lib()
+    h, eri = _c64(h), _c64(eri)
+    n, nq = ctypes.c_int(0), ctypes.c_int(0)
+    st = L.uccsd_pauli_terms_scbk(n_orb, _f64p(h), _f64p(eri), float(e_core), n_alpha, n_beta,
+                                  None, None, None, 0, ctypes.byref(n), ctypes.byref(nq))
+    if st:
+        raise UCCSDError(st, "pauli_terms_scbk")
+    x = np.zeros(n.value, dtype=np.uint32)
+    z = np.zeros(n.value, dtype=np.uint32)
+    c = np.zeros(n.value, dtype=np.float64)
+    u32 = ctypes.POINTER(ctypes.c_uint32)
+    st = L.uccsd_pauli_terms_scbk(n_orb, _f64p(h), _f64p(eri), float(e_core), n_alpha, n_beta,
+                                  x.ctypes.data_as(u32), z.ctypes.data_as(u32), _f64p(c), n.value,
+                                  ctypes.byref(n), ctypes.byref(nq))
+    if st:
+        raise UCCSDError(st, "pauli_terms_scbk")
+    return x, z, c, nq.value
 
 
 def magnitude_order(ijab, t):

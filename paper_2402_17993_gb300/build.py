@@ -19,7 +19,8 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libuccsd_gb300.so")
 BUILD = os.path.join(ROOT, "_build", "uccsd")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["jw.cpp", "plan.cpp", "capi.cpp", "trotter.cpp", "kernels.cu", "sweep.cu", "noalloc.cu"]
+SOURCES = ["jw.cpp", "plan.cpp", "capi.cpp", "trotter.cpp", "tapering.cpp", "kernels.cu", "sweep.cu",
+           "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -125,13 +125,13 @@ inline int pattern(uint32_t y, int nb, const int32_t *pos) {
 
 }  // namespace
 
-bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e_core,
-                         CompiledH *out, std::string *err) {
+namespace {
+// Eq. 2 as merged X^x Z^z terms, spin orbital P on qubit qubit_of[P]
+// (Jordan-Wigner strings in qubit order), sorted by (x, z); merge residue
+// |c| <= 1e-13 max|c| dropped.
+std::vector<XZTerm> eq2_terms(int n_orb, const double *h, const double *eri, double e_core,
+                              const int *qubit_of) {
     const int n = 2 * n_orb;
-    if (n_orb < 1 || n > 30) {
-        *err = "n_orb out of range";
-        return false;
-    }
     // distinct keys: 16 Z-patterns per flip mask of 0, 2 or 4 bits
     const size_t n2 = size_t(n) * (n - 1) / 2, n4 = n2 * (n - 2) * (n - 3) / 12;
     TermTable acc(16 * (1 + n2 + n4));
@@ -145,7 +145,7 @@ bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e
             if ((P & 1) != (Q & 1)) continue;
             double c = h[(P >> 1) * n_orb + (Q >> 1)];
             if (c == 0.0) continue;
-            int idx[2] = {P, Q};
+            int idx[2] = {qubit_of[P], qubit_of[Q]};
             bool dag[2] = {true, false};
             add(expand(2, idx, dag, c, buf));
         }
@@ -162,7 +162,7 @@ bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e
                     size_t p = P >> 1, q = Q >> 1, r = R >> 1, s = S >> 1;
                     double g = eri[((p * n_orb + r) * n_orb + q) * n_orb + s];
                     if (g == 0.0) continue;
-                    int idx[4] = {P, Q, S, R};
+                    int idx[4] = {qubit_of[P], qubit_of[Q], qubit_of[S], qubit_of[R]};
                     bool dag[4] = {true, true, false, false};
                     add(expand(4, idx, dag, g, buf));
                 }
@@ -180,6 +180,30 @@ bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e
     std::sort(terms.begin(), terms.end(), [](const XZTerm &a, const XZTerm &b) {
         return a.x != b.x ? a.x < b.x : a.z < b.z;
     });
+    return terms;
+}
+}  // namespace
+
+bool pauli_terms_ordered(int n_orb, const double *h, const double *eri, double e_core,
+                         const int *qubit_of, std::vector<XZTerm> *out, std::string *err) {
+    if (n_orb < 1 || 2 * n_orb > 30) {
+        *err = "n_orb out of range";
+        return false;
+    }
+    *out = eq2_terms(n_orb, h, eri, e_core, qubit_of);
+    return true;
+}
+
+bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e_core,
+                         CompiledH *out, std::string *err) {
+    const int n = 2 * n_orb;
+    if (n_orb < 1 || n > 30) {
+        *err = "n_orb out of range";
+        return false;
+    }
+    std::vector<int> ident(n);
+    for (int q = 0; q < n; ++q) ident[q] = q;
+    std::vector<XZTerm> terms = eq2_terms(n_orb, h, eri, e_core, ident.data());
 
     CompiledH H;
     H.n_qubits = n;

@@ -33,6 +33,11 @@ struct CompiledH {
 bool compile_hamiltonian(int n_orb, const double *h, const double *eri, double e_core,
                          CompiledH *out, std::string *err);
 
+// Merged X^x Z^z terms of Eq. 2 with spin orbital P on qubit qubit_of[P]
+// (Jordan-Wigner strings follow the qubit order), sorted by (x, z).
+bool pauli_terms_ordered(int n_orb, const double *h, const double *eri, double e_core,
+                         const int *qubit_of, std::vector<XZTerm> *out, std::string *err);
+
 // Generator G = tau - tau^dag of one excitation row (i, j, a, b) in the
 // X^x Z^z form, reduced to (flip mask, occupied-side mask, Jordan-Wigner
 // parity mask, sign s0) so that G|x> = s0 (-1)^{popc(x & par)} |x ^ flip>

@@ -162,3 +162,51 @@ def test_trotter_extrapolation_rejects_bad_input(uc):
                  ([1, 2, 3], [1.0, np.inf, 3.0])]:
         with pytest.raises(uc.UCCSDError):
             uc.trotter_extrapolate(M, E)
+
+
+def _dense_from_terms(x, z, c, nq):
+    N = 1 << nq
+    M = np.zeros((N, N))
+    ys = np.arange(N, dtype=np.int64)
+    for xi, zi, ci in zip(x.tolist(), z.tolist(), c.tolist()):
+        sign = 1.0 - 2.0 * (np.array([bin(int(v) & zi).count("1") & 1 for v in ys]))
+        M[ys ^ xi, ys] += ci * sign
+    return M
+
+
+@pytest.mark.parametrize("name,na,nb", [("8q", 2, 2), ("8q", 2, 1), ("12q", 3, 3)])
+def test_scbk_tapered_spectrum_equals_the_parity_sector(uc, oracle_mod, name, na, nb):
+    # the tapered (n - 2)-qubit Hamiltonian has exactly the eigenvalues of H on
+    # the states with the alpha and total electron parities of (na, na + nb)
+    w = synth.workload(name)
+    n_orb = w["n_orb"]
+    n = 2 * n_orb
+    x, z, c, nq = uc.pauli_terms_scbk(n_orb, w["h"], w["eri"], 0.0, na, nb)
+    assert nq == n - 2
+    T = _dense_from_terms(x, z, c, nq)
+    assert np.allclose(T, T.T, atol=1e-12)
+    amask = sum(1 << q for q in range(0, n, 2))
+    states = [s for s in range(1 << n)
+              if bin(s & amask).count("1") % 2 == na % 2 and bin(s).count("1") % 2 == (na + nb) % 2]
+    Hs = np.zeros((len(states), len(states)))
+    pos = {s: i for i, s in enumerate(states)}
+    for i, s in enumerate(states):
+        e = np.zeros(1 << n, dtype=np.complex128)
+        e[s] = 1.0
+        col = oracle_mod.h_apply(n_orb, w["h"], w["eri"], 0.0, e).real
+        for t_ in np.nonzero(col)[0]:
+            Hs[pos[int(t_)], i] = col[t_]
+    ev_t = np.linalg.eigvalsh(T)
+    ev_h = np.linalg.eigvalsh(Hs)
+    assert np.max(np.abs(ev_t - ev_h)) < 1e-9
+    # the sector ground state (FCI of the paper's CAS-CI) is among them
+    e_fci = oracle_mod.fci_energy(n_orb, w["h"], w["eri"], 0.0, na, nb)
+    assert np.min(np.abs(ev_t - e_fci)) < 1e-9
+
+
+def test_scbk_rejects_bad_input(uc):
+    w = synth.workload("8q")
+    with pytest.raises(uc.UCCSDError):
+        uc.pauli_terms_scbk(1, w["h"][:1, :1], w["eri"][:1, :1, :1, :1], 0.0, 1, 1)
+    with pytest.raises(uc.UCCSDError):
+        uc.pauli_terms_scbk(4, w["h"], w["eri"], 0.0, 5, 2)
