@@ -1116,6 +1116,19 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->adj_args.spread = p4;
     if ((st = attach_lists(c, &c->fwd, &c->fwd_args, "fwd"))) return st;
     if ((st = attach_lists(c, &c->adj, &c->adj_args, "adj"))) return st;
+    // gradient partial slots: the pair-list adjoint writes one per (tile, warp)
+    {
+        const bool lists = c->adj_args.pairs != nullptr;
+        int stride = 1;
+        for (const CRunDev &r : c->adj.runs) {
+            const int per = r.n_tiles * adjoint_partials_per_tile(r, lists);
+            stride = std::max(stride, per);
+            for (int o = r.op_begin; o < r.op_end; ++o)
+                c->adj.op_tiles[c->adj.ops[o].op_s0 & 0x7FFFFFFFu] = per;
+        }
+        c->adj.max_tiles = stride;
+        if ((st = upload(c, "op_tiles", c->adj.op_tiles, &p2))) return st;
+    }
     c->have_exc = true;
     c->state_valid = false;
     return alloc_slots(c);

@@ -130,6 +130,10 @@ cudaError_t launch_tf_grad_accum(const LaunchCfg &cfg, const double *gpart, int 
 template <typename R>
 cudaError_t launch_sector_copy(const LaunchCfg &cfg, void *dst, const void *src, const HSector &hs);
 
+// Gradient partial slots per tile that the adjoint launch of `run` writes:
+// one per warp for the pair-list kernels, one for the builder kernels.
+int adjoint_partials_per_tile(const CRunDev &run, bool lists);
+
 // Dynamic shared memory opt-in of the sweep kernels.
 cudaError_t configure_sweep_kernels(size_t max_smem);
 

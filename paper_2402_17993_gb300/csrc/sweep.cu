@@ -706,22 +706,16 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
 }
 
 // One adjoint factor over precomputed pairs: un-rotates phi and lambda and
-// leaves the warp partial of Re <lambda|G|phi> (string and rest parities and
-// the factor's sign applied) in wring[it & 1][warp]; warp 0 first writes the
-// previous factor's partial, summed over the warps in a fixed order.
+// writes each warp's partial of Re <lambda|G|phi> (string and rest parities
+// and the factor's sign applied) to its (tile, warp) slot of the gradient
+// partials.
 template <typename R, int THREADS, int KP>
-__device__ __forceinline__ void adjoint_list_step(int o, int it, int nops, V2<R> *tp, V2<R> *tl,
+__device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2<R> *tl,
                                                   const COpDev *sops, const V2<R> *scs,
                                                   const int2 *spl, const uint2 *__restrict__ pairs,
-                                                  uint32_t rest, double (*wring)[32],
-                                                  uint2 (&cur)[KP], uint2 (&nxt)[KP],
+                                                  uint32_t rest, uint2 (&cur)[KP], uint2 (&nxt)[KP],
                                                   double *__restrict__ gp, int tile_stride) {
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    if (warp == 0 && it > 0) {
-        double s2 = (lane < THREADS / 32) ? wring[(it - 1) & 1][lane] : 0.0;
-        s2 = warp_sum<double>(s2);
-        if (lane == 0) gp[(size_t)(sops[o + 1].op_s0 & 0x7FFFFFFFu) * tile_stride] = s2;
-    }
     if (o - 2 >= 0) fetch_pairs<KP>(nxt, pairs, spl[o - 2], t, THREADS);
     const int2 pl = spl[o];
     const COpDev &op = sops[o];
@@ -771,8 +765,12 @@ __device__ __forceinline__ void adjoint_list_step(int o, int it, int nops, V2<R>
                 one(q[k], fa, fb, la0, lb0);
             }
     }
+    // warp partial in the state precision, written per (tile, warp); the
+    // reduction sums them in a fixed order in FP64
     const R ws = warp_sum(part);
-    if (lane == 0) wring[it & 1][warp] = flip_sign((double)ws, op.op_s0 & 0x80000000u);
+    if (lane == 0)
+        gp[(size_t)(op.op_s0 & 0x7FFFFFFFu) * tile_stride + warp] =
+            flip_sign((double)ws, op.op_s0 & 0x80000000u);
     __syncthreads();
 }
 
@@ -782,14 +780,15 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
     double *__restrict__ gpart, int tile_stride) {
     constexpr int KP = ListPre<R>::kAdj;
+    constexpr int W = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double wring[2][32];
     const int b = blockIdx.y;
     TileView v;
     if (!make_view(run, sa, &v)) {
         // all-zero tile: its gradient partials are zero
-        for (int o = run.op_begin + threadIdx.x; o < run.op_end; o += THREADS)
-            gpart[((size_t)b * n_ops + (ops[o].op_s0 & 0x7FFFFFFFu)) * tile_stride + blockIdx.x] = 0.0;
+        for (int i = threadIdx.x; i < (run.op_end - run.op_begin) * W; i += THREADS)
+            gpart[((size_t)b * n_ops + (ops[run.op_begin + i / W].op_s0 & 0x7FFFFFFFu)) * tile_stride +
+                  (size_t)blockIdx.x * W + i % W] = 0.0;
         return;
     }
     V2<R> *tp = reinterpret_cast<V2<R> *>(smem_raw);
@@ -816,28 +815,22 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
         tp[e] = sp[x];
         tl[e] = sl[x];
     }
-    // gradient partials of this slot and tile: gp[op_index * tile_stride]
-    double *gp = gpart + (size_t)b * n_ops * tile_stride + blockIdx.x;
+    // gradient partials of this slot and tile: gp[op_index * tile_stride + warp]
+    double *gp = gpart + (size_t)b * n_ops * tile_stride + (size_t)blockIdx.x * W;
     uint2 p0[KP], p1[KP], p2[KP];
     if (nops > 0) fetch_pairs<KP>(p0, sa.pairs, spl[nops - 1], threadIdx.x, THREADS);
     if (nops > 1) fetch_pairs<KP>(p1, sa.pairs, spl[nops - 2], threadIdx.x, THREADS);
     __syncthreads();
     for (int it = 0; it < nops; it += 3) {
         const int o = nops - 1 - it;
-        adjoint_list_step<R, THREADS, KP>(o, it, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
-                                          wring, p0, p2, gp, tile_stride);
+        adjoint_list_step<R, THREADS, KP>(o, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest, p0, p2,
+                                          gp, tile_stride);
         if (it + 1 < nops)
-            adjoint_list_step<R, THREADS, KP>(o - 1, it + 1, nops, tp, tl, sops, scs, spl, sa.pairs,
-                                              v.rest, wring, p1, p0, gp, tile_stride);
+            adjoint_list_step<R, THREADS, KP>(o - 1, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
+                                              p1, p0, gp, tile_stride);
         if (it + 2 < nops)
-            adjoint_list_step<R, THREADS, KP>(o - 2, it + 2, nops, tp, tl, sops, scs, spl, sa.pairs,
-                                              v.rest, wring, p2, p1, gp, tile_stride);
-    }
-    if (nops > 0 && (threadIdx.x >> 5) == 0) {
-        const int lane = threadIdx.x & 31;
-        double s2 = (lane < THREADS / 32) ? wring[(nops - 1) & 1][lane] : 0.0;
-        s2 = warp_sum<double>(s2);
-        if (lane == 0) gp[(size_t)(sops[0].op_s0 & 0x7FFFFFFFu) * tile_stride] = s2;
+            adjoint_list_step<R, THREADS, KP>(o - 2, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
+                                              p2, p1, gp, tile_stride);
     }
     for (int e = threadIdx.x; e < D; e += THREADS) {
         const uint32_t x = entry_index(v, e);
@@ -1210,6 +1203,11 @@ cudaError_t launch_sector_copy(const LaunchCfg &cfg, void *dst, const void *src,
     sector_copy_kernel<R><<<blocks, 256, 0, cfg.stream>>>(static_cast<V2<R> *>(dst),
                                                           static_cast<const V2<R> *>(src), hs);
     return cudaGetLastError();
+}
+
+int adjoint_partials_per_tile(const CRunDev &run, bool lists) {
+    if (!lists || run.pl_base < 0) return 1;
+    return (run.max_entries >= kLargeTile ? kSweepThreadsLarge : kSweepThreadsSmall) / 32;
 }
 
 cudaError_t configure_sweep_kernels(size_t max_smem) {
