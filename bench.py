@@ -18,14 +18,19 @@ evaluations are independent, there is no data-path collective).
 """
 from __future__ import annotations
 
-import argparse
-import json
 import os
-import statistics
-import subprocess
-import sys
-import tempfile
-import time
+
+# one CUDA stream per active fragment in the serving measurement: allow more
+# hardware work queues than the default 8 (read when CUDA initialises)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -492,7 +497,7 @@ def serving_stream(uc, device, n_req, n_req_fp64):
     reqs = [Request(d["r"], d["t_unit"], d["n_orb"], d["n_alpha"], d["n_beta"], d["h"], d["eri"],
                     d["e_core"]) for d in frags]
     out = {}
-    srv = FragmentServer(precision=uc.FP32_STATE, device=device, max_active=64, n_streams=16)
+    srv = FragmentServer(precision=uc.FP32_STATE, device=device, max_active=64)
     srv.run(reqs[:64])  # warm the context pool and graph paths
     _, cap = srv.run(reqs)
     rate = capacity_rate(cap)

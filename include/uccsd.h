@@ -101,6 +101,24 @@ uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec,
 /* Free all device memory of the context.  NULL is accepted. */
 void uccsd_destroy(uccsd_ctx *ctx);
 
+/* Stream of the context's set-up transfers: the uploads, clears and
+ * reallocations made by uccsd_set_hamiltonian, uccsd_set_reference,
+ * uccsd_set_excitations, uccsd_set_batch and uccsd_opt_init.
+ *   stream NULL (the default): the context's own non-blocking stream; each
+ *          set-up call waits for its transfers before it returns.
+ *   stream a cudaStream_t: the transfers are enqueued on it (host arrays are
+ *          first copied to pinned staging owned by the context) and the calls
+ *          return without waiting.  Work launched later on the same stream
+ *          sees the data; the caller orders work on other streams after it,
+ *          and must not change the context's problem while earlier work that
+ *          reads it is still running.
+ * A host that sets up many contexts while others compute uses this form:
+ * a host wait on any stream can be held up by unrelated work that shares its
+ * hardware queue.  Switching streams first waits for the copies staged on the
+ * previous one.  Errors: UCCSD_ERR_STATE on a failed context, UCCSD_ERR_CUDA
+ * if that wait fails. */
+uccsd_status uccsd_set_setup_stream(uccsd_ctx *ctx, void *stream);
+
 /* Context-owned message of the last failure; valid until the next call on
  * the context.  Never NULL. */
 const char *uccsd_last_error(const uccsd_ctx *ctx);
@@ -290,6 +308,32 @@ uccsd_status uccsd_energy_trotter_free(uccsd_ctx *ctx, const double *theta, int 
  * device state is not |Psi> (uccsd_get_state returns UCCSD_ERR_STATE). */
 uccsd_status uccsd_energy_grad_trotter_free(uccsd_ctx *ctx, const double *theta, int theta_on_device,
                                             double *E, double *grad, void *stream);
+
+/* ---- Device optimiser for the serving loop (no counterpart in the paper, which
+ *      used COBYLA and Powell; Section 2.3) ---- */
+
+/* Fixed-step L-BFGS on the device (two-loop recursion, Nocedal and Wright
+ * Algorithm 7.4): memory m in [1, 32] pairs, steps capped at max_step in the
+ * max-norm, the first step -first_scale * grad; pairs with s.y <= 1e-16
+ * max(1, y.y) are not stored.  Allocates (2 m + 3) K + m doubles of state and
+ * max_steps doubles of energy history and resets them.  Requires
+ * uccsd_set_excitations (which discards the optimiser).  Errors:
+ * UCCSD_ERR_STATE, UCCSD_ERR_ARG for parameters out of range,
+ * UCCSD_ERR_BUDGET / UCCSD_ERR_OOM. */
+uccsd_status uccsd_opt_init(uccsd_ctx *ctx, int memory, double max_step, double first_scale,
+                            int max_steps);
+
+/* One optimiser step on `stream`, asynchronous: theta (K doubles, device) is
+ * the point at which E (one double, device) and grad (K doubles, device)
+ * were evaluated; it is replaced by the next point, and E is appended to the
+ * history (the first max_steps steps).  One single-CTA kernel. */
+uccsd_status uccsd_opt_step(uccsd_ctx *ctx, double *theta, const double *E, const double *grad,
+                            void *stream);
+
+/* Energies recorded by uccsd_opt_step, in step order, to host E (min(steps,
+ * cap) doubles); *n_out = steps recorded.  Synchronises the last stream the
+ * optimiser ran on. */
+uccsd_status uccsd_opt_history(uccsd_ctx *ctx, double *E, int cap, int *n_out);
 
 /* ---- Trotter-schedule helpers (Section 2.3 ordering; Section 3.2 extrapolation) ---- */
 

@@ -35,7 +35,8 @@ EXPORTS = [
     "uccsd_pauli_terms", "uccsd_set_profiling", "uccsd_get_profile", "uccsd_expectation_noalloc",
     "uccsd_capture", "uccsd_replay", "uccsd_mp1_amplitudes", "uccsd_magnitude_order",
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
-    "uccsd_set_layout", "uccsd_pauli_terms_scbk",
+    "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
+    "uccsd_opt_history", "uccsd_set_setup_stream",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -89,6 +90,7 @@ def lib():
         L.uccsd_set_hamiltonian.argtypes = [vp, ip, f64p, f64p, ctypes.c_double]
         L.uccsd_set_reference.argtypes = [vp, ip, ip]
         L.uccsd_set_layout.argtypes = [vp, ip]
+        L.uccsd_set_setup_stream.argtypes = [vp, vp]
         L.uccsd_build_uccsd_list.argtypes = [ip, ip, ip, i32p, ip, ctypes.POINTER(ctypes.c_int)]
         L.uccsd_set_excitations.argtypes = [vp, ip, i32p, ip, ip]
         L.uccsd_set_batch.argtypes = [vp, ip]
@@ -108,6 +110,9 @@ def lib():
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
                                         ctypes.POINTER(ctypes.c_int)]
         L.uccsd_mp1_amplitudes.argtypes = [vp, f64p, vp]
+        L.uccsd_opt_init.argtypes = [vp, ip, ctypes.c_double, ctypes.c_double, ip]
+        L.uccsd_opt_step.argtypes = [vp, dp, dp, dp, vp]
+        L.uccsd_opt_history.argtypes = [vp, f64p, ip, ctypes.POINTER(ctypes.c_int)]
         L.uccsd_pauli_terms_scbk.argtypes = [ip, f64p, f64p, ctypes.c_double, ip, ip, u32p, u32p,
                                              f64p, ip, ctypes.POINTER(ctypes.c_int),
                                              ctypes.POINTER(ctypes.c_int)]
@@ -275,6 +280,13 @@ class Context:
         self.n_qubits = 2 * n_orb
         return self
 
+    def set_setup_stream(self, stream=None):
+        """Enqueue later set-up transfers on `stream` without host waits
+        (None: the context's own stream, waited on by each call)."""
+        ptr = ctypes.c_void_p(None) if stream is None else _stream_ptr(stream)
+        self._check(self._L.uccsd_set_setup_stream(self._c, ptr), "set_setup_stream")
+        return self
+
     def set_layout(self, layout):
         self._check(self._L.uccsd_set_layout(self._c, layout), "set_layout")
         return self
@@ -380,6 +392,23 @@ class Context:
                                                            _stream_ptr(stream)),
                     "energy_grad_trotter_free")
         return float(E[0]), g[:self.K].copy()
+
+    def opt_init(self, memory=10, max_step=0.2, first_scale=0.1, max_steps=40):
+        """Device fixed-step L-BFGS state (see uccsd_opt_init)."""
+        self._check(self._L.uccsd_opt_init(self._c, memory, max_step, first_scale, max_steps),
+                    "opt_init")
+
+    def opt_step(self, theta_ptr, E_ptr, grad_ptr, stream=None):
+        """One asynchronous optimiser step on device buffers (raw pointers)."""
+        self._check(self._L.uccsd_opt_step(self._c, theta_ptr, E_ptr, grad_ptr,
+                                           _stream_ptr(stream)), "opt_step")
+
+    def opt_history(self, cap=4096):
+        E = np.zeros(max(cap, 1))
+        n = ctypes.c_int(0)
+        self._check(self._L.uccsd_opt_history(self._c, _f64p(E), cap, ctypes.byref(n)),
+                    "opt_history")
+        return E[:min(n.value, cap)].copy()
 
     def mp1_amplitudes(self, stream=None):
         """First-order amplitudes of the context's list (one device

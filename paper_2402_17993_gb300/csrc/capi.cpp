@@ -162,17 +162,22 @@ void release(uccsd_ctx *c, const std::string &name) {
     c->mem.erase(it);
 }
 
-// (Re)allocate a named device buffer; contents are undefined.
+// A named device buffer of at least `bytes`; contents are undefined.  A
+// buffer only grows (cudaFree waits for the whole device, so a context that
+// is refilled with a problem of the same shape class frees nothing); on
+// growth it takes 1/8 headroom when the budget allows.
 uccsd_status dalloc(uccsd_ctx *c, const std::string &name, size_t bytes, void **out) {
     auto it = c->mem.find(name);
-    if (it != c->mem.end() && it->second.second == bytes) {
+    if (it != c->mem.end() && it->second.second >= bytes) {
         *out = it->second.first;
         return UCCSD_OK;
     }
+    const bool grow = it != c->mem.end();
     release(c, name);
     bytes = std::max<size_t>(bytes, 16);
     if (c->budget && c->bytes + bytes > c->budget)
         return fail(c, UCCSD_ERR_BUDGET, "device footprint of '" + name + "' exceeds the HBM budget");
+    if (grow && (!c->budget || c->bytes + bytes + bytes / 8 <= c->budget)) bytes += bytes / 8;
     void *p = nullptr;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
@@ -190,13 +195,59 @@ void *dptr(uccsd_ctx *c, const std::string &name) {
     return it == c->mem.end() ? nullptr : it->second.first;
 }
 
+// Host wait for the set-up transfers when they run on the context's own
+// stream; none when they are ordered on a caller stream.
+cudaError_t setup_sync(uccsd_ctx *c) {
+    return c->setup_async ? cudaSuccess : cudaStreamSynchronize(c->setup);
+}
+
+// Copy `nb` host bytes into the pinned staging area; *out is the staged copy.
+// The area is reused from its start once the copies staged earlier (all on
+// the current set-up stream, before the last recorded stage_ev) are done.
+uccsd_status stage_bytes(uccsd_ctx *c, const void *src, size_t nb, const void **out) {
+    const size_t need = (nb + 255) & ~size_t(255);
+    cudaError_t e = cudaSuccess;
+    if (c->stage_off + need > c->stage_cap) {
+        if (c->stage_off > 0 && (e = cudaEventSynchronize(c->stage_ev)) != cudaSuccess)
+            return cuda_fail(c, e, "staging wait");
+        c->stage_off = 0;
+        if (need > c->stage_cap) {
+            if (c->stage) cudaFreeHost(c->stage);
+            c->stage = nullptr;
+            c->stage_cap = 0;
+            const size_t cap = std::max(need, size_t(1) << 20);
+            if ((e = cudaHostAlloc(reinterpret_cast<void **>(&c->stage), cap, cudaHostAllocDefault)) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                c->stage = nullptr;
+                return fail(c, UCCSD_ERR_OOM, "pinned staging allocation failed");
+            }
+            c->stage_cap = cap;
+        }
+    }
+    std::memcpy(c->stage + c->stage_off, src, nb);
+    *out = c->stage + c->stage_off;
+    c->stage_off += need;
+    return UCCSD_OK;
+}
+
 template <typename T>
 uccsd_status upload(uccsd_ctx *c, const std::string &name, const std::vector<T> &v, T **out) {
     void *p = nullptr;
     uccsd_status st = dalloc(c, name, sizeof(T) * std::max<size_t>(v.size(), 1), &p);
     if (st) return st;
     if (!v.empty()) {
-        cudaError_t e = cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+        const size_t nb = sizeof(T) * v.size();
+        cudaError_t e;
+        if (c->setup_async) {
+            const void *src = nullptr;
+            if ((st = stage_bytes(c, v.data(), nb, &src))) return st;
+            e = cudaMemcpyAsync(p, src, nb, cudaMemcpyHostToDevice, c->setup);
+            if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev, c->setup);
+        } else {
+            e = cudaMemcpyAsync(p, v.data(), nb, cudaMemcpyHostToDevice, c->setup);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
+        }
         if (e != cudaSuccess) return cuda_fail(c, e, "upload");
     }
     *out = static_cast<T *>(p);
@@ -275,9 +326,11 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
 // string -> global bit deposits of the H-apply's row/column layout (alpha
 // string bit t = qubit 2t, beta string bit t = qubit 2t + 1).
 uccsd_status upload_tile_tables(uccsd_ctx *c) {
-    std::vector<uint16_t> combos, ranks;
-    std::vector<int32_t> coffs;
-    build_comb_tables(&combos, &ranks, &coffs);
+    // the tables do not depend on the problem: built once per process
+    static std::once_flag once;
+    static std::vector<uint16_t> combos, ranks;
+    static std::vector<int32_t> coffs;
+    std::call_once(once, [] { build_comb_tables(&combos, &ranks, &coffs); });
     uint16_t *p5;
     int32_t *p2;
     uint32_t *p4;
@@ -369,11 +422,12 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     const size_t n_ops = std::max<size_t>(c->op_k.size(), 1);
     if ((st = dalloc(c, "psi", B * state_elems(c) * amp_bytes(c), &p))) return st;
     // the sweeps touch only electron-sector amplitudes; the rest stays zero
-    cudaError_t e0 = cudaMemset(p, 0, B * state_elems(c) * amp_bytes(c));
+    cudaError_t e0 = cudaMemsetAsync(p, 0, B * state_elems(c) * amp_bytes(c), c->setup);
     if (e0 != cudaSuccess) return cuda_fail(c, e0, "memset");
     if ((st = dalloc(c, "sig", B * state_elems(c) * amp_bytes(c), &p))) return st;
     // sigma is written only inside the electron sector; the rest stays zero
-    cudaError_t e = cudaMemset(p, 0, B * state_elems(c) * amp_bytes(c));
+    cudaError_t e = cudaMemsetAsync(p, 0, B * state_elems(c) * amp_bytes(c), c->setup);
+    if (e == cudaSuccess) e = setup_sync(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
     if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
@@ -576,7 +630,7 @@ struct CachedLists {
 };
 
 std::mutex g_list_mu;
-std::vector<std::pair<uint64_t, CachedLists>> g_list_cache;  // most recent last, at most 8
+std::vector<std::pair<uint64_t, CachedLists>> g_list_cache;  // most recent last, at most 32
 
 CachedLists cached_lists(const uccsd_ctx *c, SweepPlan *pl, uint64_t key) {
     {
@@ -592,7 +646,7 @@ CachedLists cached_lists(const uccsd_ctx *c, SweepPlan *pl, uint64_t key) {
     for (const CRunDev &r : pl->runs) cl.pl_base.push_back(r.pl_base);
     std::lock_guard<std::mutex> lk(g_list_mu);
     g_list_cache.emplace_back(key, cl);
-    if (g_list_cache.size() > 8) g_list_cache.erase(g_list_cache.begin());
+    if (g_list_cache.size() > 32) g_list_cache.erase(g_list_cache.begin());
     return cl;
 }
 
@@ -661,7 +715,8 @@ uccsd_status prepare_trotter_free(uccsd_ctx *c) {
     for (const char *name : {"tf_u", "tf_w"}) {
         if ((st = dalloc(c, name, state_elems(c) * amp_bytes(c), &p))) return st;
         // only electron-sector entries are ever written; the rest stays zero
-        cudaError_t e = cudaMemset(p, 0, state_elems(c) * amp_bytes(c));
+        cudaError_t e = cudaMemsetAsync(p, 0, state_elems(c) * amp_bytes(c), c->setup);
+        if (e == cudaSuccess) e = setup_sync(c);
         if (e != cudaSuccess) return cuda_fail(c, e, "memset");
     }
     if ((st = dalloc(c, "tf_grad", sizeof(double) * std::max(c->K, 1), &p))) return st;
@@ -926,12 +981,33 @@ uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec, size_t h
         return UCCSD_ERR_ARG;
     }
     if (cudaSetDevice(device) != cudaSuccess) return UCCSD_ERR_CUDA;
-    if (configure_kernels() != cudaSuccess) return UCCSD_ERR_CUDA;
-    if (configure_sweep_kernels(kSweepBudget) != cudaSuccess) return UCCSD_ERR_CUDA;
+    {
+        // kernel attributes are per device and set once, never while another
+        // host thread may be launching the same kernels
+        static std::mutex mu;
+        static std::vector<char> done;
+        std::lock_guard<std::mutex> lk(mu);
+        if (done.size() < size_t(nd)) done.resize(nd, 0);
+        if (!done[device]) {
+            if (configure_kernels() != cudaSuccess) return UCCSD_ERR_CUDA;
+            if (configure_sweep_kernels(kSweepBudget) != cudaSuccess) return UCCSD_ERR_CUDA;
+            done[device] = 1;
+        }
+    }
     uccsd_ctx *c = new uccsd_ctx();
     c->device = device;
     c->prec = int(prec);
     c->budget = hbm_budget_bytes;
+    if (cudaStreamCreateWithFlags(&c->own_setup, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return UCCSD_ERR_CUDA;
+    }
+    if (cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(c->own_setup);
+        delete c;
+        return UCCSD_ERR_CUDA;
+    }
+    c->setup = c->own_setup;
     *out = c;
     return UCCSD_OK;
 }
@@ -942,8 +1018,26 @@ void uccsd_destroy(uccsd_ctx *c) {
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->graph) cudaGraphDestroy(c->graph);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->stage_off > 0) cudaEventSynchronize(c->stage_ev);
     for (auto &kv : c->mem) cudaFree(kv.second.first);
+    if (c->stage) cudaFreeHost(c->stage);
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->own_setup) cudaStreamDestroy(c->own_setup);
     delete c;
+}
+
+uccsd_status uccsd_set_setup_stream(uccsd_ctx *c, void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    cudaError_t e = cudaSetDevice(c->device);
+    // staged copies still queued on the previous set-up stream finish first
+    if (e == cudaSuccess && c->stage_off > 0) e = cudaEventSynchronize(c->stage_ev);
+    if (e == cudaSuccess && !c->setup_async) e = cudaStreamSynchronize(c->setup);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set-up stream switch");
+    c->stage_off = 0;
+    c->setup_async = stream != nullptr;
+    c->setup = stream ? static_cast<cudaStream_t>(stream) : c->own_setup;
+    return UCCSD_OK;
 }
 
 const char *uccsd_last_error(const uccsd_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -981,8 +1075,12 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, con
     c->shift = 0.0;
     make_fixed_point(c);
     if ((st = upload_tile_tables(c))) return st;
-    if ((st = upload_ham<float>(c, &c->hf32, "h32_"))) return st;
-    if ((st = upload_ham<double>(c, &c->hf64, "h64_"))) return st;
+    // only the context's precision is ever used by its kernels
+    if (c->prec) {
+        if ((st = upload_ham<float>(c, &c->hf32, "h32_"))) return st;
+    } else {
+        if ((st = upload_ham<double>(c, &c->hf64, "h64_"))) return st;
+    }
     c->have_h = true;
     return UCCSD_OK;
 }
@@ -1071,6 +1169,7 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->ijab.assign(ijab, ijab + 4 * size_t(K));
     c->exc = exc;
     c->tf_ready = false;
+    c->opt_m = 0;
     build_schedule(K, trotter_order, n_slices, &c->op_k, &c->op_scale);
     const size_t A = c->prec ? 8 : 16;
     c->fwd = plan_sweep(n, c->n_alpha, c->n_beta, A, 1, kSweepBudget, exc, c->op_k);
@@ -1232,10 +1331,12 @@ uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {
     double *dst = c->layout ? dense.data() : out;
     if (c->prec) {
         std::vector<float> tmp(2 * N);
-        e = cudaMemcpy(tmp.data(), src, N * 8, cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(tmp.data(), src, N * 8, cudaMemcpyDeviceToHost, c->setup);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
         for (size_t i = 0; i < 2 * N; ++i) dst[i] = tmp[i];
     } else {
-        e = cudaMemcpy(dst, src, N * 16, cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(dst, src, N * 16, cudaMemcpyDeviceToHost, c->setup);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "state download");
     if (c->layout) {
@@ -1347,6 +1448,69 @@ uccsd_status uccsd_energy_grad_trotter_free(uccsd_ctx *c, const double *theta, i
                                             double *grad, void *stream) {
     if (c && c->K > 0 && !grad) return fail(c, UCCSD_ERR_ARG, "null grad");
     return trotter_free(c, theta, on_dev, E, grad, stream);
+}
+
+uccsd_status uccsd_opt_init(uccsd_ctx *c, int memory, double max_step, double first_scale,
+                            int max_steps) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
+    if (memory < 1 || memory > 32 || !(max_step > 0.0) || !(first_scale > 0.0) || max_steps < 1)
+        return fail(c, UCCSD_ERR_ARG, "optimiser parameters out of range");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const size_t K = size_t(std::max(c->K, 1));
+    void *p;
+    uccsd_status st;
+    if ((st = dalloc(c, "opt_state", sizeof(double) * (2 * size_t(memory) * K + memory + 3 * K), &p)))
+        return st;
+    if ((st = dalloc(c, "opt_meta", 4 * sizeof(int), &p))) return st;
+    if ((e = cudaMemsetAsync(p, 0, 4 * sizeof(int), c->setup)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    if ((st = dalloc(c, "opt_hist", sizeof(double) * max_steps, &p))) return st;
+    if ((e = cudaMemsetAsync(p, 0, sizeof(double) * max_steps, c->setup)) != cudaSuccess)
+        return cuda_fail(c, e, "memset");
+    if ((e = setup_sync(c)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    c->opt_m = memory;
+    c->opt_steps = max_steps;
+    c->opt_max_step = max_step;
+    c->opt_first = first_scale;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_opt_step(uccsd_ctx *c, double *theta, const double *E, const double *grad,
+                            void *stream) {
+    if (!c) return UCCSD_ERR_ARG;
+    if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+    if (c->opt_m == 0) return fail(c, UCCSD_ERR_STATE, "uccsd_opt_init must come first");
+    if (c->K > 0 && (!theta || !grad)) return fail(c, UCCSD_ERR_ARG, "null theta or grad");
+    if (!E) return fail(c, UCCSD_ERR_ARG, "null E");
+    cudaError_t e = launch_lbfgs(static_cast<cudaStream_t>(stream), c->K, c->opt_m, c->opt_max_step,
+                                 c->opt_first, theta, E, grad, static_cast<double *>(dptr(c, "opt_state")),
+                                 static_cast<int *>(dptr(c, "opt_meta")),
+                                 static_cast<double *>(dptr(c, "opt_hist")), c->opt_steps);
+    if (e != cudaSuccess) return cuda_fail(c, e, "optimiser kernel");
+    ++c->launches;
+    c->last_stream = static_cast<cudaStream_t>(stream);
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_opt_history(uccsd_ctx *c, double *E, int cap, int *n_out) {
+    if (!c || !n_out || cap < 0 || (cap > 0 && !E)) return UCCSD_ERR_ARG;
+    if (c->opt_m == 0) return fail(c, UCCSD_ERR_STATE, "uccsd_opt_init must come first");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+    int meta[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(meta, dptr(c, "opt_meta"), sizeof(meta), cudaMemcpyDeviceToHost, c->setup);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
+    const int n = std::min(meta[3], c->opt_steps);
+    if (e == cudaSuccess && cap > 0 && n > 0)
+        e = cudaMemcpyAsync(E, dptr(c, "opt_hist"), sizeof(double) * std::min(n, cap),
+                            cudaMemcpyDeviceToHost, c->setup);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
+    if (e != cudaSuccess) return cuda_fail(c, e, "optimiser history download");
+    *n_out = n;
+    return UCCSD_OK;
 }
 
 uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *eri, double e_core,

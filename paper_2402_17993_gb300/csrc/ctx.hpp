@@ -29,6 +29,17 @@ struct uccsd_ctx {
     bool failed = false;
     uint64_t launches = 0;
     cudaStream_t last_stream = nullptr;
+    // Stream of the set-up transfers (uploads, clears, downloads).  By default
+    // the context's own non-blocking stream, waited on by the host after each
+    // transfer.  After uccsd_set_setup_stream with a caller stream the
+    // transfers are enqueued there from pinned staging and nothing waits: the
+    // caller orders later work after that stream.
+    cudaStream_t setup = nullptr;
+    cudaStream_t own_setup = nullptr;
+    bool setup_async = false;
+    char *stage = nullptr;  // pinned staging of asynchronous uploads
+    size_t stage_cap = 0, stage_off = 0;
+    cudaEvent_t stage_ev = nullptr;  // recorded on `setup` after the last staged copy
 
     // problem
     int n_orb = 0, n = 0;
@@ -71,6 +82,10 @@ struct uccsd_ctx {
     std::vector<long long> diag_qa, diag_qb;
     double diag_unit = 0.0;
     double shift = 0.0;
+
+    // device optimiser (fixed-step L-BFGS)
+    int opt_m = 0, opt_steps = 0;
+    double opt_max_step = 0.0, opt_first = 0.0;
 
     // captured evaluation graph
     cudaGraph_t graph = nullptr;

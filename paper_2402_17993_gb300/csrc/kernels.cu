@@ -436,6 +436,122 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
 // ---------------------------------------------------------------------------
 // Launch wrappers
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Fixed-step L-BFGS update on the device (two-loop recursion, Nocedal and
+// Wright Algorithm 7.4), one CTA: the serving loop's optimiser step without
+// a host round trip.  State (all device): S, Y [m][K] ring of (s, y) pairs,
+// rho [m], prev_theta, prev_g, work [K], meta = {count, head, has_prev,
+// step}.  Pairs with s.y <= 1e-16 max(1, y.y) are not stored; the step is
+// -first_scale g while no pair is stored; the step is capped at max_step in
+// the max-norm.  All dot products are FP64 in a fixed order.
+// ---------------------------------------------------------------------------
+constexpr int kOptThreads = 256;
+
+__device__ double opt_dot(const double *a, const double *b, int K, double *red) {
+    double v = 0.0;
+    for (int i = threadIdx.x; i < K; i += kOptThreads) v += a[i] * b[i];
+    v = block_sum(v, red);
+    __shared__ double bc;
+    if (threadIdx.x == 0) bc = v;
+    __syncthreads();
+    v = bc;
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(kOptThreads) lbfgs_kernel(
+    int K, int m, double max_step, double first_scale, double *__restrict__ theta,
+    const double *__restrict__ E, const double *__restrict__ g, double *__restrict__ S,
+    double *__restrict__ Y, double *__restrict__ rho, double *__restrict__ prev_t,
+    double *__restrict__ prev_g, double *__restrict__ work, int *__restrict__ meta,
+    double *__restrict__ E_hist, int max_steps) {
+    __shared__ double red[32];
+    __shared__ double alpha[64];
+    const int count0 = meta[0], head0 = meta[1], has_prev = meta[2], step = meta[3];
+    if (threadIdx.x == 0 && step < max_steps) E_hist[step] = E[0];
+    int count = count0, head = head0;
+    if (has_prev) {
+        const int nxt = (head0 + 1) % m;
+        double *sn = S + (size_t)nxt * K, *yn = Y + (size_t)nxt * K;
+        for (int i = threadIdx.x; i < K; i += kOptThreads) {
+            sn[i] = theta[i] - prev_t[i];
+            yn[i] = g[i] - prev_g[i];
+        }
+        __syncthreads();
+        const double sy = opt_dot(sn, yn, K, red);
+        const double yy = opt_dot(yn, yn, K, red);
+        if (sy > 1e-16 * fmax(1.0, yy)) {
+            if (threadIdx.x == 0) rho[nxt] = 1.0 / sy;
+            head = nxt;
+            count = min(count0 + 1, m);
+        }
+        __syncthreads();
+    }
+    // direction d in work
+    if (count == 0) {
+        for (int i = threadIdx.x; i < K; i += kOptThreads) work[i] = -first_scale * g[i];
+        __syncthreads();
+    } else {
+        for (int i = threadIdx.x; i < K; i += kOptThreads) work[i] = g[i];
+        __syncthreads();
+        for (int k = 0; k < count; ++k) {  // newest first
+            const int idx = (head - k + m) % m;
+            const double a = rho[idx] * opt_dot(S + (size_t)idx * K, work, K, red);
+            if (threadIdx.x == 0) alpha[k] = a;
+            for (int i = threadIdx.x; i < K; i += kOptThreads) work[i] -= a * Y[(size_t)idx * K + i];
+            __syncthreads();
+        }
+        const double *yh = Y + (size_t)head * K, *sh = S + (size_t)head * K;
+        const double gamma = opt_dot(sh, yh, K, red) / opt_dot(yh, yh, K, red);
+        for (int i = threadIdx.x; i < K; i += kOptThreads) work[i] *= gamma;
+        __syncthreads();
+        for (int k = count - 1; k >= 0; --k) {  // oldest first
+            const int idx = (head - k + m) % m;
+            const double b = rho[idx] * opt_dot(Y + (size_t)idx * K, work, K, red);
+            const double c = alpha[k] - b;
+            for (int i = threadIdx.x; i < K; i += kOptThreads) work[i] += c * S[(size_t)idx * K + i];
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < K; i += kOptThreads) work[i] = -work[i];
+        __syncthreads();
+    }
+    // cap in the max-norm
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < K; i += kOptThreads) mx = fmax(mx, fabs(work[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < kOptThreads / 32 ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) alpha[63] = v;
+    }
+    __syncthreads();
+    mx = alpha[63];
+    const double scale = mx > max_step ? max_step / mx : 1.0;
+    for (int i = threadIdx.x; i < K; i += kOptThreads) {
+        prev_t[i] = theta[i];
+        prev_g[i] = g[i];
+        theta[i] += work[i] * scale;
+    }
+    if (threadIdx.x == 0) {
+        meta[0] = count;
+        meta[1] = head;
+        meta[2] = 1;
+        meta[3] = step + 1;
+    }
+}
+
+cudaError_t launch_lbfgs(cudaStream_t stream, int K, int m, double max_step, double first_scale,
+                         double *theta, const double *E, const double *g, double *state,
+                         int *meta, double *E_hist, int max_steps) {
+    double *S = state, *Y = S + (size_t)m * K, *rho = Y + (size_t)m * K;
+    double *prev_t = rho + m, *prev_g = prev_t + K, *work = prev_g + K;
+    lbfgs_kernel<<<1, kOptThreads, 0, stream>>>(K, m, max_step, first_scale, theta, E, g, S, Y, rho,
+                                                prev_t, prev_g, work, meta, E_hist, max_steps);
+    return cudaGetLastError();
+}
+
 template <typename R>
 size_t happly_smem(const HSector &hs, int n_orb) {
     return happly_aspec_offset<R>(hs.Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1);

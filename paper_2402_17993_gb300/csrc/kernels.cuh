@@ -156,6 +156,13 @@ cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles
 template <typename R>
 size_t happly_smem(const HSector &hs, int n_orb);
 
+// Fixed-step L-BFGS update of theta (K doubles, device) from the gradient g
+// and energy E of the evaluation at theta; state holds 2 m K + m + 3 K
+// doubles, meta 4 ints (zeroed to start); E is recorded in E_hist[step].
+cudaError_t launch_lbfgs(cudaStream_t stream, int K, int m, double max_step, double first_scale,
+                         double *theta, const double *E, const double *g, double *state,
+                         int *meta, double *E_hist, int max_steps);
+
 // One-time kernel attribute set-up (dynamic shared memory opt-in).
 cudaError_t configure_kernels();
 

@@ -10,13 +10,17 @@ qubits, each with its own integrals) and share one GPU:
   remaining HBM budget; the library enforces the same budget per context;
 * residency: every admitted fragment keeps its context, state vectors and
   amplitudes on the device until its solve finishes;
-* continuous batching: each tick launches one energy + gradient evaluation
-  for every active fragment, each as a captured CUDA graph on one of several
-  streams so that the evaluations of different fragments overlap on the
-  device; the host then applies one fixed-step L-BFGS update per fragment
-  and admits newly arrived requests into freed slots;
+* continuous batching: at admission a fragment's whole solve is enqueued on
+  its own stream: a fixed number of steps, each one replay of its captured
+  evaluation graph and one fixed-step L-BFGS update on the device
+  (uccsd_opt_step), so no step waits for the host; solves of different
+  fragments overlap on the device, and the host only admits arrivals into
+  freed slots and collects finished solves;
 * each solve runs a fixed number of optimiser steps (one evaluation each);
   its latency is arrival -> last step done.
+
+The plain form (max_active = 1, use_graphs = False) steps one request at a
+time from the host: evaluation, download, host L-BFGS update.
 
 Fragments never share device buffers or reductions, so a fragment's result
 does not depend on what else is in flight (checked by the GPU tests).
@@ -136,6 +140,40 @@ class _Slot:
         return E
 
 
+class _DevSlot:
+    """A fragment whose whole solve is enqueued on its stream at admission:
+    `steps` x (graph replay of the evaluation + device L-BFGS step)."""
+
+    def __init__(self, req, ctx, stream, t_admit, steps):
+        import torch
+        self.req = req
+        self.ctx = ctx
+        self.stream = stream
+        self.K = ctx.K
+        self.t_admit = t_admit
+        self.steps = steps
+        dev = torch.device("cuda", ctx.device)
+        k = max(self.K, 1)
+        ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=steps)
+        # everything of this fragment is ordered on its own stream
+        with torch.cuda.stream(stream):
+            self.th_dev = torch.zeros(k, dtype=torch.float64, device=dev)
+            self.E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+            self.g_dev = torch.zeros(k, dtype=torch.float64, device=dev)
+            ctx.capture(self.th_dev[: k].view(1, -1), self.E_dev, self.g_dev[: k].view(1, -1), stream)
+            for _ in range(steps):
+                ctx.replay(stream)
+                ctx.opt_step(self.th_dev.data_ptr(), self.E_dev.data_ptr(), self.g_dev.data_ptr(),
+                             stream)
+            self.done = torch.cuda.Event()
+            self.done.record(stream)
+
+    def result(self, keep_theta):
+        energies = [float(e) for e in self.ctx.opt_history(self.steps)]
+        theta = self.th_dev[: self.K].cpu().numpy().copy() if keep_theta else None
+        return energies, theta
+
+
 class FragmentServer:
     """Serve fragment VQE solves with continuous batching on one GPU.
 
@@ -143,7 +181,7 @@ class FragmentServer:
     use_graphs = False gives the plain one-request-at-a-time form."""
 
     def __init__(self, precision=FP32_STATE, device=0, hbm_budget=8 << 30, max_active=48,
-                 n_streams=16, steps=40, use_graphs=True):
+                 n_streams=None, steps=40, use_graphs=True):
         import torch
         self.precision = precision
         self.device = device
@@ -151,17 +189,22 @@ class FragmentServer:
         self.max_active = max_active
         self.steps = steps
         self.use_graphs = use_graphs
+        n_streams = max_active if n_streams is None else n_streams
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
         self.pool = {}
 
-    def _context(self, req, used):
+    def _context(self, req, used, stream=None):
         """A context for the request: a recycled one of the same shape class
         (its device buffers are reused, nothing is allocated) or a new one
-        whose HBM budget is what the server has left."""
+        whose HBM budget is what the server has left.  With `stream` the
+        set-up transfers are enqueued on it and nothing waits for them, so
+        the host never stalls behind another fragment's solve."""
         key = (req.n_orb, req.n_alpha, req.n_beta)
         pool = self.pool.get(key)
-        ctx = pool.pop() if pool else Context(self.device, self.precision,
-                                              max(1, self.hbm_budget - used))
+        ctx = pool.pop() if pool else None
+        if ctx is None:
+            ctx = Context(self.device, self.precision, max(1, self.hbm_budget - used))
+        ctx.set_setup_stream(stream)
         ctx.set_hamiltonian(req.n_orb, req.h, req.eri, req.e_core)
         ctx.set_reference(req.n_alpha, req.n_beta)
         ctx.set_excitations(build_uccsd_list(req.n_orb, req.n_alpha, req.n_beta))
@@ -179,6 +222,89 @@ class FragmentServer:
     def run(self, requests, rate=None, keep_theta=False):
         """Serve `requests` (arrivals at t_unit / rate seconds; rate None =
         all at once).  Returns (results, stats)."""
+        if self.use_graphs:
+            return self._run_device(requests, rate, keep_theta)
+        return self._run_host(requests, rate, keep_theta)
+
+    def _stats(self, results, n_evals, makespan, active_hist, peak_used, peak_dev):
+        lat = np.array([r.latency for r in results])
+        return {
+            "requests": len(results), "steps_per_solve": self.steps, "evals": n_evals,
+            "makespan_s": makespan, "evals_per_s": n_evals / makespan,
+            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+            "mean_active": float(np.mean(active_hist)) if active_hist else 0.0,
+            "peak_hbm_reserved_bytes": int(peak_used),
+            "peak_hbm_device_bytes": int(peak_dev),
+            "precision": "fp32" if self.precision == FP32_STATE else "fp64",
+            "max_active": self.max_active, "graphs": self.use_graphs,
+        }
+
+    def _run_device(self, requests, rate, keep_theta):
+        """Arrived requests are admitted in arrival order while slots and the
+        HBM budget allow, one per pass of the loop between completion checks:
+        the context is prepared with its set-up transfers enqueued on a free
+        stream (host work, no host waits), then the evaluation graph is
+        captured and the whole solve enqueued behind them on that stream."""
+        reqs = sorted(requests, key=lambda q: q.t_unit)
+        arrive = [0.0 if rate is None else q.t_unit / rate for q in reqs]
+        t0 = time.perf_counter()
+        pending = 0
+        active: list[_DevSlot] = []
+        free_streams = list(self.streams)
+        results: list[Result] = []
+        used = peak_used = dev_used = peak_dev = 0
+        n_evals = 0
+        while pending < len(reqs) or active:
+            now = time.perf_counter() - t0
+            progressed = False
+            if (pending < len(reqs) and arrive[pending] <= now
+                    and len(active) < self.max_active and free_streams):
+                q = reqs[pending]
+                need = footprint_bytes(q.n_orb, q.n_alpha, q.n_beta, self.precision)
+                if used + need <= self.hbm_budget or not active:
+                    st = free_streams.pop()
+                    ctx = self._context(q, used, st)
+                    slot = _DevSlot(q, ctx, st, time.perf_counter() - t0, self.steps)
+                    slot.reserved = need
+                    slot.dev_bytes = ctx.info()["device_bytes"]
+                    slot.t_arrive = arrive[pending]
+                    used += need
+                    dev_used += slot.dev_bytes
+                    peak_used = max(peak_used, used)
+                    peak_dev = max(peak_dev, dev_used)
+                    active.append(slot)
+                    pending += 1
+                    progressed = True
+            still = []
+            for s in active:
+                if s.done.query():
+                    t_done = time.perf_counter() - t0
+                    energies, theta = s.result(keep_theta)
+                    results.append(Result(s.req.r, 2 * s.req.n_orb, s.t_arrive, s.t_admit,
+                                          t_done, energies[-1], energies, theta))
+                    n_evals += s.steps
+                    used -= s.reserved
+                    dev_used -= s.dev_bytes
+                    free_streams.append(s.stream)
+                    self._release(s.req, s.ctx)
+                    progressed = True
+                else:
+                    still.append(s)
+            active = still
+            if not progressed:
+                wait = 50e-6
+                if pending < len(reqs) and not active:
+                    wait = max(0.0, min(arrive[pending] - (time.perf_counter() - t0), 0.01))
+                time.sleep(wait)
+        makespan = time.perf_counter() - t0
+        stats = self._stats(results, n_evals, makespan, [], peak_used, peak_dev)
+        # time average of the number of admitted, unfinished fragments
+        stats["mean_active"] = (sum(r.t_done - r.t_admit for r in results) / makespan
+                                if makespan > 0 else 0.0)
+        return sorted(results, key=lambda r: r.r), stats
+
+    def _run_host(self, requests, rate, keep_theta):
         reqs = sorted(requests, key=lambda q: q.t_unit)
         arrive = [0.0 if rate is None else q.t_unit / rate for q in reqs]
         t0 = time.perf_counter()
@@ -236,19 +362,8 @@ class FragmentServer:
                     still.append(s)
             active = still
         makespan = time.perf_counter() - t0
-        lat = np.array([r.latency for r in results])
-        stats = {
-            "requests": len(results), "steps_per_solve": self.steps, "evals": n_evals,
-            "makespan_s": makespan, "evals_per_s": n_evals / makespan,
-            "p50_latency_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
-            "p99_latency_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
-            "mean_active": float(np.mean(active_hist)) if active_hist else 0.0,
-            "peak_hbm_reserved_bytes": int(peak_used),
-            "peak_hbm_device_bytes": int(peak_dev),
-            "precision": "fp32" if self.precision == FP32_STATE else "fp64",
-            "max_active": self.max_active, "graphs": self.use_graphs,
-        }
-        return sorted(results, key=lambda r: r.r), stats
+        return (sorted(results, key=lambda r: r.r),
+                self._stats(results, n_evals, makespan, active_hist, peak_used, peak_dev))
 
 
 def fmo2_sum(monomer_E, dimer_E, n_frag):

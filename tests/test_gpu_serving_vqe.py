@@ -49,9 +49,13 @@ def test_server_result_is_the_same_alone_and_in_the_mix(uc, prec):
     from paper_2402_17993_gb300.serving import FragmentServer
     reqs = _requests(12)
     srv = FragmentServer(precision=prec, steps=6, max_active=12)
+    cold, _ = srv.run(reqs, rate=None, keep_theta=True)
+    # warm: pooled contexts and cached pair lists, so the solves overlap
     mixed, stats = srv.run(reqs, rate=None, keep_theta=True)
     assert stats["requests"] == 12 and stats["evals"] == 72
     assert stats["mean_active"] > 1.5
+    for c, m in zip(cold, mixed):
+        assert c.energies == m.energies and np.array_equal(c.theta, m.theta)
     for q, m in zip(reqs, mixed):
         alone, _ = srv.run([q], rate=None, keep_theta=True)
         a = alone[0]
@@ -98,3 +102,58 @@ def test_server_open_loop_latencies(uc):
     assert 0 < stats["p50_latency_ms"] <= stats["p99_latency_ms"]
     assert all(r.t_done >= r.t_arrive for r in res)
     srv.close()
+
+
+def test_device_lbfgs_follows_the_host_lbfgs(uc):
+    # the device optimiser (uccsd_opt_step) and the host LBFGS class take the
+    # same steps from the same evaluations (FP64, 12 qubits, 8 steps)
+    import torch
+    from paper_2402_17993_gb300.vqe import LBFGS
+    w = synth.workload("12q")
+    ctx = uc.make_context(6, w["h"], w["eri"], 0.0, 3, 3)
+    K = ctx.K
+    ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=8)
+    th = torch.zeros(K, dtype=torch.float64, device="cuda")
+    E = torch.zeros(1, dtype=torch.float64, device="cuda")
+    G = torch.zeros(K, dtype=torch.float64, device="cuda")
+    opt = LBFGS(K)
+    theta = np.zeros(K)
+    s = torch.cuda.current_stream()
+    for _ in range(8):
+        ctx.energy_grad_device(th.view(1, -1), E, G.view(1, -1), s)
+        ctx.opt_step(th.data_ptr(), E.data_ptr(), G.data_ptr(), s)
+        Eh, gh = ctx.energy_grad(theta)
+        theta = opt.step(theta, gh)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(th.cpu().numpy() - theta)) < 1e-9
+    hist = ctx.opt_history()
+    assert len(hist) == 8 and hist[0] == ctx.energy(np.zeros(K))
+    assert hist[-1] < hist[0]
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_setup_on_a_caller_stream_is_the_synchronous_setup(uc, prec):
+    # One context refilled with fragments of different shapes and integrals,
+    # its set-up transfers enqueued on a caller stream without host waits
+    # (pinned staging, buffers that only grow), gives bitwise the energies and
+    # gradients of fresh contexts set up synchronously.
+    import torch
+    s = torch.cuda.Stream()
+    reuse = uc.Context(0, prec)
+    rng = np.random.default_rng(5)
+    frags = synth.stream_fragments(7, seed=11)
+    for i, d in enumerate(frags):
+        reuse.set_setup_stream(None if i == len(frags) - 1 else s)  # last one synchronous again
+        reuse.set_hamiltonian(d["n_orb"], d["h"], d["eri"], d["e_core"])
+        reuse.set_reference(d["n_alpha"], d["n_beta"])
+        reuse.set_excitations(uc.build_uccsd_list(d["n_orb"], d["n_alpha"], d["n_beta"]))
+        th = rng.uniform(-0.1, 0.1, reuse.K)
+        Ea, ga = reuse.energy_grad(th, stream=s)
+        fresh = uc.make_context(d["n_orb"], d["h"], d["eri"], d["e_core"], d["n_alpha"],
+                                d["n_beta"], precision=prec)
+        Eb, gb = fresh.energy_grad(th)
+        fresh.close()
+        assert Ea == Eb and np.array_equal(ga, gb), (i, d["n_orb"])
+    assert len({d["n_orb"] for d in frags}) > 1
+    reuse.close()
