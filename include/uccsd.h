@@ -330,6 +330,17 @@ uccsd_status uccsd_opt_init(uccsd_ctx *ctx, int memory, double max_step, double 
 uccsd_status uccsd_opt_step(uccsd_ctx *ctx, double *theta, const double *E, const double *grad,
                             void *stream);
 
+/* Capture one VQE iteration of a single-slot solve into the context's graph
+ * (replacing any earlier capture): the energy and adjoint gradient at
+ * theta_dev (K doubles on the device) into E_dev (1) and grad_dev (K),
+ * followed by one uccsd_opt_step that updates theta_dev in place.  Each
+ * uccsd_replay then runs one iteration of the Section 2.3 loop (ansatz
+ * state, energy, gradient, classical update) as one graph launch.  Needs
+ * uccsd_opt_init first; the optimiser history advances on every replay.
+ * Errors as uccsd_capture; UCCSD_ERR_STATE without uccsd_opt_init. */
+uccsd_status uccsd_capture_vqe_step(uccsd_ctx *ctx, double *theta_dev, double *E_dev,
+                                    double *grad_dev, void *stream);
+
 /* Energies recorded by uccsd_opt_step, in step order, to host E (min(steps,
  * cap) doubles); *n_out = steps recorded.  Synchronises the last stream the
  * optimiser ran on. */

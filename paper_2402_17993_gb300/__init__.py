@@ -36,7 +36,7 @@ EXPORTS = [
     "uccsd_capture", "uccsd_replay", "uccsd_mp1_amplitudes", "uccsd_magnitude_order",
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
     "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
-    "uccsd_opt_history", "uccsd_set_setup_stream",
+    "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -105,6 +105,7 @@ def lib():
         L.uccsd_expectation_noalloc.argtypes = [vp, vp, vp, vp]
         L.uccsd_capture.argtypes = [vp, ip, dp, dp, dp, vp]
         L.uccsd_replay.argtypes = [vp, vp]
+        L.uccsd_capture_vqe_step.argtypes = [vp, dp, dp, dp, vp]
         L.uccsd_set_profiling.argtypes = [vp, ip]
         L.uccsd_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
@@ -349,6 +350,13 @@ class Context:
         gp = None if grad is None else grad.data_ptr()
         self._check(self._L.uccsd_capture(self._c, B, theta.data_ptr(), E.data_ptr(), gp,
                                           _stream_ptr(stream)), "capture")
+
+    def capture_vqe_step(self, theta, E, grad, stream):
+        """Capture evaluation + device optimiser step on the CUDA tensors
+        theta (K,), E (1,), grad (K,); replay() then runs one VQE iteration."""
+        self._check(self._L.uccsd_capture_vqe_step(self._c, theta.data_ptr(), E.data_ptr(),
+                                                   grad.data_ptr(), _stream_ptr(stream)),
+                    "capture_vqe_step")
 
     def replay(self, stream):
         self._check(self._L.uccsd_replay(self._c, _stream_ptr(stream)), "replay")

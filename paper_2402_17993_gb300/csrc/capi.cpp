@@ -1143,6 +1143,27 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     if (trotter_order != 1 && trotter_order != 2) return fail(c, UCCSD_ERR_ARG, "trotter_order must be 1 or 2");
     if (n_slices < 1 || n_slices > 64) return fail(c, UCCSD_ERR_ARG, "n_slices must be in [1, 64]");
     const int n = c->n;
+    if (c->exc_valid && K == c->K && trotter_order == c->order && n_slices == c->M &&
+        c->exc_n == n && c->exc_na == c->n_alpha && c->exc_nb == c->n_beta &&
+        c->exc_layout == c->layout &&
+        (K == 0 || std::memcmp(ijab, c->ijab.data(), sizeof(int32_t) * 4 * size_t(K)) == 0)) {
+        // The same reference shape and list as the last call (a refilled
+        // context): the plans, schedule tables, pair lists and slots stand.
+        // Only the table pointers are refreshed and the state invalidated.
+        for (SweepArgs *a : {&c->fwd_args, &c->adj_args}) {
+            a->combos = c->comb_combos;
+            a->ranks = c->comb_ranks;
+            a->comb_offs = c->comb_offs;
+            a->aoff = c->hsec.aoff;
+            a->boff = c->hsec.boff;
+        }
+        c->tf_ready = false;
+        c->opt_m = 0;
+        c->have_exc = true;
+        c->state_valid = false;
+        return alloc_slots(c);
+    }
+    c->exc_valid = false;
     std::vector<CompiledExc> exc(K);
     for (int k = 0; k < K; ++k) {
         const int32_t *r = ijab + 4 * k;
@@ -1230,7 +1251,13 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     }
     c->have_exc = true;
     c->state_valid = false;
-    return alloc_slots(c);
+    if ((st = alloc_slots(c))) return st;
+    c->exc_valid = true;
+    c->exc_n = n;
+    c->exc_na = c->n_alpha;
+    c->exc_nb = c->n_beta;
+    c->exc_layout = c->layout;
+    return UCCSD_OK;
 }
 
 uccsd_status uccsd_set_batch(uccsd_ctx *c, int B) {
@@ -1266,14 +1293,21 @@ uccsd_status uccsd_energy_grad_batch(uccsd_ctx *c, int B, const double *theta, i
     return eval(c, B, theta, on_dev, E, grad, stream);
 }
 
-uccsd_status uccsd_capture(uccsd_ctx *c, int B, const double *theta, double *E, double *grad,
-                           void *stream) {
+}  // extern "C"
+
+namespace {
+// Capture one B-slot evaluation, followed by one optimiser step when
+// opt_step is set, into the context's graph.
+uccsd_status capture_graph(uccsd_ctx *c, int B, const double *theta, double *E, double *grad,
+                           void *stream, bool opt_step) {
     if (!c) return UCCSD_ERR_ARG;
     if (c->profiling) return fail(c, UCCSD_ERR_STATE, "capture needs profiling off");
     if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
     if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
     if (B < 1 || B > c->B || !E || (!theta && c->K > 0))
         return fail(c, UCCSD_ERR_ARG, "bad capture arguments");
+    if (opt_step && c->opt_m == 0) return fail(c, UCCSD_ERR_STATE, "uccsd_opt_init must come first");
+    if (opt_step && c->K > 0 && !grad) return fail(c, UCCSD_ERR_ARG, "null grad");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1291,6 +1325,15 @@ uccsd_status uccsd_capture(uccsd_ctx *c, int B, const double *theta, double *E, 
     const uint64_t l0 = c->launches;
     uccsd_status st = c->prec ? run_eval<float>(c, B, theta, 1, E, grad, s)
                               : run_eval<double>(c, B, theta, 1, E, grad, s);
+    if (st == UCCSD_OK && opt_step) {
+        cudaError_t eo = launch_lbfgs(s, c->K, c->opt_m, c->opt_max_step, c->opt_first,
+                                      const_cast<double *>(theta), E, grad,
+                                      static_cast<double *>(dptr(c, "opt_state")),
+                                      static_cast<int *>(dptr(c, "opt_meta")),
+                                      static_cast<double *>(dptr(c, "opt_hist")), c->opt_steps);
+        if (eo != cudaSuccess) st = fail(c, UCCSD_ERR_CUDA, "optimiser kernel in capture");
+        else ++c->launches;
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(s, &g);
     c->graph_kernels = c->launches - l0;  // kernels inside the graph
@@ -1304,6 +1347,19 @@ uccsd_status uccsd_capture(uccsd_ctx *c, int B, const double *theta, double *E, 
     e = cudaGraphInstantiate(&c->graph_exec, g, 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
     return UCCSD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+uccsd_status uccsd_capture(uccsd_ctx *c, int B, const double *theta, double *E, double *grad,
+                           void *stream) {
+    return capture_graph(c, B, theta, E, grad, stream, false);
+}
+
+uccsd_status uccsd_capture_vqe_step(uccsd_ctx *c, double *theta, double *E, double *grad,
+                                    void *stream) {
+    return capture_graph(c, 1, theta, E, grad, stream, true);
 }
 
 uccsd_status uccsd_replay(uccsd_ctx *c, void *stream) {

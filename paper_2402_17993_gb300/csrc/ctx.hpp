@@ -55,6 +55,10 @@ struct uccsd_ctx {
     uccsd::SweepPlan fwd, adj;
     uccsd::SweepArgs fwd_args, adj_args;
     uint64_t list_key[2] = {0, 0};  // plan hashes of the pair lists held (forward, adjoint)
+    // shape of the last complete set_excitations (plans, tables and slots
+    // depend on it and the list only, not on the integrals)
+    bool exc_valid = false;
+    int exc_n = 0, exc_na = 0, exc_nb = 0, exc_layout = -1;
     std::vector<uccsd::CompiledExc> exc;  // list order
     // Trotter-free ansatz: plan with every excitation once (built on first use)
     uccsd::SweepPlan tf;

@@ -134,40 +134,58 @@ std::vector<XZTerm> eq2_terms(int n_orb, const double *h, const double *eri, dou
     const int n = 2 * n_orb;
     // distinct keys: 16 Z-patterns per flip mask of 0, 2 or 4 bits
     const size_t n2 = size_t(n) * (n - 1) / 2, n4 = n2 * (n - 2) * (n - 3) / 12;
-    TermTable acc(16 * (1 + n2 + n4));
+    TermTable acc(2 * (1 + n2 + n4));  // grows if needed
     XZTerm buf[16];
     auto add = [&](int cnt) {
         for (int i = 0; i < cnt; ++i) acc.add(key(buf[i].x, buf[i].z), buf[i].c);
     };
-    // one-body: sum_PQ h_PQ a+_P a_Q  (same spin)
+    // A + A^dagger of an expanded A: (X^x Z^z)^dagger = (-1)^{popc(x & z)} X^x Z^z,
+    // so odd terms cancel and even terms double.
+    auto add_hermitian = [&](int cnt) {
+        for (int i = 0; i < cnt; ++i)
+            if (!(popc(buf[i].x & buf[i].z) & 1)) acc.add(key(buf[i].x, buf[i].z), 2.0 * buf[i].c);
+    };
+    // one-body: sum_PQ h_PQ a+_P a_Q (same spin); h is symmetric, so the
+    // pair P < Q is (a+_P a_Q) + its adjoint and P = Q stands alone
     for (int P = 0; P < n; ++P)
-        for (int Q = 0; Q < n; ++Q) {
+        for (int Q = P; Q < n; ++Q) {
             if ((P & 1) != (Q & 1)) continue;
             double c = h[(P >> 1) * n_orb + (Q >> 1)];
             if (c == 0.0) continue;
             int idx[2] = {qubit_of[P], qubit_of[Q]};
             bool dag[2] = {true, false};
-            add(expand(2, idx, dag, c, buf));
+            const int cnt = expand(2, idx, dag, c, buf);
+            if (P == Q) add(cnt);
+            else add_hermitian(cnt);
         }
-    // two-body: 1/2 sum_PQRS <PQ|RS> a+_P a+_Q a_S a_R, <PQ|RS> = (pr|qs).
-    // (P,Q,R,S) and (Q,P,S,R) give the same operator with the same
-    // coefficient (two anticommutations; <QP|SR> = <PQ|RS>), so the sum runs
-    // over P < Q with weight 1 instead of 1/2; P = Q vanishes.
+    // two-body: 1/2 sum_PQRS <PQ|RS> a+_P a+_Q a_S a_R with <PQ|RS> = (pr|qs)
+    // for spin(P) = spin(R), spin(Q) = spin(S), else 0.
+    //  - (P,Q,R,S) and (Q,P,S,R) give the same operator and coefficient, so
+    //    the sum runs over P < Q with weight 1 (P = Q vanishes);
+    //  - a_R a_S = -a_S a_R, so (R,S) and (S,R) combine into R < S with
+    //    coefficient c = <PQ|RS> - <PQ|SR>;
+    //  - with real integrals the pair (R<S, P<Q) has the same c and the
+    //    adjoint operator, so (P,Q) < (R,S) is expanded once as A + A^dagger
+    //    and (P,Q) = (R,S) stands alone.
+    auto g_of = [&](int P, int Q, int R, int S) {
+        if ((P & 1) != (R & 1) || (Q & 1) != (S & 1)) return 0.0;
+        const size_t p = P >> 1, q = Q >> 1, r = R >> 1, s = S >> 1;
+        return eri[((p * n_orb + r) * n_orb + q) * n_orb + s];
+    };
     for (int P = 0; P < n; ++P)
-        for (int Q = P + 1; Q < n; ++Q) {
-            for (int R = 0; R < n; ++R) {
-                if ((P & 1) != (R & 1)) continue;
-                for (int S = 0; S < n; ++S) {
-                    if (R == S || (Q & 1) != (S & 1)) continue;
-                    size_t p = P >> 1, q = Q >> 1, r = R >> 1, s = S >> 1;
-                    double g = eri[((p * n_orb + r) * n_orb + q) * n_orb + s];
-                    if (g == 0.0) continue;
+        for (int Q = P + 1; Q < n; ++Q)
+            for (int R = P; R < n; ++R)
+                for (int S = (R == P ? Q : R + 1); S < n; ++S) {
+                    // spin conservation of the pair: N_alpha of (P,Q) = of (R,S)
+                    if (((P & 1) + (Q & 1)) != ((R & 1) + (S & 1))) continue;
+                    const double c = g_of(P, Q, R, S) - g_of(P, Q, S, R);
+                    if (c == 0.0) continue;
                     int idx[4] = {qubit_of[P], qubit_of[Q], qubit_of[S], qubit_of[R]};
                     bool dag[4] = {true, true, false, false};
-                    add(expand(4, idx, dag, g, buf));
+                    const int cnt = expand(4, idx, dag, c, buf);
+                    if (R == P && S == Q) add(cnt);
+                    else add_hermitian(cnt);
                 }
-            }
-        }
     acc.add(key(0, 0), e_core);
 
     // merge residue: drop |c| <= 1e-13 max|c| (no approximate truncation)

@@ -142,7 +142,7 @@ class _Slot:
 
 class _DevSlot:
     """A fragment whose whole solve is enqueued on its stream at admission:
-    `steps` x (graph replay of the evaluation + device L-BFGS step)."""
+    `steps` replays of one captured graph (evaluation + device L-BFGS step)."""
 
     def __init__(self, req, ctx, stream, t_admit, steps):
         import torch
@@ -157,14 +157,11 @@ class _DevSlot:
         ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=steps)
         # everything of this fragment is ordered on its own stream
         with torch.cuda.stream(stream):
-            self.th_dev = torch.zeros(k, dtype=torch.float64, device=dev)
-            self.E_dev = torch.zeros(1, dtype=torch.float64, device=dev)
-            self.g_dev = torch.zeros(k, dtype=torch.float64, device=dev)
-            ctx.capture(self.th_dev[: k].view(1, -1), self.E_dev, self.g_dev[: k].view(1, -1), stream)
+            buf = torch.zeros(2 * k + 1, dtype=torch.float64, device=dev)  # theta | grad | E
+            self.th_dev, self.g_dev, self.E_dev = buf[:k], buf[k:2 * k], buf[2 * k:]
+            ctx.capture_vqe_step(self.th_dev, self.E_dev, self.g_dev, stream)
             for _ in range(steps):
-                ctx.replay(stream)
-                ctx.opt_step(self.th_dev.data_ptr(), self.E_dev.data_ptr(), self.g_dev.data_ptr(),
-                             stream)
+                ctx.replay(stream)  # evaluation + device L-BFGS step
             self.done = torch.cuda.Event()
             self.done.record(stream)
 
