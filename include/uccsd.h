@@ -88,7 +88,10 @@ typedef struct {
     int batch;            /* state slots reserved */
     int precision;        /* uccsd_prec */
     int layout;           /* uccsd_layout */
-    size_t device_bytes;  /* device memory held by the context */
+    size_t device_bytes;  /* device memory held by the context alone (the
+                             precomputed pair lists of a plan are one copy
+                             per device, shared by all contexts of the plan,
+                             and not counted here) */
     uint64_t launches;    /* kernels launched by this context so far */
 } uccsd_info_t;
 

@@ -624,68 +624,114 @@ uint64_t plan_hash(const uccsd_ctx *c, const SweepPlan &pl) {
     return h;
 }
 
-struct CachedLists {
+// One device copy of a plan's pair lists, shared by every context on that
+// device whose plan has the same hash.  Freed when the cache has dropped the
+// plan and no context holds it.
+struct DeviceLists {
+    int device = -1;
+    void *op_pl = nullptr, *pairs = nullptr;
+    size_t bytes = 0;
+    ~DeviceLists() {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) return;
+        cudaSetDevice(device);
+        if (op_pl) cudaFree(op_pl);
+        if (pairs) cudaFree(pairs);
+        cudaSetDevice(cur);
+        cudaGetLastError();
+    }
+};
+
+struct ListEntry {
     std::shared_ptr<PairLists> lists;  // null: over the size limit
     std::vector<int32_t> pl_base;
+    std::mutex dev_mu;
+    std::vector<std::shared_ptr<DeviceLists>> dev;  // by device, uploaded on first use
 };
 
 std::mutex g_list_mu;
-std::vector<std::pair<uint64_t, CachedLists>> g_list_cache;  // most recent last, at most 32
+// most recent last, at most 32; never destroyed (no CUDA calls at exit)
+auto *g_list_cache = new std::vector<std::pair<uint64_t, std::shared_ptr<ListEntry>>>();
 
-CachedLists cached_lists(const uccsd_ctx *c, SweepPlan *pl, uint64_t key) {
+std::shared_ptr<ListEntry> cached_lists(const uccsd_ctx *c, SweepPlan *pl, uint64_t key) {
     {
         std::lock_guard<std::mutex> lk(g_list_mu);
-        for (auto &kv : g_list_cache)
+        for (auto &kv : *g_list_cache)
             if (kv.first == key) return kv.second;
     }
-    CachedLists cl;
+    auto ent = std::make_shared<ListEntry>();
     auto L = std::make_shared<PairLists>();
     // 8-byte amplitudes: 16 lanes per shared-memory wavefront; 16-byte: 8
     if (build_pair_lists(c->n, c->n_alpha, c->n_beta, kMaxListPairs, pl, L.get(), c->prec ? 16 : 8))
-        cl.lists = L;
-    for (const CRunDev &r : pl->runs) cl.pl_base.push_back(r.pl_base);
+        ent->lists = L;
+    for (const CRunDev &r : pl->runs) ent->pl_base.push_back(r.pl_base);
     std::lock_guard<std::mutex> lk(g_list_mu);
-    g_list_cache.emplace_back(key, cl);
-    if (g_list_cache.size() > 32) g_list_cache.erase(g_list_cache.begin());
-    return cl;
+    for (auto &kv : *g_list_cache)
+        if (kv.first == key) return kv.second;  // another thread built it meanwhile
+    g_list_cache->emplace_back(key, ent);
+    if (g_list_cache->size() > 32) g_list_cache->erase(g_list_cache->begin());
+    return ent;
 }
 
-// Attach pair lists to a plan and its sweep arguments (tag "fwd" / "adj").
-// Without lists (too large, or over the HBM budget) the plan keeps the
-// builder kernels.
-uccsd_status attach_lists(uccsd_ctx *c, SweepPlan *pl, SweepArgs *args, const std::string &tag) {
+// The device copy of an entry's lists on c's device, uploaded once (a
+// synchronous copy: no context may see the lists before they are complete).
+uccsd_status device_lists(uccsd_ctx *c, ListEntry &ent, std::shared_ptr<DeviceLists> *out) {
+    std::lock_guard<std::mutex> lk(ent.dev_mu);
+    if (ent.dev.size() <= size_t(c->device)) ent.dev.resize(c->device + 1);
+    if (!ent.dev[c->device]) {
+        const PairLists &L = *ent.lists;
+        auto d = std::make_shared<DeviceLists>();
+        d->device = c->device;
+        const size_t b1 = sizeof(int32_t) * std::max<size_t>(L.op_pl.size(), 1);
+        const size_t b2 = sizeof(uint32_t) * std::max<size_t>(L.pairs.size(), 1);
+        cudaError_t e = cudaMalloc(&d->op_pl, b1);
+        if (e == cudaSuccess) e = cudaMalloc(&d->pairs, b2);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, UCCSD_ERR_OOM, "cudaMalloc of the shared pair lists failed");
+        }
+        d->bytes = b1 + b2;
+        if (!L.op_pl.empty())
+            e = cudaMemcpy(d->op_pl, L.op_pl.data(), sizeof(int32_t) * L.op_pl.size(),
+                           cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !L.pairs.empty())
+            e = cudaMemcpy(d->pairs, L.pairs.data(), sizeof(uint32_t) * L.pairs.size(),
+                           cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pair-list upload");
+        ent.dev[c->device] = d;
+    }
+    *out = ent.dev[c->device];
+    return UCCSD_OK;
+}
+
+// Attach pair lists to a plan and its sweep arguments (slot 0 forward,
+// 1 adjoint).  Without lists (too large, or beyond the context's HBM budget)
+// the plan keeps the builder kernels.
+uccsd_status attach_lists(uccsd_ctx *c, SweepPlan *pl, SweepArgs *args, int slot) {
     args->op_pl = nullptr;
     args->pairs = nullptr;
     const uint64_t key = plan_hash(c, *pl);
-    CachedLists cl = cached_lists(c, pl, key);
-    for (size_t r = 0; r < pl->runs.size(); ++r) pl->runs[r].pl_base = cl.lists ? cl.pl_base[r] : -1;
-    uint64_t &held = c->list_key[tag == "fwd" ? 0 : 1];
-    if (!cl.lists) {
-        release(c, tag + "_pl");
-        release(c, tag + "_pairs");
-        held = 0;
+    std::shared_ptr<ListEntry> ent = cached_lists(c, pl, key);
+    auto no_lists = [&] {
+        for (CRunDev &r : pl->runs) r.pl_base = -1;
+        c->lists_held[slot].reset();
+        c->list_key[slot] = 0;
         return UCCSD_OK;
-    }
-    if (held != key || !dptr(c, tag + "_pl") || !dptr(c, tag + "_pairs")) {
-        // (re)upload unless this context already holds the lists of the same plan
-        const PairLists &L = *cl.lists;
-        int32_t *p2;
-        uint32_t *p4;
-        held = 0;
-        uccsd_status st = upload(c, tag + "_pl", L.op_pl, &p2);
-        if (st == UCCSD_OK) st = upload(c, tag + "_pairs", L.pairs, &p4);
-        if (st == UCCSD_ERR_BUDGET) {
-            release(c, tag + "_pl");
-            release(c, tag + "_pairs");
-            for (CRunDev &r : pl->runs) r.pl_base = -1;
-            c->err.clear();
-            return UCCSD_OK;
-        }
+    };
+    if (!ent->lists) return no_lists();
+    std::shared_ptr<DeviceLists> d;
+    if (c->list_key[slot] == key && c->lists_held[slot]) {
+        d = std::static_pointer_cast<DeviceLists>(c->lists_held[slot]);
+    } else {
+        uccsd_status st = device_lists(c, *ent, &d);
         if (st) return st;
-        held = key;
+        if (c->budget && c->bytes + d->bytes > c->budget) return no_lists();
+        c->lists_held[slot] = d;
+        c->list_key[slot] = key;
     }
-    args->op_pl = static_cast<const int2 *>(dptr(c, tag + "_pl"));
-    args->pairs = static_cast<const uint2 *>(dptr(c, tag + "_pairs"));
+    for (size_t r = 0; r < pl->runs.size(); ++r) pl->runs[r].pl_base = ent->pl_base[r];
+    args->op_pl = static_cast<const int2 *>(d->op_pl);
+    args->pairs = static_cast<const uint2 *>(d->pairs);
     return UCCSD_OK;
 }
 
@@ -1234,8 +1280,8 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->fwd_args.spread = p4;
     if ((st = upload(c, "adj_spread", c->adj.spread, &p4))) return st;
     c->adj_args.spread = p4;
-    if ((st = attach_lists(c, &c->fwd, &c->fwd_args, "fwd"))) return st;
-    if ((st = attach_lists(c, &c->adj, &c->adj_args, "adj"))) return st;
+    if ((st = attach_lists(c, &c->fwd, &c->fwd_args, 0))) return st;
+    if ((st = attach_lists(c, &c->adj, &c->adj_args, 1))) return st;
     // gradient partial slots: the pair-list adjoint writes one per (tile, warp)
     {
         const bool lists = c->adj_args.pairs != nullptr;
@@ -1369,6 +1415,7 @@ uccsd_status uccsd_replay(uccsd_ctx *c, void *stream) {
     cudaError_t e = cudaGraphLaunch(c->graph_exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
     c->launches += c->graph_kernels;
+    c->last_stream = static_cast<cudaStream_t>(stream);
     return UCCSD_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -54,7 +55,10 @@ struct uccsd_ctx {
     std::vector<double> op_scale;
     uccsd::SweepPlan fwd, adj;
     uccsd::SweepArgs fwd_args, adj_args;
-    uint64_t list_key[2] = {0, 0};  // plan hashes of the pair lists held (forward, adjoint)
+    // Pair lists of the forward and adjoint plans: device copies shared with
+    // every context of the same plan (not counted in `bytes`), and their hashes
+    std::shared_ptr<void> lists_held[2];
+    uint64_t list_key[2] = {0, 0};
     // shape of the last complete set_excitations (plans, tables and slots
     // depend on it and the list only, not on the integrals)
     bool exc_valid = false;

@@ -27,6 +27,7 @@ does not depend on what else is in flight (checked by the GPU tests).
 """
 from __future__ import annotations
 
+import functools
 import math
 import time
 from dataclasses import dataclass, field
@@ -69,25 +70,35 @@ class Result:
         return self.t_done - self.t_arrive
 
 
-def footprint_bytes(n_orb: int, n_alpha: int, n_beta: int, precision: int) -> int:
-    """Upper estimate of one context's device memory (bytes)."""
-    n = 2 * n_orb
-    N = 1 << n
-    A = 8 if precision == FP32_STATE else 16
-    ijab = build_uccsd_list(n_orb, n_alpha, n_beta)
-    K = len(ijab)
-    tiles = max(1, N >> 10)
-    tables = 200 * (n_orb ** 4) + (4 << 20)
-    # precomputed pair lists: the pairs of each excitation on the whole sector
-    # (exact for one-tile plans), for the forward plan and up to twice that
-    # for the adjoint plan, 8 bytes per pair
+@functools.lru_cache(maxsize=None)
+def list_bytes(n_orb: int, n_alpha: int, n_beta: int) -> int:
+    """Upper estimate of the precomputed pair lists of one shape class
+    (bytes): the pairs of each excitation on the whole sector (exact for
+    one-tile plans), for the forward plan and up to twice that for the
+    adjoint plan, 8 bytes per pair.  One device copy serves every context of
+    the class."""
     from math import comb
     pairs = 0
-    for i, j, a, b in ijab.tolist():
+    for i, j, a, b in build_uccsd_list(n_orb, n_alpha, n_beta).tolist():
         na = sum(1 for q in (i, j, a, b) if q >= 0 and q % 2 == 0) // 2
         nb = sum(1 for q in (i, j, a, b) if q >= 0 and q % 2 == 1) // 2
         pairs += (comb(n_orb - 2 * na, n_alpha - na) * comb(n_orb - 2 * nb, n_beta - nb))
-    return 2 * N * A + K * tiles * 8 + K * 256 + tables + 3 * 8 * pairs
+    return 3 * 8 * pairs
+
+
+@functools.lru_cache(maxsize=None)
+def footprint_bytes(n_orb: int, n_alpha: int, n_beta: int, precision: int,
+                    lists: bool = True) -> int:
+    """Upper estimate of one context's device memory (bytes); lists=False
+    leaves out the pair lists shared within the shape class."""
+    n = 2 * n_orb
+    N = 1 << n
+    A = 8 if precision == FP32_STATE else 16
+    K = len(build_uccsd_list(n_orb, n_alpha, n_beta))
+    tiles = max(1, N >> 10)
+    tables = 200 * (n_orb ** 4) + (4 << 20)
+    own = 2 * N * A + K * tiles * 8 + K * 256 + tables
+    return own + (list_bytes(n_orb, n_alpha, n_beta) if lists else 0)
 
 
 class _Slot:
@@ -189,6 +200,8 @@ class FragmentServer:
         n_streams = max_active if n_streams is None else n_streams
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
         self.pool = {}
+        # pair lists held for each shape class seen (one shared copy per class)
+        self.shared = {}
 
     def _context(self, req, used, stream=None):
         """A context for the request: a recycled one of the same shape class
@@ -207,6 +220,13 @@ class FragmentServer:
         ctx.set_excitations(build_uccsd_list(req.n_orb, req.n_alpha, req.n_beta))
         return ctx
 
+    def _need(self, req):
+        """(per-request reservation, shared pair-list bytes still to reserve
+        for the request's shape class)."""
+        key = (req.n_orb, req.n_alpha, req.n_beta)
+        need = footprint_bytes(*key, self.precision, lists=False)
+        return need, (0 if key in self.shared else list_bytes(*key))
+
     def _release(self, req, ctx):
         self.pool.setdefault((req.n_orb, req.n_alpha, req.n_beta), []).append(ctx)
 
@@ -215,6 +235,7 @@ class FragmentServer:
             for ctx in lst:
                 ctx.close()
         self.pool = {}
+        self.shared = {}
 
     def run(self, requests, rate=None, keep_theta=False):
         """Serve `requests` (arrivals at t_unit / rate seconds; rate None =
@@ -250,7 +271,8 @@ class FragmentServer:
         active: list[_DevSlot] = []
         free_streams = list(self.streams)
         results: list[Result] = []
-        used = peak_used = dev_used = peak_dev = 0
+        used = peak_used = sum(self.shared.values())
+        dev_used = peak_dev = 0
         n_evals = 0
         while pending < len(reqs) or active:
             now = time.perf_counter() - t0
@@ -258,15 +280,17 @@ class FragmentServer:
             if (pending < len(reqs) and arrive[pending] <= now
                     and len(active) < self.max_active and free_streams):
                 q = reqs[pending]
-                need = footprint_bytes(q.n_orb, q.n_alpha, q.n_beta, self.precision)
-                if used + need <= self.hbm_budget or not active:
+                need, extra = self._need(q)
+                if used + need + extra <= self.hbm_budget or not active:
                     st = free_streams.pop()
                     ctx = self._context(q, used, st)
                     slot = _DevSlot(q, ctx, st, time.perf_counter() - t0, self.steps)
                     slot.reserved = need
                     slot.dev_bytes = ctx.info()["device_bytes"]
                     slot.t_arrive = arrive[pending]
-                    used += need
+                    if extra:
+                        self.shared[(q.n_orb, q.n_alpha, q.n_beta)] = extra
+                    used += need + extra
                     dev_used += slot.dev_bytes
                     peak_used = max(peak_used, used)
                     peak_dev = max(peak_dev, dev_used)
@@ -308,8 +332,8 @@ class FragmentServer:
         pending = 0
         active: list[_Slot] = []
         results: list[Result] = []
-        used = 0          # reserved by admission (upper estimates)
-        peak_used = 0
+        used = sum(self.shared.values())  # reserved by admission (upper estimates)
+        peak_used = used
         dev_used = 0      # device bytes the active contexts report
         peak_dev = 0
         n_evals = 0
@@ -321,9 +345,12 @@ class FragmentServer:
             while (pending < len(reqs) and arrive[pending] <= now
                    and len(active) < self.max_active):
                 q = reqs[pending]
-                need = footprint_bytes(q.n_orb, q.n_alpha, q.n_beta, self.precision)
-                if used + need > self.hbm_budget and active:
+                need, extra = self._need(q)
+                if used + need + extra > self.hbm_budget and active:
                     break
+                if extra:
+                    self.shared[(q.n_orb, q.n_alpha, q.n_beta)] = extra
+                used += extra
                 ctx = self._context(q, used)
                 slot = _Slot(q, ctx, self.precision, self.streams[next_stream % len(self.streams)],
                              now, self.steps)
