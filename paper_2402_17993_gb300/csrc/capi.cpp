@@ -284,6 +284,10 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     std::string err;
     if (!make_tables<R>(c->H, c->n_orb, &T, &err)) return fail(c, UCCSD_ERR_ARG, err);
     std::string t(tag);
+    c->spec_s1a.resize(T.s1a.size());
+    c->spec_s1b.resize(T.s1b.size());
+    for (size_t i = 0; i < T.s1a.size(); ++i) c->spec_s1a[i] = T.s1a[i].spec;
+    for (size_t i = 0; i < T.s1b.size(); ++i) c->spec_s1b[i] = T.s1b[i].spec;
     MixT<R> *mx;
     MixO<R> *mo, *oa, *ob;
     SglT<R> *sa, *sb;
@@ -368,6 +372,59 @@ uccsd_status upload_tile_tables(uccsd_ctx *c) {
 
 // Row/column layout of the sector for the reference's electron counts and
 // the state addressing of the context's layout.
+// Beta-spectator sums of the pair groups per column of the reference's
+// beta strings (see DevHam::bspec_a / bspec_b), summed in FP64 and rounded
+// once to R.
+template <typename R>
+uccsd_status upload_spectator_tables(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
+    const int no = c->n_orb;
+    std::vector<uint32_t> bstr;
+    for (uint32_t sv = 0; sv < (1u << no); ++sv)
+        if (__builtin_popcount(sv) == c->n_beta) bstr.push_back(sv);
+    const size_t Db = bstr.size();
+    const int np = no * (no - 1) / 2;
+    const std::vector<double> &spec = c->H.spec;
+    auto row_sum = [&](int spec_row, int pat, uint32_t occ) {
+        double v = 0.0;
+        for (uint32_t w = occ; w; w &= w - 1u)
+            v += spec[size_t(spec_row + 2 * __builtin_ctz(w) + 1) * 4 + pat];
+        return v;
+    };
+    std::vector<R> ta(size_t(2) * std::max(np, 1) * std::max<size_t>(Db, 1), R(0));
+    for (int pa = 0; pa < np; ++pa) {
+        const int sr = pa < int(c->spec_s1a.size()) ? c->spec_s1a[pa] : -1;
+        if (sr < 0) continue;
+        for (int sel = 0; sel < 2; ++sel)
+            for (size_t col = 0; col < Db; ++col)
+                ta[(size_t(pa) * 2 + sel) * Db + col] = R(row_sum(sr, sel ? 2 : 1, bstr[col]));
+    }
+    const int ns = c->n_beta * (no - c->n_beta);
+    std::vector<R> tb(size_t(std::max(ns, 1)) * std::max<size_t>(Db, 1), R(0));
+    for (size_t col = 0; col < Db; ++col) {
+        const uint32_t sb = bstr[col];
+        int k = 0;
+        for (int j = 0; j < no; ++j) {
+            if (!((sb >> j) & 1u)) continue;
+            for (int bb = 0; bb < no; ++bb) {
+                if ((sb >> bb) & 1u) continue;
+                const int pb = pair_idx(std::min(j, bb), std::max(j, bb));
+                const int sr = pb < int(c->spec_s1b.size()) ? c->spec_s1b[pb] : -1;
+                const uint32_t yb = sb ^ (1u << j) ^ (1u << bb);
+                if (sr >= 0) tb[size_t(k) * Db + col] = R(row_sum(sr, bb > j ? 2 : 1, yb & ~(1u << bb)));
+                ++k;
+            }
+        }
+    }
+    std::string t(tag);
+    R *pa_, *pb_;
+    uccsd_status st;
+    if ((st = upload(c, t + "bspec_a", ta, &pa_))) return st;
+    if ((st = upload(c, t + "bspec_b", tb, &pb_))) return st;
+    dh->bspec_a = pa_;
+    dh->bspec_b = pb_;
+    return UCCSD_OK;
+}
+
 uccsd_status set_row_layout(uccsd_ctx *c) {
     const int no = c->n_orb;
     const size_t base = (size_t(1) << no) - 1;
@@ -381,7 +438,45 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
     c->hsec.n_beta = c->n_beta;
     c->hsec.aoff = c->hsec.aspread;
     c->hsec.boff = c->hsec.bspread;
+    {
+        // beta single excitations of every column (layout independent)
+        std::vector<uint32_t> bstr_h, rank_h(size_t(1) << no, 0u);
+        for (uint32_t sv = 0; sv < (1u << no); ++sv)
+            if (__builtin_popcount(sv) == c->n_beta) {
+                rank_h[sv] = uint32_t(bstr_h.size());
+                bstr_h.push_back(sv);
+            }
+        const int Db = int(bstr_h.size());
+        const int ns = c->n_beta * (no - c->n_beta);
+        std::vector<uint32_t> tab(size_t(2) * std::max(ns, 1) * std::max(Db, 1), 0u);
+        for (int col = 0; col < Db; ++col) {
+            const uint32_t sb = bstr_h[col];
+            int k = 0;
+            for (int j = 0; j < no; ++j) {
+                if (!((sb >> j) & 1u)) continue;
+                for (int bb = 0; bb < no; ++bb) {
+                    if ((sb >> bb) & 1u) continue;
+                    const uint32_t yb = sb ^ (1u << j) ^ (1u << bb);
+                    const size_t at = 2 * (size_t(k) * Db + col);
+                    const int lo = std::min(j, bb), hi = std::max(j, bb);
+                    tab[at] = rank_h[yb] | (uint32_t(j * no + bb) << 16);
+                    tab[at + 1] = yb | (uint32_t(pair_idx(lo, hi)) << 16) | (uint32_t(bb > j) << 24);
+                    ++k;
+                }
+            }
+        }
+        uint32_t *p4;
+        uccsd_status st = upload(c, "bsing", tab, &p4);
+        if (st) return st;
+        c->hsec.bsing = reinterpret_cast<const uint2 *>(p4);
+        c->hsec.n_bs = ns;
+    }
     c->hsec_full = c->hsec;
+    {
+        uccsd_status st = c->prec ? upload_spectator_tables<float>(c, &c->hf32, "h32_")
+                                  : upload_spectator_tables<double>(c, &c->hf64, "h64_");
+        if (st) return st;
+    }
     const uint32_t hfa = uint32_t((1u << c->n_alpha) - 1u), hfb = uint32_t((1u << c->n_beta) - 1u);
     c->hf_addr = c->hf;
     if (c->layout) {

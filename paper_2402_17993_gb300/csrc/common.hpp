@@ -53,6 +53,14 @@ struct alignas(sizeof(R) == 4 ? 8 : 16) MixO {
     R w;
     uint32_t j;
 };
+// One alpha double excitation of an H-apply row, staged per CTA: the
+// same-spin double's table value, the source row offset, the source alpha
+// string and the group's Jordan-Wigner mask.
+template <typename R>
+struct ADbl {
+    R w;
+    uint32_t xoff, s, j;
+};
 // Same-spin single (pair): lut[sel] at the source occupying the higher
 // (sel = 1) or lower orbital; spectator rows start at spec (rows of 4,
 // pattern 1 = lower occupied, 2 = higher occupied).

@@ -50,6 +50,7 @@ struct uccsd_ctx {
     int layout = 0;        // 0 full 2^n vector, 1 electron-sector array (UCCSD_LAYOUT_*)
     uint32_t hf_addr = 0;  // address of the reference amplitude in a slot
     uccsd::CompiledH H;
+    std::vector<int32_t> spec_s1a, spec_s1b;  // spectator row of each alpha / beta pair group
     int K = 0, order = 1, M = 1;
     std::vector<int32_t> ijab, op_k;
     std::vector<double> op_scale;

@@ -128,6 +128,19 @@ __host__ __device__ inline size_t happly_aspec_offset(int Db, int n_orb) {
     return (o + 7) & ~(size_t)7;
 }
 
+// Then (16-byte aligned) the current alpha single's row of the ordered
+// mixed table (n_orb^2 entries) and the row's alpha doubles.
+template <typename R>
+__host__ __device__ inline size_t happly_mrow_offset(int Db, int n_orb) {
+    const size_t o = happly_aspec_offset<R>(Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1);
+    return (o + 15) & ~(size_t)15;
+}
+template <typename R>
+__host__ __device__ inline size_t happly_adbl_offset(int Db, int n_orb) {
+    const size_t o = happly_mrow_offset<R>(Db, n_orb) + sizeof(MixO<R>) * (size_t)n_orb * n_orb;
+    return (o + 15) & ~(size_t)15;
+}
+
 __device__ __forceinline__ int pair_index(int p, int q) {  // p < q
     return (q * (q - 1) >> 1) + p;
 }
@@ -156,6 +169,8 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
     // alpha-spectator part of each beta single's value for this row, [pair][sel]
     R *aspec = reinterpret_cast<R *>(smem_raw + happly_aspec_offset<R>(hs.Db, H.n_orb));
+    MixO<R> *mrow_s = reinterpret_cast<MixO<R> *>(smem_raw + happly_mrow_offset<R>(hs.Db, H.n_orb));
+    ADbl<R> *adl = reinterpret_cast<ADbl<R> *>(smem_raw + happly_adbl_offset<R>(hs.Db, H.n_orb));
     __shared__ double red[32];
     __shared__ int nb4[16 * 5];
     __shared__ R a_single;  // alpha part of the current alpha single's value
@@ -182,6 +197,38 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         const uint32_t xR = hs.aoff[sR];
         for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
             src[c] = st[xR + hs.boff[hs.bstr[c]]];
+    }
+    // the row's alpha doubles: occupied pair t (loop order o1 < o2) owns the
+    // entries [t * nvp, (t + 1) * nvp) over the empty pairs (q1 < q2)
+    const uint32_t virA = full & ~sR;
+    const int nva = n_orb - hs.n_alpha;
+    const int nop = hs.n_alpha * (hs.n_alpha - 1) / 2, nvp = nva * (nva - 1) / 2;
+    for (int t = threadIdx.x; t < nop; t += blockDim.x) {
+        int k = 0, p1 = -1, p2 = -1;
+        for (uint32_t o1 = sR; o1 && p1 < 0; o1 &= o1 - 1u)
+            for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u, ++k)
+                if (k == t) {
+                    p1 = __ffs(o1) - 1;
+                    p2 = __ffs(o2) - 1;
+                    break;
+                }
+        const MixO<R> *Dp = H.d2ao + (size_t)(p1 * n_orb + p2) * n_orb * n_orb;
+        ADbl<R> *L = adl + (size_t)t * nvp;
+        int m = 0;
+        for (uint32_t v1 = virA; v1; v1 &= v1 - 1u) {
+            const int q1 = __ffs(v1) - 1;
+            for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
+                const int q2 = __ffs(v2) - 1;
+                const MixO<R> Dq = Dp[q1 * n_orb + q2];
+                const uint32_t sRp = sR ^ ((1u << p1) | (1u << p2) | (1u << q1) | (1u << q2));
+                ADbl<R> e;
+                e.w = Dq.w;
+                e.xoff = hs.aoff[sRp];
+                e.s = sRp;
+                e.j = Dq.j;
+                L[m++] = e;
+            }
+        }
     }
     __syncthreads();
 
@@ -221,26 +268,23 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             }
             accumulate<R>(acc[i], comp[i], (R)q * (R)H.diag_unit, own[i]);
         }
-        const uint32_t vir = full & ~cb_str;
-        for (uint32_t o = cb_str; o; o &= o - 1u) {
-            const int j = __ffs(o) - 1;
-            for (uint32_t v = vir; v; v &= v - 1u) {
-                const int bb = __ffs(v) - 1;
-                const int lo = min(j, bb), hi = max(j, bb);
-                const int pb = pair_index(lo, hi);
+        // beta singles (precomputed per column: source rank, pair group,
+        // source side, beta-spectator sum)
+        {
+            const uint2 *bsc = hs.bsing + cix[i];
+            const R *bsp = H.bspec_b + cix[i];
+            for (int t = 0; t < hs.n_bs; ++t) {
+                const uint2 e = __ldg(bsc + (size_t)t * hs.Db);
+                const int pb = (int)((e.y >> 16) & 0xFFu);
+                const int sel = (int)(e.y >> 24);
                 const SglT<R> &S = H.s1b[pb];
-                const int sel = bb > j;
-                const uint32_t yb = cb_str ^ (1u << j) ^ (1u << bb);
                 R val = S.lut[sel] + aspec[2 * pb + sel];
-                if (S.spec >= 0) {
-                    const int pat = sel ? 2 : 1;
-                    for (uint32_t w = yb & ~(1u << bb); w; w &= w - 1u)
-                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
-                }
-                val = with_sign(val, jw_sign(sR | (yb << 16), S.j));
-                accumulate<R>(acc[i], comp[i], val, src[brk[yb]]);
+                val += __ldg(bsp + (size_t)t * hs.Db);
+                val = with_sign(val, jw_sign(sR | (e.y << 16), S.j));
+                accumulate<R>(acc[i], comp[i], val, src[e.x & 0xFFFFu]);
             }
         }
+        const uint32_t vir = full & ~cb_str;
         for (uint32_t o1 = cb_str; o1; o1 &= o1 - 1u) {
             const int j1 = __ffs(o1) - 1;
             for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
@@ -268,7 +312,6 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     }
 
     // ---- alpha singles: source row R ^ {p, q} ----
-    const uint32_t virA = full & ~sR;
     for (uint32_t op = sR; op; op &= op - 1u) {
         const int p = __ffs(op) - 1;
         for (uint32_t vq = virA; vq; vq &= vq - 1u) {
@@ -281,6 +324,10 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             __syncthreads();
             for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
                 src[c] = st[xRp + hs.boff[hs.bstr[c]]];
+            {
+                const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * n_orb * n_orb;
+                for (int t = threadIdx.x; t < n_orb * n_orb; t += blockDim.x) mrow_s[t] = Mrow[t];
+            }
             if (threadIdx.x == 0) {
                 // the value's alpha part: the same for every column
                 R va = S.lut[asel];
@@ -290,39 +337,28 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                 a_single = va;
             }
             __syncthreads();
-            const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * n_orb * n_orb;
 #pragma unroll
             for (int i = 0; i < EPT; ++i) {
                 if (cix[i] < 0) continue;
                 const uint32_t cb_str = sc[i];
-                // alpha-only pair group: same column
-                R val = a_single;
-                if (S.spec >= 0) {
-                    const int pat = asel ? 2 : 1;
-                    for (uint32_t w = cb_str; w; w &= w - 1u)
-                        val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1) + 1) * 4 + pat];
-                }
+                // alpha-only pair group: same column (beta-spectator sum per column)
+                R val = a_single + __ldg(H.bspec_a + ((size_t)pa * 2 + asel) * hs.Db + cix[i]);
                 val = with_sign(val, jw_sign(sRp | (cb_str << 16), S.j));
                 accumulate<R>(acc[i], comp[i], val, src[cix[i]]);
-                // mixed groups through the lane's beta single excitations:
-                // a plain partial sum per segment, added with compensation
-                const uint32_t vir = full & ~cb_str;
+                // mixed groups through the lane's beta single excitations
+                // (precomputed per column: source rank, table index, source
+                // string): a plain partial sum per segment, added with
+                // compensation
                 V2<R> seg = V2<R>{(R)0, (R)0};
-                for (uint32_t o = cb_str; o; o &= o - 1u) {
-                    const int j = __ffs(o) - 1;
-                    const MixO<R> *Mj = Mrow + j * n_orb;
-                    const uint32_t yj = cb_str ^ (1u << j);
-                    const uint32_t xj = sRp | (yj << 16);  // packed source strings
-                    for (uint32_t v = vir; v; v &= v - 1u) {
-                        const int bb = __ffs(v) - 1;
-                        const MixO<R> M = Mj[bb];
-                        const uint32_t bit = 1u << bb;
-                        const uint32_t yb = yj ^ bit;
-                        const R w = with_sign(M.w, jw_sign(xj ^ (bit << 16), M.j));
-                        const V2<R> y = src[brk[yb]];
-                        seg.x += w * y.x;
-                        seg.y += w * y.y;
-                    }
+                const uint2 *bs = hs.bsing + cix[i];
+#pragma unroll 4
+                for (int t = 0; t < hs.n_bs; ++t) {
+                    const uint2 e = __ldg(bs + (size_t)t * hs.Db);
+                    const MixO<R> M = mrow_s[e.x >> 16];
+                    const R w = with_sign(M.w, jw_sign(sRp | (e.y << 16), M.j));
+                    const V2<R> y = src[e.x & 0xFFFFu];
+                    seg.x += w * y.x;
+                    seg.y += w * y.y;
                 }
                 accumulate<R>(acc[i], comp[i], (R)1, seg);
             }
@@ -330,36 +366,23 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     }
 
     // ---- alpha doubles: source amplitude of the same column ----
-    for (uint32_t o1 = sR; o1; o1 &= o1 - 1u) {
-        const int p1 = __ffs(o1) - 1;
-        for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
-            const int p2 = __ffs(o2) - 1;
-            const MixO<R> *Dp = H.d2ao + (size_t)(p1 * n_orb + p2) * n_orb * n_orb;
-            V2<R> dseg[EPT];  // plain partial per occupied pair
 #pragma unroll
-            for (int i = 0; i < EPT; ++i) dseg[i] = V2<R>{(R)0, (R)0};
-            for (uint32_t v1 = virA; v1; v1 &= v1 - 1u) {
-                const int q1 = __ffs(v1) - 1;
-                for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
-                    const int q2 = __ffs(v2) - 1;
-                    const uint32_t m = (1u << p1) | (1u << p2) | (1u << q1) | (1u << q2);
-                    const MixO<R> Dq = Dp[q1 * n_orb + q2];
-                    const uint32_t sRp = sR ^ m;
-                    const uint32_t xRp = hs.aoff[sRp];
-                    const R base = Dq.w;
-#pragma unroll
-                    for (int i = 0; i < EPT; ++i) {
-                        if (cix[i] < 0) continue;
-                        const R val = with_sign(base, jw_sign(sRp | (sc[i] << 16), Dq.j));
-                        const V2<R> y = st[xRp + hs.boff[sc[i]]];
-                        dseg[i].x += val * y.x;
-                        dseg[i].y += val * y.y;
-                    }
-                }
+    for (int i = 0; i < EPT; ++i) {
+        if (cix[i] < 0) continue;
+        const uint32_t boffc = hs.boff[sc[i]];
+        const uint32_t cbs = sc[i] << 16;
+        for (int t = 0; t < nop; ++t) {
+            const ADbl<R> *L = adl + (size_t)t * nvp;
+            V2<R> dseg = V2<R>{(R)0, (R)0};  // plain partial per occupied pair
+#pragma unroll 4
+            for (int m = 0; m < nvp; ++m) {
+                const ADbl<R> e = L[m];
+                const R val = with_sign(e.w, jw_sign(e.s | cbs, e.j));
+                const V2<R> y = st[e.xoff + boffc];
+                dseg.x += val * y.x;
+                dseg.y += val * y.y;
             }
-#pragma unroll
-            for (int i = 0; i < EPT; ++i)
-                if (cix[i] >= 0) accumulate<R>(acc[i], comp[i], (R)1, dseg[i]);
+            accumulate<R>(acc[i], comp[i], (R)1, dseg);
         }
     }
 
@@ -554,7 +577,9 @@ cudaError_t launch_lbfgs(cudaStream_t stream, int K, int m, double max_step, dou
 
 template <typename R>
 size_t happly_smem(const HSector &hs, int n_orb) {
-    return happly_aspec_offset<R>(hs.Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1);
+    const int nva = n_orb - hs.n_alpha;
+    const size_t nad = (size_t)(hs.n_alpha * (hs.n_alpha - 1) / 2) * (nva * (nva - 1) / 2);
+    return happly_adbl_offset<R>(hs.Db, n_orb) + sizeof(ADbl<R>) * nad;
 }
 
 template <typename R>

@@ -24,6 +24,15 @@ struct DevHam {
     const DblT<R> *d2a = nullptr;  // [n_quads] alpha doubles
     const DblT<R> *d2b = nullptr;  // [n_quads] beta doubles
     const R *spec = nullptr;       // spectator rows [row][4]
+    // Beta-spectator sums per column (Db columns, the reference's beta
+    // strings), zero for groups without spectator rows:
+    //   bspec_a[(pa * 2 + sel) * Db + c]: alpha pair group pa, source side sel,
+    //     summed over the occupied beta orbitals of column c;
+    //   bspec_b[t * Db + c]: the t-th beta single of column c (order of
+    //     HSector::bsing), summed over the source's occupied beta orbitals
+    //     other than the created one.
+    const R *bspec_a = nullptr;
+    const R *bspec_b = nullptr;
     // Diagonal group as an occupation quadratic form in 64-bit fixed point
     // (one unit = diag_unit Ha), summed exactly:
     //   d(x) - shift = q0 + sum_{q in occ(x)} qa[q] + sum_{q<r in occ(x)} qb[q*n + r]
@@ -53,6 +62,13 @@ struct HSector {
     const uint32_t *aoff = nullptr;
     const uint32_t *boff = nullptr;
     const int32_t *binom = nullptr;    // binom[t * 5 + k], t < 16, k <= 4
+    // Beta single excitations of every column, [s][Db] with s over the
+    // column's occupied j (ascending) then virtual b (ascending):
+    // x = rank of the source string yb = bstr ^ {j, b} | (j * n_orb + b) << 16,
+    // y = yb | pair_index(min(j, b), max(j, b)) << 16 | (b > j) << 24.
+    // n_bs = n_beta * (n_orb - n_beta) per column.
+    const uint2 *bsing = nullptr;
+    int n_bs = 0;
     int n_alpha = 0, n_beta = 0;
     int Da = 0, Db = 0;
     int colblock = 0, ncb = 1;
