@@ -470,6 +470,11 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
         if (st) return st;
         c->hsec.bsing = reinterpret_cast<const uint2 *>(p4);
         c->hsec.n_bs = ns;
+        // alpha singles per H-apply phase: up to 4 while their staged source
+        // rows take at most 24 KiB of shared memory
+        const size_t row = size_t(Db) * (c->prec ? 8 : 16);  // one staged source row
+        c->hsec.ag = 1;
+        while (c->hsec.ag < 4 && size_t(2 * c->hsec.ag) * row <= (size_t(24) << 10)) c->hsec.ag *= 2;
     }
     c->hsec_full = c->hsec;
     {

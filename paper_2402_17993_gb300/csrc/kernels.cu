@@ -128,17 +128,33 @@ __host__ __device__ inline size_t happly_aspec_offset(int Db, int n_orb) {
     return (o + 7) & ~(size_t)7;
 }
 
-// Then (16-byte aligned) the current alpha single's row of the ordered
-// mixed table (n_orb^2 entries) and the row's alpha doubles.
+// One alpha single excitation of an H-apply row: source alpha string,
+// source row offset, p | q << 8 (p occupied, q empty in the target).
+struct ASgl {
+    uint32_t s, xoff, pq;
+};
+
+// Shared-memory layout after the aspec block (offsets 16-byte aligned):
+// the row's alpha singles, its alpha doubles, then for a group of G alpha
+// singles their source rows, their rows of the ordered mixed table and
+// their alpha-only values.
+struct HappLayout {
+    size_t asl, adl, srcg, mrow, asing, total;
+};
 template <typename R>
-__host__ __device__ inline size_t happly_mrow_offset(int Db, int n_orb) {
-    const size_t o = happly_aspec_offset<R>(Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1);
-    return (o + 15) & ~(size_t)15;
-}
-template <typename R>
-__host__ __device__ inline size_t happly_adbl_offset(int Db, int n_orb) {
-    const size_t o = happly_mrow_offset<R>(Db, n_orb) + sizeof(MixO<R>) * (size_t)n_orb * n_orb;
-    return (o + 15) & ~(size_t)15;
+__host__ __device__ inline HappLayout happly_layout(int Db, int n_orb, int n_alpha, int G) {
+    auto up = [](size_t o) { return (o + 15) & ~(size_t)15; };
+    const int nva = n_orb - n_alpha;
+    const size_t nas = (size_t)n_alpha * nva;
+    const size_t nad = (size_t)(n_alpha * (n_alpha - 1) / 2) * (nva * (nva - 1) / 2);
+    HappLayout L;
+    L.asl = up(happly_aspec_offset<R>(Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1));
+    L.adl = up(L.asl + sizeof(ASgl) * nas);
+    L.srcg = up(L.adl + sizeof(ADbl<R>) * nad);
+    L.mrow = up(L.srcg + sizeof(V2<R>) * (size_t)G * Db);
+    L.asing = up(L.mrow + sizeof(MixO<R>) * (size_t)G * n_orb * n_orb);
+    L.total = L.asing + sizeof(R) * (size_t)G;
+    return L;
 }
 
 __device__ __forceinline__ int pair_index(int p, int q) {  // p < q
@@ -169,11 +185,14 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
     // alpha-spectator part of each beta single's value for this row, [pair][sel]
     R *aspec = reinterpret_cast<R *>(smem_raw + happly_aspec_offset<R>(hs.Db, H.n_orb));
-    MixO<R> *mrow_s = reinterpret_cast<MixO<R> *>(smem_raw + happly_mrow_offset<R>(hs.Db, H.n_orb));
-    ADbl<R> *adl = reinterpret_cast<ADbl<R> *>(smem_raw + happly_adbl_offset<R>(hs.Db, H.n_orb));
+    const HappLayout lay = happly_layout<R>(hs.Db, H.n_orb, hs.n_alpha, hs.ag);
+    ASgl *asl = reinterpret_cast<ASgl *>(smem_raw + lay.asl);
+    ADbl<R> *adl = reinterpret_cast<ADbl<R> *>(smem_raw + lay.adl);
+    V2<R> *srcg = reinterpret_cast<V2<R> *>(smem_raw + lay.srcg);
+    MixO<R> *mrowg = reinterpret_cast<MixO<R> *>(smem_raw + lay.mrow);
+    R *asing = reinterpret_cast<R *>(smem_raw + lay.asing);
     __shared__ double red[32];
     __shared__ int nb4[16 * 5];
-    __shared__ R a_single;  // alpha part of the current alpha single's value
     const int b = blockIdx.y;
     const int row = blockIdx.x / hs.ncb;
     const int cb = blockIdx.x - row * hs.ncb;
@@ -198,9 +217,25 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
             src[c] = st[xR + hs.boff[hs.bstr[c]]];
     }
+    // the row's alpha singles in loop order (p occupied ascending, then q
+    // empty ascending): entry ip * nva + iq
+    const uint32_t virA = full & ~sR;
+    for (int t = threadIdx.x; t < hs.n_alpha * (n_orb - hs.n_alpha); t += blockDim.x) {
+        const int nv = n_orb - hs.n_alpha;
+        int ip = t / nv, iq = t - (t / nv) * nv;
+        uint32_t o = sR, v = virA;
+        for (; ip > 0; --ip) o &= o - 1u;
+        for (; iq > 0; --iq) v &= v - 1u;
+        const int p = __ffs(o) - 1, q = __ffs(v) - 1;
+        const uint32_t sRp = sR ^ (1u << p) ^ (1u << q);
+        ASgl a;
+        a.s = sRp;
+        a.xoff = hs.aoff[sRp];
+        a.pq = (uint32_t)p | ((uint32_t)q << 8);
+        asl[t] = a;
+    }
     // the row's alpha doubles: occupied pair t (loop order o1 < o2) owns the
     // entries [t * nvp, (t + 1) * nvp) over the empty pairs (q1 < q2)
-    const uint32_t virA = full & ~sR;
     const int nva = n_orb - hs.n_alpha;
     const int nop = hs.n_alpha * (hs.n_alpha - 1) / 2, nvp = nva * (nva - 1) / 2;
     for (int t = threadIdx.x; t < nop; t += blockDim.x) {
@@ -311,56 +346,77 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         }
     }
 
-    // ---- alpha singles: source row R ^ {p, q} ----
-    for (uint32_t op = sR; op; op &= op - 1u) {
-        const int p = __ffs(op) - 1;
-        for (uint32_t vq = virA; vq; vq &= vq - 1u) {
-            const int q = __ffs(vq) - 1;
-            const uint32_t sRp = sR ^ (1u << p) ^ (1u << q);
-            const uint32_t xRp = hs.aoff[sRp];
-            const int pa = pair_index(min(p, q), max(p, q));
-            const int asel = q > p;
-            const SglT<R> &S = H.s1a[pa];
-            __syncthreads();
+    // ---- alpha singles, G per phase: source rows R ^ {p, q} ----
+    const int nas = hs.n_alpha * nva, G = hs.ag;
+    const int nn = n_orb * n_orb;
+    for (int g0 = 0; g0 < nas; g0 += G) {
+        const int gn = min(G, nas - g0);
+        __syncthreads();  // the previous group's rows are consumed
+        for (int g = 0; g < gn; ++g) {
+            const ASgl a = asl[g0 + g];
+            V2<R> *dst = srcg + (size_t)g * hs.Db;
             for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
-                src[c] = st[xRp + hs.boff[hs.bstr[c]]];
-            {
-                const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * n_orb * n_orb;
-                for (int t = threadIdx.x; t < n_orb * n_orb; t += blockDim.x) mrow_s[t] = Mrow[t];
-            }
-            if (threadIdx.x == 0) {
-                // the value's alpha part: the same for every column
-                R va = S.lut[asel];
-                if (S.spec >= 0)
-                    for (uint32_t w = sRp & ~(1u << q); w; w &= w - 1u)
-                        va += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + (asel ? 2 : 1)];
-                a_single = va;
-            }
-            __syncthreads();
+                dst[c] = st[a.xoff + hs.boff[hs.bstr[c]]];
+            const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
+            const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * nn;
+            for (int t = threadIdx.x; t < nn; t += blockDim.x) mrowg[g * nn + t] = Mrow[t];
+        }
+        if (threadIdx.x < gn) {
+            // the alpha-only group value's alpha part: the same for every column
+            const ASgl a = asl[g0 + threadIdx.x];
+            const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
+            const int asel = q > p;
+            const SglT<R> &S = H.s1a[pair_index(min(p, q), max(p, q))];
+            R va = S.lut[asel];
+            if (S.spec >= 0)
+                for (uint32_t w = a.s & ~(1u << q); w; w &= w - 1u)
+                    va += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + (asel ? 2 : 1)];
+            asing[threadIdx.x] = va;
+        }
+        __syncthreads();
+        uint32_t sg[4];
 #pragma unroll
-            for (int i = 0; i < EPT; ++i) {
-                if (cix[i] < 0) continue;
-                const uint32_t cb_str = sc[i];
-                // alpha-only pair group: same column (beta-spectator sum per column)
-                R val = a_single + __ldg(H.bspec_a + ((size_t)pa * 2 + asel) * hs.Db + cix[i]);
-                val = with_sign(val, jw_sign(sRp | (cb_str << 16), S.j));
-                accumulate<R>(acc[i], comp[i], val, src[cix[i]]);
-                // mixed groups through the lane's beta single excitations
-                // (precomputed per column: source rank, table index, source
-                // string): a plain partial sum per segment, added with
-                // compensation
-                V2<R> seg = V2<R>{(R)0, (R)0};
-                const uint2 *bs = hs.bsing + cix[i];
-#pragma unroll 4
-                for (int t = 0; t < hs.n_bs; ++t) {
-                    const uint2 e = __ldg(bs + (size_t)t * hs.Db);
-                    const MixO<R> M = mrow_s[e.x >> 16];
-                    const R w = with_sign(M.w, jw_sign(sRp | (e.y << 16), M.j));
-                    const V2<R> y = src[e.x & 0xFFFFu];
-                    seg.x += w * y.x;
-                    seg.y += w * y.y;
+        for (int g = 0; g < 4; ++g) sg[g] = g < gn ? asl[g0 + g].s : 0u;
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            if (cix[i] < 0) continue;
+            const uint32_t cb_str = sc[i];
+            // mixed groups through the lane's beta single excitations
+            // (precomputed per column: source rank, table index, source
+            // string), one table entry for the G singles of the phase: a
+            // plain partial sum per alpha single, added with compensation
+            V2<R> seg[4];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) seg[g] = V2<R>{(R)0, (R)0};
+            const uint2 *bs = hs.bsing + cix[i];
+#pragma unroll 2
+            for (int t = 0; t < hs.n_bs; ++t) {
+                const uint2 e = __ldg(bs + (size_t)t * hs.Db);
+                const uint32_t jb = e.x >> 16, rk = e.x & 0xFFFFu, yb16 = e.y << 16;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if (g < gn) {
+                        const MixO<R> M = mrowg[g * nn + jb];
+                        const R w = with_sign(M.w, jw_sign(sg[g] | yb16, M.j));
+                        const V2<R> y = srcg[(size_t)g * hs.Db + rk];
+                        seg[g].x += w * y.x;
+                        seg[g].y += w * y.y;
+                    }
                 }
-                accumulate<R>(acc[i], comp[i], (R)1, seg);
+            }
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (g < gn) {
+                    const ASgl a = asl[g0 + g];
+                    const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
+                    const int pa = pair_index(min(p, q), max(p, q));
+                    const int asel = q > p;
+                    // alpha-only pair group: same column (beta-spectator sum per column)
+                    R val = asing[g] + __ldg(H.bspec_a + ((size_t)pa * 2 + asel) * hs.Db + cix[i]);
+                    val = with_sign(val, jw_sign(a.s | (cb_str << 16), H.s1a[pa].j));
+                    accumulate<R>(acc[i], comp[i], val, srcg[(size_t)g * hs.Db + cix[i]]);
+                    accumulate<R>(acc[i], comp[i], (R)1, seg[g]);
+                }
             }
         }
     }
@@ -577,9 +633,7 @@ cudaError_t launch_lbfgs(cudaStream_t stream, int K, int m, double max_step, dou
 
 template <typename R>
 size_t happly_smem(const HSector &hs, int n_orb) {
-    const int nva = n_orb - hs.n_alpha;
-    const size_t nad = (size_t)(hs.n_alpha * (hs.n_alpha - 1) / 2) * (nva * (nva - 1) / 2);
-    return happly_adbl_offset<R>(hs.Db, n_orb) + sizeof(ADbl<R>) * nad;
+    return happly_layout<R>(hs.Db, n_orb, hs.n_alpha, hs.ag).total;
 }
 
 template <typename R>

@@ -69,6 +69,7 @@ struct HSector {
     // n_bs = n_beta * (n_orb - n_beta) per column.
     const uint2 *bsing = nullptr;
     int n_bs = 0;
+    int ag = 1;  // alpha singles staged per phase of the H-apply (1..4)
     int n_alpha = 0, n_beta = 0;
     int Da = 0, Db = 0;
     int colblock = 0, ncb = 1;
