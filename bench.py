@@ -201,6 +201,9 @@ def run_reference(args):
 # 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz; FP64 is GB300's 1.25 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
+# Shared-memory bandwidth of the sweeps' resident tiles, derived the same
+# way: 152 SMs x 32 banks x 4 bytes per clock at the 2.07 GHz maximum clock.
+SMEM_PEAK_GBS = 152 * 128 * 2.07e9 / 1e9
 
 KERNEL_SOURCES = {"happly": "kernels.cu", "forward": "sweep.cu", "adjoint": "sweep.cu"}
 
@@ -264,6 +267,20 @@ def roofline(prof, B, n, amp_bytes, ijab, n_groups, prec_fp32, workload, n_alpha
                      "frac": achieved / peak, "ms_per_step": ms, "launches_per_step": launches,
                      "algorithmic_per_launch": work / max(1.0, launches),
                      "avg_launch_ms": ms / max(1.0, launches)}
+        if fam in ("forward", "adjoint"):
+            # the rotations as the tiled sweep performs them: every active
+            # pair of the electron sector loaded and stored once per factor,
+            # one vector forward, phi and lambda in the adjoint, all in
+            # shared memory (the 2^n basis above counts HBM traffic that a
+            # resident tile never makes)
+            vecs = 1 if fam == "forward" else 2
+            sm = sector_pairs_per_state(n // 2, n_alpha, n_beta, ijab) * 4 * amp_bytes * vecs * B
+            fams[fam]["smem_basis"] = {
+                "achieved": sm / (ms / 1e3) / 1e9, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
+                "frac": sm / (ms / 1e3) / 1e9 / SMEM_PEAK_GBS,
+                "note": "shared-memory bytes of the sector's active pairs (2 loads + 2 stores "
+                        "per pair and vector); the sweep is bound by its per-factor latency "
+                        "chain (one barrier per factor, ncu profile)"}
         if fam == "happly":
             # the same updates counted on the electron sector only (the kernel
             # skips the structurally zero amplitudes the 2^n basis includes)
@@ -283,7 +300,23 @@ def roofline(prof, B, n, amp_bytes, ijab, n_groups, prec_fp32, workload, n_alpha
            "families": fams}
     if "sector_basis" in d:
         out["sector_basis"] = d["sector_basis"]
+    if "smem_basis" in d:
+        out["smem_basis"] = d["smem_basis"]
     return out
+
+
+def sector_pairs_per_state(n_orb, na, nb, ijab):
+    """Active pairs of the electron sector over the excitation list: for
+    each excitation the sector determinants with its occupied orbitals
+    filled and its virtual orbitals empty."""
+    from math import comb
+    pairs = 0
+    for row in np.asarray(ijab).reshape(-1, 4).tolist():
+        qs = [q for q in row if q >= 0]
+        ka = sum(1 for q in qs if q % 2 == 0) // 2
+        kb = sum(1 for q in qs if q % 2 == 1) // 2
+        pairs += comb(n_orb - 2 * ka, na - ka) * comb(n_orb - 2 * kb, nb - kb)
+    return pairs
 
 
 def sector_updates_per_state(n_orb, na, nb):
