@@ -57,6 +57,7 @@ def parse():
                          "beside the full one as a comparison)")
     ap.add_argument("--no-layout-compare", action="store_true")
     ap.add_argument("--no-scaleup", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=512)
@@ -433,6 +434,8 @@ def run_ours(args):
                                           "FP64 oracle, OpenMP)"}
     if rank == 0 and not args.no_layout_compare and args.layout == "full":
         line["sector_layout"] = layout_compare(uc, local, w, prec, B, th_host, args, flush)
+    if rank == 0 and not args.no_fp64_compare and prec == uc.FP32_STATE:
+        line["fp64_b1"] = fp64_compare(uc, local, w, th_host, E, G, args.layout)
     if rank == 0 and not args.no_scaleup:
         line["scaleup"] = scaleup_26q(uc, local)
     if rank == 0 and not args.no_serving:
@@ -475,6 +478,49 @@ def layout_compare(uc, device, w, prec, B, th_host, args, flush):
            "device_bytes": ctx.info()["device_bytes"]}
     ctx.close()
     return out
+
+
+def fp64_compare(uc, device, w, th_host, E32, G32, layout_name):
+    """The same 18q workload in the FP64 form, one state per call: its
+    evaluation rate, and the error of the batched FP32-state evaluations of
+    the timed loop against FP64 evaluations at the same 64 theta vectors (the
+    FP64 path itself matches the oracle to 1e-10 in the parity tests)."""
+    import torch
+    layout = uc.LAYOUT_SECTOR if layout_name == "sector" else uc.LAYOUT_FULL
+    ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
+                          precision=uc.FP64, device=device, batch=1, layout=layout)
+    K = ctx.K
+    th = torch.tensor(th_host, device="cuda", dtype=torch.float64)
+    E = torch.empty(1, device="cuda", dtype=torch.float64)
+    G = torch.empty(1, K, device="cuda", dtype=torch.float64)
+    E64, G64 = [], []
+    for b in range(th.shape[0]):
+        ctx.energy_grad_device(th[b:b + 1], E, G)
+        E64.append(float(E[0].item()))
+        G64.append(G[0].cpu().numpy().copy())
+    steps = 16
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for s_ in range(steps):
+        ctx.energy_grad_device(th[s_ % th.shape[0]:s_ % th.shape[0] + 1], E, G)
+    z.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / steps
+    e32 = E32.cpu().numpy()
+    g32 = G32.cpu().numpy()
+    del ctx
+    torch.cuda.empty_cache()
+    g64 = np.stack(G64)
+    return {"evals_per_s": 1e3 / ms, "ms_per_eval": ms, "batch": 1,
+            "fp32_state_vs_fp64": {
+                "max_abs_dE": float(np.max(np.abs(e32 - np.array(E64)))),
+                "max_abs_dgrad": float(np.max(np.abs(g32 - g64))),
+                # the FP32 arithmetic's bound: |dg_k| <= 1e-5 max(1, |g_k|)
+                "max_dgrad_over_max1_absg": float(np.max(np.abs(g32 - g64)
+                                                         / np.maximum(1.0, np.abs(g64)))),
+                "max_abs_g": float(np.max(np.abs(g64))),
+                "evals_compared": int(th.shape[0])}}
 
 
 def scaleup_26q(uc, device):
