@@ -591,11 +591,13 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
 // critical path is the barrier, two shared-memory loads per pair, the
 // rotation and the stores.
 // ---------------------------------------------------------------------------
-// Pairs per thread held in registers, loaded two factors ahead.
+// Pairs per thread held in registers, loaded two factors ahead (measured on
+// 18 qubits, batch 64, FP32: forward 8 against 3, 4 or 6; adjoint 2 against
+// 3 or 4).
 template <typename R>
 struct ListPre {
     static constexpr int kFwd = sizeof(R) == 4 ? 8 : 4;
-    static constexpr int kAdj = sizeof(R) == 4 ? 4 : 2;
+    static constexpr int kAdj = 2;
 };
 
 template <int KP>
