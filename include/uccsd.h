@@ -193,6 +193,20 @@ uccsd_status uccsd_energy_grad_batch(uccsd_ctx *ctx, int B, const double *theta,
                                      int theta_on_device, double *E, double *grad,
                                      void *stream);
 
+/* One call over B contexts, for example the monomer and dimer fragments of
+ * an FMO job (Eq. 1), each with its own Hamiltonian, reference and list:
+ * thetas[i] (K_i doubles), grads[i] (K_i doubles, or grads = NULL for
+ * energies only) and E (B doubles) are device pointers.  Each evaluation
+ * runs on its context's own stream, forked from `stream` and joined back
+ * into it, so the fragments overlap on the device; outputs are ready when
+ * `stream` reaches the point of the call (also inside a stream capture).
+ * A context may appear more than once (its evaluations run in order).
+ * Errors: UCCSD_ERR_ARG for a null pointer or contexts on different
+ * devices, UCCSD_ERR_STATE for a failed context or one without
+ * excitations; every context is checked before anything is enqueued. */
+uccsd_status uccsd_energy_grad_batched(uccsd_ctx *const *ctxs, int B, const double *const *thetas,
+                                       double *E, double *const *grads, void *stream);
+
 /* Capture one B-slot evaluation (as uccsd_energy_grad_batch with device
  * pointers: theta B*K, E B, grad B*K or NULL) into a CUDA graph owned by the
  * context, replacing any earlier capture.  The graph keeps the pointers:

@@ -37,6 +37,7 @@ EXPORTS = [
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
     "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
     "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
+    "uccsd_energy_grad_batched",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -106,6 +107,8 @@ def lib():
         L.uccsd_capture.argtypes = [vp, ip, dp, dp, dp, vp]
         L.uccsd_replay.argtypes = [vp, vp]
         L.uccsd_capture_vqe_step.argtypes = [vp, dp, dp, dp, vp]
+        vpp = ctypes.POINTER(vp)
+        L.uccsd_energy_grad_batched.argtypes = [vpp, ip, vpp, dp, vpp, vp]
         L.uccsd_set_profiling.argtypes = [vp, ip]
         L.uccsd_get_profile.argtypes = [vp, ctypes.POINTER(Profile)]
         L.uccsd_pauli_terms.argtypes = [ip, f64p, f64p, ctypes.c_double, u32p, u32p, f64p, ip,
@@ -430,6 +433,33 @@ class Context:
         inf = Info()
         self._check(self._L.uccsd_info(self._c, ctypes.byref(inf)), "info")
         return inf.as_dict()
+
+
+def energy_grad_batched(ctxs, thetas, E, grads=None, stream=None):
+    """One evaluation per context in a single call (uccsd_energy_grad_batched):
+    thetas a list of CUDA float64 tensors (K_i,), E a CUDA float64 tensor
+    (len(ctxs),), grads a list of CUDA float64 tensors (K_i,) or None.  The
+    contexts' evaluations overlap on the device; results are ordered on
+    `stream`."""
+    B = len(ctxs)
+    if len(thetas) != B or E.numel() < B or (grads is not None and len(grads) != B):
+        raise ValueError("one theta (and grad) per context, E of length len(ctxs)")
+    for t in list(thetas) + ([E] + list(grads) if grads is not None else [E]):
+        if not (t.is_cuda and t.dtype == torch_float64() and t.is_contiguous()):
+            raise ValueError("thetas, E and grads must be contiguous CUDA float64 tensors")
+    P = ctypes.c_void_p * max(B, 1)
+    cs = P(*[c._c.value for c in ctxs])
+    ts = P(*[t.data_ptr() for t in thetas])
+    gs = P(*[g.data_ptr() for g in grads]) if grads is not None else None
+    st = lib().uccsd_energy_grad_batched(cs, B, ts, E.data_ptr(), gs, _stream_ptr(stream))
+    if st:
+        msg = lib().uccsd_last_error(ctxs[0]._c).decode() if ctxs else ""
+        raise UCCSDError(st, f"energy_grad_batched: {msg}")
+
+
+def torch_float64():
+    import torch
+    return torch.float64
 
 
 def make_context(n_orb, h, eri, e_core, n_alpha, n_beta, ijab=None, precision=FP64, device=0,

@@ -1151,7 +1151,15 @@ uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec, size_t h
         delete c;
         return UCCSD_ERR_CUDA;
     }
-    if (cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->join_ev) cudaEventDestroy(c->join_ev);
+        if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+        if (c->aux) cudaStreamDestroy(c->aux);
+        if (c->stage_ev) cudaEventDestroy(c->stage_ev);
         cudaStreamDestroy(c->own_setup);
         delete c;
         return UCCSD_ERR_CUDA;
@@ -1171,6 +1179,9 @@ void uccsd_destroy(uccsd_ctx *c) {
     for (auto &kv : c->mem) cudaFree(kv.second.first);
     if (c->stage) cudaFreeHost(c->stage);
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+    if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->aux) cudaStreamDestroy(c->aux);
     if (c->own_setup) cudaStreamDestroy(c->own_setup);
     delete c;
 }
@@ -1440,6 +1451,37 @@ uccsd_status uccsd_energy_grad(uccsd_ctx *c, const double *theta, int on_dev, do
 uccsd_status uccsd_energy_grad_batch(uccsd_ctx *c, int B, const double *theta, int on_dev, double *E,
                                      double *grad, void *stream) {
     return eval(c, B, theta, on_dev, E, grad, stream);
+}
+
+uccsd_status uccsd_energy_grad_batched(uccsd_ctx *const *ctxs, int B, const double *const *thetas,
+                                       double *E, double *const *grads, void *stream) {
+    if (B < 0 || (B > 0 && (!ctxs || !thetas || !E))) return UCCSD_ERR_ARG;
+    if (B == 0) return UCCSD_OK;
+    // every context is checked before anything is enqueued
+    for (int i = 0; i < B; ++i) {
+        uccsd_ctx *c = ctxs[i];
+        if (!c) return UCCSD_ERR_ARG;
+        if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
+        if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "set_excitations must come first");
+        if (c->K > 0 && !thetas[i]) return fail(c, UCCSD_ERR_ARG, "null theta");
+        if (c->device != ctxs[0]->device)
+            return fail(c, UCCSD_ERR_ARG, "the contexts of one batched call share a device");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    uccsd_ctx *c0 = ctxs[0];
+    cudaError_t e = cudaSetDevice(c0->device);
+    if (e == cudaSuccess) e = cudaEventRecord(c0->fork_ev, s);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "fork event");
+    for (int i = 0; i < B; ++i) {
+        uccsd_ctx *c = ctxs[i];
+        if ((e = cudaStreamWaitEvent(c->aux, c0->fork_ev, 0)) != cudaSuccess)
+            return cuda_fail(c, e, "fork wait");
+        uccsd_status st = eval(c, 1, thetas[i], 1, E + i, grads ? grads[i] : nullptr, c->aux);
+        if (st) return st;
+        if ((e = cudaEventRecord(c->join_ev, c->aux)) != cudaSuccess) return cuda_fail(c, e, "join event");
+        if ((e = cudaStreamWaitEvent(s, c->join_ev, 0)) != cudaSuccess) return cuda_fail(c, e, "join wait");
+    }
+    return UCCSD_OK;
 }
 
 }  // extern "C"

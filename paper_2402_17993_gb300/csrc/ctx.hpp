@@ -37,6 +37,10 @@ struct uccsd_ctx {
     // caller orders later work after that stream.
     cudaStream_t setup = nullptr;
     cudaStream_t own_setup = nullptr;
+    // evaluation stream of uccsd_energy_grad_batched (forked from and joined
+    // back into the caller's stream) and its fork / join events
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool setup_async = false;
     char *stage = nullptr;  // pinned staging of asynchronous uploads
     size_t stage_cap = 0, stage_off = 0;

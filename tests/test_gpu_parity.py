@@ -244,3 +244,33 @@ def test_26q_matches_golden(uc, prec):
         # to FP32 in ~2 x 300 rotations, a relative error ~ sqrt(600) 2^-24 =
         # 1.5e-6 each, so dE/dtheta_k carries ~3e-6 |g_k|; bound 1e-5 max(1, |g_k|).
         assert np.all(np.abs(g - g0) <= TOL[1] * np.maximum(1.0, np.abs(g0)))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batched_over_contexts_equals_single_calls(uc, prec):
+    # one uccsd_energy_grad_batched call over fragments of different sizes
+    # (one of them twice) gives bitwise the energies and gradients of the
+    # single calls; energies-only form as well
+    import torch
+    ws = [synth.workload(n) for n in ("8q", "12q", "18q")]
+    ctxs = [ctx_for(uc, w, prec) for w in ws]
+    order = [0, 1, 2, 1]
+    thetas = [synth.theta_normal(ctxs[i].K, 0.05, 600 + j) for j, i in enumerate(order)]
+    single = []
+    for j, i in enumerate(order):
+        single.append(ctxs[i].energy_grad(thetas[j]))
+    th_d = [torch.tensor(t, device="cuda", dtype=torch.float64) for t in thetas]
+    E = torch.zeros(len(order), device="cuda", dtype=torch.float64)
+    G = [torch.zeros(ctxs[i].K, device="cuda", dtype=torch.float64) for i in order]
+    s = torch.cuda.Stream()
+    uc.energy_grad_batched([ctxs[i] for i in order], th_d, E, G, stream=s)
+    s.synchronize()
+    for j in range(len(order)):
+        assert E[j].item() == single[j][0], j
+        assert np.array_equal(G[j].cpu().numpy(), single[j][1]), j
+    E2 = torch.zeros(len(order), device="cuda", dtype=torch.float64)
+    uc.energy_grad_batched([ctxs[i] for i in order], th_d, E2, None, stream=s)
+    s.synchronize()
+    assert torch.equal(E, E2)
+    with pytest.raises(ValueError):
+        uc.energy_grad_batched(ctxs[:2], th_d[:1], E)
