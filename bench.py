@@ -40,6 +40,8 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "UCCSD energy+grad evals/s (18q dimer fragment, batch 64)"
+WORKLOAD = ("18q/10e UCCSD K=560 (seed 2, 16 Cholesky), batch 64 theta ~N(0,0.05), "
+            "energy+adjoint gradient, M=1 first-order Trotter")
 UNIT = "evals/s"
 L2_BYTES = 129 * 1024 * 1024
 
@@ -187,7 +189,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "18q/10e UCCSD K=560, batch 64 theta"},
+        "data": "synthetic", "config": {"workload": WORKLOAD},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -411,8 +413,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == uc.FP32_STATE else "f64", "data": "synthetic",
-        "config": {"workload": "18q/10e UCCSD K=560 (seed 2, 16 Cholesky), batch 64 theta "
-                               "~N(0,0.05), energy+adjoint gradient, M=1 first-order Trotter",
+        "config": {"workload": WORKLOAD,
                    "state": "complex64 + FP64 reductions" if prec else "complex128",
                    "layout": args.layout + (" (2^n vector per slot)" if args.layout == "full"
                                             else " (electron-sector array per slot)"),
