@@ -256,10 +256,11 @@ uccsd_status uccsd_get_profile(const uccsd_ctx *ctx, uccsd_profile_t *out);
 /* Energy of a state vector that the caller already holds on the device,
  * computed without allocating any device memory.  The paper has no
  * counterpart; it exists for callers that cannot call cudaMalloc when they
- * need an energy: code running while a stream is captured into a CUDA
- * graph (an allocation would invalidate the capture), serving or real-time
- * loops held to a memory budget reserved up front, and programs whose
- * device allocator belongs to another framework.
+ * need an energy: serving or real-time loops held to a memory budget
+ * reserved up front (an allocation there may fail, or stall the device
+ * while other work is in flight), and plugins inside programs whose device
+ * allocator belongs to another framework (memory taken behind that
+ * allocator's back is memory it cannot account for).
  *
  *   ctx    context with set_hamiltonian and set_reference done (its tables
  *          were uploaded then; set_excitations is not needed)

@@ -1,10 +1,11 @@
 // Energy of a caller-supplied state vector without any device allocation.
 //
 // Some callers cannot call cudaMalloc at the moment they need an energy:
-// code that runs while a CUDA stream is being captured into a graph (an
-// allocation would break the capture), real-time or serving loops that
-// run under a fixed, pre-reserved memory budget, and hosts whose allocator
-// is owned by another framework.  uccsd_expectation_noalloc serves them: it
+// real-time or serving loops that run under a fixed, pre-reserved memory
+// budget (an allocation there may fail, or stall the device while other
+// work is in flight), and plugins inside hosts whose device allocator is
+// owned by another framework (memory taken behind that allocator's back is
+// memory it cannot account for).  uccsd_expectation_noalloc serves them: it
 // reuses the Hamiltonian tables that the context uploaded when it was set
 // up, takes the state and the result buffer from the caller, and keeps its
 // only scratch (the per-tile energy partials) in the file-scope device

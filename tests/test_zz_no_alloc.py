@@ -1,9 +1,10 @@
 """The energy entry point that allocates no device memory.
 
 uccsd_expectation_noalloc serves callers that cannot call cudaMalloc when
-they need an energy: a stream being captured into a CUDA graph, a serving
-loop held to a memory budget reserved up front, or a program whose device
-allocator belongs to another framework.  It takes the state vector and the
+they need an energy: a serving loop held to a memory budget reserved up
+front, where an allocation may fail or stall the device, or a plugin in a
+program whose device allocator belongs to another framework and must not be
+bypassed.  It takes the state vector and the
 result buffer from the caller and keeps its per-tile partial sums in a fixed
 array inside the library.
 
