@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the 8- and 12-qubit workloads (sweep, VQE)")
     ap.add_argument("--serving-requests", type=int, default=512)
     ap.add_argument("--serving-fp64-requests", type=int, default=48)
     return ap.parse_args()
@@ -437,6 +439,8 @@ def run_ours(args):
         line["sector_layout"] = layout_compare(uc, local, w, prec, B, th_host, args, flush)
     if rank == 0 and not args.no_fp64_compare and prec == uc.FP32_STATE:
         line["fp64_b1"] = fp64_compare(uc, local, w, th_host, E, G, args.layout)
+    if rank == 0 and not args.no_small:
+        line["small"] = small_workloads(uc, local)
     if rank == 0 and not args.no_scaleup:
         line["scaleup"] = scaleup_26q(uc, local)
     if rank == 0 and not args.no_serving:
@@ -524,6 +528,74 @@ def fp64_compare(uc, device, w, th_host, E32, G32, layout_name):
                 "evals_compared": int(th.shape[0])}}
 
 
+def small_workloads(uc, device):
+    """The two small workloads, each in FP64 and in the FP32-state form.
+
+    8 qubits (4 electrons, seed 0): one energy + gradient at theta0 ~
+    U(-0.1, 0.1) and the 16-point sweep theta0 + phi_s e_k along the first
+    double (phi_s = -pi + 2 pi s / 16), against the oracle's stored values;
+    along one amplitude the energy is a trigonometric polynomial of degree
+    2, so the sweep's DFT content above frequency 2 measures rounding only.
+
+    12 qubits (6 electrons, seed 1): VQE by L-BFGS-B with the adjoint
+    gradient from theta = 0 to a gradient 2-norm below 1e-6 (FP64; the
+    FP32-state run stops at 1e-3, the resolution of its gradient), with the
+    iterations, evaluations, rate and final energy against the stored FCI
+    energy, and the FP32-state energy at the FP64 optimum."""
+    import time as _t
+
+    from paper_2402_17993_gb300 import vqe
+    gdir = os.path.join(ROOT, "tests", "golden")
+    out = {}
+    g8 = json.load(open(os.path.join(gdir, "golden_8q.json")))
+    w = synth.workload("8q")
+    K8 = len(uc.build_uccsd_list(w["n_orb"], w["n_alpha"], w["n_beta"]))
+    th0 = synth.theta_uniform(K8, -0.1, 0.1, 1000)
+    k = g8["sweep_k"]
+    sweep = np.tile(th0, (16, 1))
+    sweep[:, k] += -np.pi + 2 * np.pi * np.arange(16) / 16
+    for name, prec in (("fp64", uc.FP64), ("fp32_state", uc.FP32_STATE)):
+        ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
+                              precision=prec, device=device)
+        ctx.energy_grad(np.zeros(ctx.K))  # first launches load the kernels: not timed
+        E, g = ctx.energy_grad(th0)
+        Es = np.array([ctx.energy(t) for t in sweep])
+        t0 = _t.perf_counter()
+        for t in sweep:
+            ctx.energy_grad(t)
+        dt = (_t.perf_counter() - t0) / 16
+        F = np.abs(np.fft.rfft(Es)) / 16
+        out[f"8q_{name}"] = {
+            "abs_dE_vs_oracle": abs(E - g8["E"]),
+            "max_abs_dgrad_vs_oracle": float(np.max(np.abs(g - np.array(g8["grad"])))),
+            "sweep_max_abs_dE_vs_oracle": float(np.max(np.abs(Es - np.array(g8["sweep_E"])))),
+            "sweep_dft_above_2": float(np.max(F[3:])),
+            "ms_per_eval_host_call": 1e3 * dt}
+        ctx.close()
+    g12 = json.load(open(os.path.join(gdir, "golden_12q.json")))
+    w = synth.workload("12q")
+    res = {}
+    for name, prec, gtol in (("fp64", uc.FP64, 1e-6), ("fp32_state", uc.FP32_STATE, 1e-3)):
+        ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
+                              precision=prec, device=device)
+        ctx.energy_grad(np.zeros(ctx.K))  # first launches load the kernels: not timed
+        t0 = _t.perf_counter()
+        E, theta, n_eval, gnorm = vqe.minimize(ctx, gtol=gtol)
+        dt = _t.perf_counter() - t0
+        res[name] = (ctx, theta, E)
+        out[f"12q_vqe_{name}"] = {
+            "gtol": gtol, "evals": n_eval, "grad_norm": gnorm, "E": E,
+            "E_minus_fci": E - g12["E_fci"], "E_hf": g12["E_hf"], "E_fci": g12["E_fci"],
+            "evals_per_s_host_loop": n_eval / dt, "seconds": dt}
+    ctx64, th64, E64 = res["fp64"]
+    ctx32 = res["fp32_state"][0]
+    out["12q_vqe_fp32_state"]["abs_dE_at_fp64_optimum"] = abs(ctx32.energy(th64) - E64)
+    out["12q_vqe_fp32_state"]["abs_dE_converged_vs_fp64"] = abs(res["fp32_state"][2] - E64)
+    ctx64.close()
+    ctx32.close()
+    return out
+
+
 def scaleup_26q(uc, device):
     import torch
     w = synth.workload("26q")
@@ -569,7 +641,7 @@ def scaleup_26q(uc, device):
 def serving_stream(uc, device, n_req, n_req_fp64):
     """FMO fragment stream (60% monomers at 8-12 qubits, 40% dimers at 16-18
     qubits, 40 fixed-step L-BFGS evaluations per solve): capacity of the
-    batched FP32 server (closed loop), latency percentiles at 0.8x that
+    batched FP32 server (closed loop), latency percentiles at 0.5x, 0.8x and 1.2x that
     capacity with Poisson arrivals (seed 7), and the one-request-at-a-time
     FP64 form on the first requests of the same stream."""
     from paper_2402_17993_gb300.serving import FragmentServer, Request, capacity_rate
@@ -581,9 +653,11 @@ def serving_stream(uc, device, n_req, n_req_fp64):
     srv.run(reqs[:64])  # warm the context pool and graph paths
     _, cap = srv.run(reqs)
     rate = capacity_rate(cap)
-    _, op = srv.run(reqs, rate=0.8 * rate)
+    out["batched_fp32"] = {"closed_loop": cap}
+    for f in (0.5, 0.8, 1.2):
+        _, op = srv.run(reqs, rate=f * rate)
+        out["batched_fp32"][f"open_loop_{f}x"] = dict(op, rate_req_per_s=f * rate)
     srv.close()
-    out["batched_fp32"] = {"closed_loop": cap, "open_loop_0.8x": dict(op, rate_req_per_s=0.8 * rate)}
     one = FragmentServer(precision=uc.FP64, device=device, max_active=1, n_streams=1,
                          use_graphs=False)
     _, st1 = one.run(reqs[:n_req_fp64])

@@ -5,7 +5,7 @@ records the workload, the theta recipe and the oracle's FP64 energy and
 adjoint gradient of the first-order (M = 1) Trotterised UCCSD ansatz
 (Eq. 5, energy of Section 2.3).
 
-    python tests/golden/make_golden.py [8q] [18q] [26q]
+    python tests/golden/make_golden.py [8q] [12q] [18q] [26q]
 """
 from __future__ import annotations
 
@@ -49,6 +49,19 @@ def golden_8q():
         sweep_k=k, E=E0, grad=g0.tolist(), sweep_E=sweep))
 
 
+def golden_12q():
+    """Reference energies of the 12-qubit VQE workload: the Hartree-Fock
+    determinant (theta = 0) and the exact sector ground state (FCI by
+    dense diagonalisation), the lower bound of every UCCSD energy."""
+    w = synth.workload("12q")
+    ex = oracle.excitations(6, 3, 3)
+    E_hf = oracle.energy_grad(6, w["h"], w["eri"], 0.0, 3, 3, ex, np.zeros(len(ex)), grad=False)[0]
+    E_fci = oracle.fci_energy(6, w["h"], w["eri"], 0.0, 3, 3)
+    _dump("golden_12q.json", dict(
+        workload="12 qubits, 6 electrons, 6 spatial orbitals, integrals seed 1, 10 Cholesky vectors",
+        K=len(ex), E_hf=E_hf, E_fci=E_fci))
+
+
 def golden_18q(n_theta=4):
     w = synth.workload("18q")
     ex = oracle.excitations(9, 5, 5)
@@ -76,8 +89,8 @@ def golden_26q():
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["8q", "18q", "26q"]
+    which = sys.argv[1:] or ["8q", "12q", "18q", "26q"]
     for name in which:
         t = time.time()
-        {"8q": golden_8q, "18q": golden_18q, "26q": golden_26q}[name]()
+        {"8q": golden_8q, "12q": golden_12q, "18q": golden_18q, "26q": golden_26q}[name]()
         print(name, "done in", round(time.time() - t, 1), "s", flush=True)
