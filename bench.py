@@ -49,7 +49,7 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=64)
@@ -99,6 +99,81 @@ def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
+class NvmlClocks:
+    """SM clock, its maximum and the clock-event reasons of one GPU, read
+    through NVML (libnvidia-ml, read-only queries) every 10 ms by a host
+    thread while the timed region runs, so even a short region gets many
+    samples.  The GPU is found by its PCI bus id (as CUDA numbers it)."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, device):
+        import ctypes
+        import threading
+        self._ct = ctypes
+        self.nv = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.nv.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        bus = None
+        try:
+            import torch
+            pr = torch.cuda.get_device_properties(device)
+            bus = "%08x:%02x:%02x.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+        except Exception:
+            bus = None
+        ok = bus is not None and self.nv.nvmlDeviceGetHandleByPciBusId_v2(
+            bus.encode(), ctypes.byref(self.h)) == 0
+        if not ok and self.nv.nvmlDeviceGetHandleByIndex_v2(device, ctypes.byref(self.h)) != 0:
+            raise RuntimeError("no NVML handle")
+        try:
+            self._reasons_fn = self.nv.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self._reasons_fn = self.nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.samples = []
+        self.reasons = 0
+        self.stop_ev = threading.Event()
+        self.th = threading.Thread(target=self._run, daemon=True)
+
+    def _read(self):
+        ct = self._ct
+        mhz = ct.c_uint()
+        rs = ct.c_ulonglong()
+        if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(mhz)) == 0:  # NVML_CLOCK_SM
+            self.samples.append(mhz.value)
+        if self._reasons_fn(self.h, ct.byref(rs)) == 0:
+            self.reasons |= rs.value
+
+    def _run(self):
+        while not self.stop_ev.is_set():
+            self._read()
+            self.stop_ev.wait(0.01)
+
+    def start(self):
+        self.th.start()
+
+    def stop(self):
+        self.stop_ev.set()
+        self.th.join()
+        self._read()
+        mx = self._ct.c_uint()
+        smax = (float(mx.value) if self.nv.nvmlDeviceGetMaxClockInfo(self.h, 1, self._ct.byref(mx)) == 0
+                else None)
+        self.nv.nvmlShutdown()
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": smax,
+                "reasons": sorted(v for b, v in self.REASONS.items() if self.reasons & b),
+                "samples": len(self.samples), "source": "NVML every 10 ms"}
+
+
+def clock_sampler(device):
+    """NVML sampler where libnvidia-ml loads, else nvidia-smi every 200 ms."""
+    try:
+        return NvmlClocks(device)
+    except Exception:
+        return Clocks(device)
+
+
 class Clocks:
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -144,7 +219,7 @@ class Clocks:
                     reasons.add(nm)
         os.unlink(self.path)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi every 200 ms"}
 
 
 def peaks():
@@ -371,7 +446,7 @@ def run_ours(args):
     barrier()
     ctx.set_profiling(True)
     launches0 = ctx.info()["launches"]
-    clocks = Clocks(local)
+    clocks = clock_sampler(local)
     clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
