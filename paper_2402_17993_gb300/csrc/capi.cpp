@@ -786,7 +786,8 @@ uccsd_status device_lists(uccsd_ctx *c, ListEntry &ent, std::shared_ptr<DeviceLi
         auto d = std::make_shared<DeviceLists>();
         d->device = c->device;
         const size_t b1 = sizeof(int32_t) * std::max<size_t>(L.op_pl.size(), 1);
-        const size_t b2 = sizeof(uint32_t) * std::max<size_t>(L.pairs.size(), 1);
+        // 16 bytes of padding: L2 prefetches round list ranges out to 16-byte boundaries
+        const size_t b2 = sizeof(uint32_t) * std::max<size_t>(L.pairs.size(), 1) + 16;
         cudaError_t e = cudaMalloc(&d->op_pl, b1);
         if (e == cudaSuccess) e = cudaMalloc(&d->pairs, b2);
         if (e != cudaSuccess) {

@@ -610,12 +610,28 @@ __device__ __forceinline__ void fetch_pairs(uint2 (&dst)[KP], const uint2 *__res
     }
 }
 
+// Bring one factor's pair list into L2 ahead of use: one bulk prefetch
+// (cp.async.bulk.prefetch.L2) by one thread, kListAhead factors before the
+// list is read, so the register prefetch two factors ahead finds it in L2
+// even when the lists were evicted since the last evaluation (they come
+// from DRAM otherwise).  The range is widened to 16-byte boundaries, which
+// the 16 bytes of padding after the device copy of the lists cover.
+constexpr int kListAhead = 6;
+__device__ __forceinline__ void prefetch_list_l2(const uint2 *pairs, int2 pl) {
+    if (pl.y <= 0) return;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(pairs + pl.x) & ~uintptr_t(15);
+    const uintptr_t e = (reinterpret_cast<uintptr_t>(pairs + pl.x + pl.y) + 15) & ~uintptr_t(15);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a), "r"((uint32_t)(e - a))
+                 : "memory");
+}
+
 template <typename R, int THREADS, int KP>
 __device__ __forceinline__ void forward_list_step(int o, int nops, V2<R> *tile, const COpDev *sops,
                                                   const V2<R> *scs, const int2 *spl,
                                                   const uint2 *__restrict__ pairs, uint32_t rest,
                                                   uint2 (&cur)[KP], uint2 (&nxt)[KP]) {
     const int t = threadIdx.x;
+    if (t == 0 && o + kListAhead < nops) prefetch_list_l2(pairs, spl[o + kListAhead]);
     if (o + 2 < nops) fetch_pairs<KP>(nxt, pairs, spl[o + 2], t, THREADS);
     const int2 pl = spl[o];
     const COpDev &op = sops[o];
@@ -693,6 +709,7 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
         }
         tile[e] = val;
     }
+    if (threadIdx.x < kListAhead && (int)threadIdx.x < nops) prefetch_list_l2(sa.pairs, spl[threadIdx.x]);
     uint2 p0[KP], p1[KP], p2[KP];
     if (nops > 0) fetch_pairs<KP>(p0, sa.pairs, spl[0], threadIdx.x, THREADS);
     if (nops > 1) fetch_pairs<KP>(p1, sa.pairs, spl[1], threadIdx.x, THREADS);
@@ -718,6 +735,7 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
                                                   uint32_t rest, uint2 (&cur)[KP], uint2 (&nxt)[KP],
                                                   double *__restrict__ gp, int tile_stride) {
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    if (t == 0 && o - kListAhead >= 0) prefetch_list_l2(pairs, spl[o - kListAhead]);
     if (o - 2 >= 0) fetch_pairs<KP>(nxt, pairs, spl[o - 2], t, THREADS);
     const int2 pl = spl[o];
     const COpDev &op = sops[o];
@@ -819,6 +837,8 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     }
     // gradient partials of this slot and tile: gp[op_index * tile_stride + warp]
     double *gp = gpart + (size_t)b * n_ops * tile_stride + (size_t)blockIdx.x * W;
+    if (threadIdx.x < kListAhead && (int)threadIdx.x < nops)
+        prefetch_list_l2(sa.pairs, spl[nops - 1 - threadIdx.x]);
     uint2 p0[KP], p1[KP], p2[KP];
     if (nops > 0) fetch_pairs<KP>(p0, sa.pairs, spl[nops - 1], threadIdx.x, THREADS);
     if (nops > 1) fetch_pairs<KP>(p1, sa.pairs, spl[nops - 2], threadIdx.x, THREADS);
