@@ -224,7 +224,8 @@ uccsd_status uccsd_replay(uccsd_ctx *ctx, void *stream);
 /* Copy the state vector of slot `slot` after the last uccsd_energy or
  * energies-only batch call to host memory as 2*2^n interleaved (re, im)
  * doubles.  len must be >= 2*2^n.  Synchronises the context's last stream.
- * After a gradient call the slot holds the swept-back state instead. */
+ * After a gradient call the slot's content is unspecified (the adjoint
+ * sweep may leave it partly swept back). */
 uccsd_status uccsd_get_state(uccsd_ctx *ctx, int slot, double *out_re_im, size_t len);
 
 /* Sizes and counters of the context. */

@@ -487,9 +487,11 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
     }
     const uint32_t hfa = uint32_t((1u << c->n_alpha) - 1u), hfb = uint32_t((1u << c->n_beta) - 1u);
     c->hf_addr = c->hf;
-    if (c->layout) {
-        // rank of a string among the n_orb-bit strings of its popcount, in
-        // ascending order (the order of astr / bstr)
+    {
+        // sector addressing: rank of a string among the n_orb-bit strings of
+        // its popcount, in ascending order (the order of astr / bstr).  The
+        // sector layout stores states this way; the full layout uses it for
+        // the adjoint's hand-over between runs.
         std::vector<uint32_t> off(size_t(2) << no, 0u);
         std::vector<int> cnt(no + 2, 0);
         for (uint32_t sv = 0; sv < (1u << no); ++sv) {
@@ -501,9 +503,13 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
         uint32_t *p4;
         uccsd_status st = upload(c, "hoff", off, &p4);
         if (st) return st;
-        c->hsec.aoff = p4;
-        c->hsec.boff = p4 + (size_t(1) << no);
-        c->hf_addr = off[hfa] + off[(size_t(1) << no) + hfb];
+        c->sec_aoff = p4;
+        c->sec_boff = p4 + (size_t(1) << no);
+        if (c->layout) {
+            c->hsec.aoff = c->sec_aoff;
+            c->hsec.boff = c->sec_boff;
+            c->hf_addr = off[hfa] + off[(size_t(1) << no) + hfb];
+        }
     }
     return UCCSD_OK;
 }
@@ -532,6 +538,16 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     cudaError_t e = cudaMemsetAsync(p, 0, B * state_elems(c) * amp_bytes(c), c->setup);
     if (e == cudaSuccess) e = setup_sync(c);
     if (e != cudaSuccess) return cuda_fail(c, e, "memset");
+    // Full layout, adjoint of several runs: each run hands phi and lambda to
+    // the next in the compact sector order instead of scattering them into
+    // the 2^n vectors and gathering them back (every run writes all sector
+    // entries of its tiles before the next one reads them, so no clearing).
+    c->adj_compact = !c->layout && c->adj.runs.size() > 1;
+    if (c->adj_compact) {
+        const size_t D = size_t(c->hsec.Da) * size_t(c->hsec.Db);
+        if ((st = dalloc(c, "phic", B * D * amp_bytes(c), &p))) return st;
+        if ((st = dalloc(c, "lamc", B * D * amp_bytes(c), &p))) return st;
+    }
     if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
     if ((st = dalloc(c, "E", B * sizeof(double), &p))) return st;
@@ -657,9 +673,41 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     if (grad) {
         const COpDev *aops = static_cast<const COpDev *>(dptr(c, "adj_ops"));
         mk.begin(UCCSD_K_ADJOINT);
-        for (int r = int(c->adj.runs.size()) - 1; r >= 0; --r) {
-            if ((e = launch_adjoint_sweep<R>(cfg, psi, sig, c->adj.runs[r], aops, cs, c->adj_args,
-                                             gpart, n_tiles_a(c))) != cudaSuccess)
+        // the last run (first in the schedule) leaves phi and lambda nowhere:
+        // nothing reads them after the gradient
+        const int R_ = int(c->adj.runs.size());
+        const size_t Dsec = size_t(c->hsec.Da) * size_t(c->hsec.Db);
+        void *phic = c->adj_compact ? dptr(c, "phic") : nullptr;
+        void *lamc = c->adj_compact ? dptr(c, "lamc") : nullptr;
+        for (int r = R_ - 1; r >= 0; --r) {
+            LaunchCfg acfg = cfg;
+            SweepArgs in = c->adj_args;
+            void *phi_in = psi, *lam_in = sig;
+            if (c->adj_compact && r != R_ - 1) {  // read what the previous run handed over
+                phi_in = phic;
+                lam_in = lamc;
+                acfg.N = Dsec;
+                in.aoff = c->sec_aoff;
+                in.boff = c->sec_boff;
+            }
+            SweepOut out;
+            if (r > 0) {
+                if (c->adj_compact) {
+                    out.phi = phic;
+                    out.lam = lamc;
+                    out.N = Dsec;
+                    out.aoff = c->sec_aoff;
+                    out.boff = c->sec_boff;
+                } else {  // in place
+                    out.phi = phi_in;
+                    out.lam = lam_in;
+                    out.N = acfg.N;
+                    out.aoff = in.aoff;
+                    out.boff = in.boff;
+                }
+            }
+            if ((e = launch_adjoint_sweep<R>(acfg, phi_in, lam_in, c->adj.runs[r], aops, cs, in,
+                                             gpart, n_tiles_a(c), out)) != cudaSuccess)
                 return cuda_fail(c, e, "adjoint kernel");
             ++c->launches;
             c->prof.launches[UCCSD_K_ADJOINT]++;

@@ -109,10 +109,21 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
                                  int init_hf, uint32_t hf);
 
+// Where an adjoint run leaves phi and lambda after its factors: slot b of
+// each at phi + b * N (same for lam), amplitude of determinant (alpha string
+// sa, beta string sb) at aoff[sa] + boff[sb].  phi == nullptr: nowhere (the
+// last run of a sweep; nothing reads the vectors afterwards).
+struct SweepOut {
+    void *phi = nullptr, *lam = nullptr;
+    size_t N = 0;
+    const uint32_t *aoff = nullptr, *boff = nullptr;
+};
+
+// phi, lam, cfg.N and sa.aoff / sa.boff address the vectors the run reads.
 template <typename R>
 cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, const CRunDev &run,
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
-                                 double *gpart, int tile_stride);
+                                 double *gpart, int tile_stride, const SweepOut &out);
 
 // |HF> in every slot (used when the schedule is empty).
 template <typename R>

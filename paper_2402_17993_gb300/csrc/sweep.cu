@@ -108,11 +108,32 @@ __device__ __forceinline__ bool make_view(const CRunDev &run, const SweepArgs &s
     return true;
 }
 
-// Address of tile entry e in a slot of the state.
-__device__ __forceinline__ uint32_t entry_index(const TileView &v, int e) {
+// Address of tile entry e in a slot addressed by the tables aoff / boff.
+__device__ __forceinline__ uint32_t entry_index_at(const TileView &v, int e, const uint32_t *aoff,
+                                                   const uint32_t *boff) {
     const int ia = e / v.Db;
     const int ib = e - ia * v.Db;
-    return v.aoff[v.restA | v.spa[v.ca[ia]]] + v.boff[v.restB | v.spb[v.cb[ib]]];
+    return aoff[v.restA | v.spa[v.ca[ia]]] + boff[v.restB | v.spb[v.cb[ib]]];
+}
+
+// Address of tile entry e in a slot of the state.
+__device__ __forceinline__ uint32_t entry_index(const TileView &v, int e) {
+    return entry_index_at(v, e, v.aoff, v.boff);
+}
+
+// Write an adjoint tile's phi and lambda entries to where the next run reads
+// them (nothing after the last run).
+template <typename R, int THREADS>
+__device__ __forceinline__ void store_adjoint_tile(const TileView &v, int D, const V2<R> *tp,
+                                                   const V2<R> *tl, const SweepOut &out) {
+    if (!out.phi) return;
+    V2<R> *op = static_cast<V2<R> *>(out.phi) + (size_t)blockIdx.y * out.N;
+    V2<R> *ol = static_cast<V2<R> *>(out.lam) + (size_t)blockIdx.y * out.N;
+    for (int e = threadIdx.x; e < D; e += THREADS) {
+        const uint32_t x = entry_index_at(v, e, out.aoff, out.boff);
+        op[x] = tp[e];
+        ol[x] = tl[e];
+    }
 }
 
 // Pairs of factor `op` inside the tile: occupied-side strings have the op's
@@ -457,7 +478,7 @@ template <typename R, int THREADS>
 __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
-    double *__restrict__ gpart, int tile_stride) {
+    double *__restrict__ gpart, int tile_stride, SweepOut out) {
     using RL = Roles<THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ OpHdr<R> hdr[2];
@@ -577,11 +598,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
         __syncthreads();
     }
     if (builder && bl < 32 && nops > 0) flush_partial(it - 1, 0);
-    for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index(v, e);
-        sp[x] = tp[e];
-        sl[x] = tl[e];
-    }
+    store_adjoint_tile<R, THREADS>(v, D, tp, tl, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -798,7 +815,7 @@ template <typename R, int THREADS>
 __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
-    double *__restrict__ gpart, int tile_stride) {
+    double *__restrict__ gpart, int tile_stride, SweepOut out) {
     constexpr int KP = ListPre<R>::kAdj;
     constexpr int W = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -854,11 +871,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
             adjoint_list_step<R, THREADS, KP>(o - 2, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
                                               p2, p1, gp, tile_stride);
     }
-    for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index(v, e);
-        sp[x] = tp[e];
-        sl[x] = tl[e];
-    }
+    store_adjoint_tile<R, THREADS>(v, D, tp, tl, out);
 }
 
 // Trotter-free ansatz (Eq. 3): w = scale * sum_k coef_k G_k u over the
@@ -1121,7 +1134,7 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
 template <typename R>
 cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, const CRunDev &run,
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
-                                 double *gpart, int tile_stride) {
+                                 double *gpart, int tile_stride, const SweepOut &out) {
     dim3 grid(run.n_tiles, cfg.B);
     const size_t smem = sweep_smem_bytes(run.max_entries, run.max_da, run.max_db, sizeof(V2<R>), 2,
                                          run.op_end - run.op_begin, max(run.La, run.Lb));
@@ -1131,18 +1144,18 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
     if (run.pl_base >= 0 && sa.pairs) {
         if (run.max_entries >= kLargeTile)
             adjoint_list_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
         else
             adjoint_list_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
         return cudaGetLastError();
     }
     if (run.max_entries >= kLargeTile)
         adjoint_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
     else
         adjoint_sweep_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride);
+            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
     return cudaGetLastError();
 }
 
@@ -1271,7 +1284,8 @@ cudaError_t configure_sweep_kernels(size_t max_smem) {
                                                  const SweepArgs &, int, uint32_t);            \
     template cudaError_t launch_adjoint_sweep<R>(const LaunchCfg &, void *, void *,            \
                                                  const CRunDev &, const COpDev *, const void *, \
-                                                 const SweepArgs &, double *, int);            \
+                                                 const SweepArgs &, double *, int,             \
+                                                 const SweepOut &);                            \
     template cudaError_t launch_set_hf<R>(const LaunchCfg &, void *, uint32_t);                \
     template cudaError_t launch_gen_apply<R>(const LaunchCfg &, const void *, void *,          \
                                              const CRunDev &, const COpDev *, const double *,   \

@@ -97,7 +97,8 @@ def footprint_bytes(n_orb: int, n_alpha: int, n_beta: int, precision: int,
     K = len(build_uccsd_list(n_orb, n_alpha, n_beta))
     tiles = max(1, N >> 10)
     tables = 200 * (n_orb ** 4) + (4 << 20)
-    own = 2 * N * A + K * tiles * 8 + K * 256 + tables
+    sector = math.comb(n_orb, n_alpha) * math.comb(n_orb, n_beta)  # adjoint hand-over vectors
+    own = 2 * N * A + 2 * sector * A + K * tiles * 8 + K * 256 + tables
     return own + (list_bytes(n_orb, n_alpha, n_beta) if lists else 0)
 
 
