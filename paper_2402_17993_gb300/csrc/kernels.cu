@@ -460,6 +460,26 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     }
 }
 
+// Energy of slot b from the H-apply's tile partials, summed by the first
+// warp in a fixed order (the same in every reduction kernel, so energy-only
+// and energy+gradient calls agree bitwise); the norm goes to *s_nrm.
+__device__ __forceinline__ void energy_sums(const double *__restrict__ Epart, int n_tiles_h, int b,
+                                            double shift, int rayleigh, double *__restrict__ E,
+                                            double *s_nrm) {
+    if (threadIdx.x >= 32) return;
+    double e = 0.0, nr = 0.0;
+    for (int t = threadIdx.x; t < n_tiles_h; t += 32) {
+        e += Epart[2 * ((size_t)b * n_tiles_h + t)];
+        nr += Epart[2 * ((size_t)b * n_tiles_h + t) + 1];
+    }
+    e = warp_sum(e);
+    nr = warp_sum(nr);
+    if (threadIdx.x == 0) {
+        *s_nrm = nr;
+        if (blockIdx.x == 0) E[b] = rayleigh ? shift + e / nr : shift * nr + e;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Final deterministic reductions: E[b] = sum over H tiles; grad[b][k] =
 // sum over the schedule factors o of k of 2 * scale_o * sum over tiles.
@@ -476,20 +496,9 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
                                                           double shift, int rayleigh,
                                                           double *__restrict__ E,
                                                           double *__restrict__ grad) {
-    __shared__ double red[32];
     __shared__ double s_nrm;
     const int b = blockIdx.y;
-    double e = 0.0, nr = 0.0;
-    for (int t = threadIdx.x; t < n_tiles_h; t += blockDim.x) {
-        e += Epart[2 * ((size_t)b * n_tiles_h + t)];
-        nr += Epart[2 * ((size_t)b * n_tiles_h + t) + 1];
-    }
-    e = block_sum(e, red);
-    nr = block_sum(nr, red);
-    if (threadIdx.x == 0) {
-        s_nrm = nr;
-        if (blockIdx.x == 0) E[b] = rayleigh ? shift + e / nr : shift * nr + e;
-    }
+    energy_sums(Epart, n_tiles_h, b, shift, rayleigh, E, &s_nrm);
     __syncthreads();
     if (!grad) return;
     const double gscale = rayleigh ? 1.0 / s_nrm : 1.0;
@@ -508,6 +517,38 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
         }
         if (lane == 0) grad[(size_t)b * K + k] = gk * gscale;
     }
+}
+
+// The same reductions with one thread per gradient component, for plans
+// whose factors have few partial slots (the pair-list adjoint writes one per
+// tile and warp: 32 at 18 qubits).  GB300's FP64 rate is low, so the energy
+// and norm are summed by one warp per block instead of a block-wide tree in
+// every block, and each component's partials by one thread in slot order.
+constexpr int kReduceSerialMax = 64;
+
+__global__ void __launch_bounds__(kThreads) reduce_serial_kernel(
+    const double *__restrict__ Epart, int n_tiles_h, const double *__restrict__ gpart,
+    int tile_stride, const int32_t *__restrict__ op_tiles, int n_ops, int K,
+    const int32_t *__restrict__ k_ptr, const int32_t *__restrict__ k_ops,
+    const double *__restrict__ op_scale, double shift, int rayleigh, double *__restrict__ E,
+    double *__restrict__ grad) {
+    __shared__ double s_nrm;
+    const int b = blockIdx.y;
+    energy_sums(Epart, n_tiles_h, b, shift, rayleigh, E, &s_nrm);
+    __syncthreads();
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const double gscale = rayleigh ? 1.0 / s_nrm : 1.0;
+    double gk = 0.0;
+    for (int u = k_ptr[k]; u < k_ptr[k + 1]; ++u) {
+        const int o = k_ops[u];
+        const double *p = gpart + ((size_t)b * n_ops + o) * tile_stride;
+        const int nt = op_tiles[o];
+        double s = 0.0;
+        for (int t = 0; t < nt; ++t) s += p[t];
+        gk += 2.0 * op_scale[o] * s;
+    }
+    grad[(size_t)b * K + k] = gk * gscale;
 }
 
 }  // namespace
@@ -670,6 +711,13 @@ cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles
                           int K, const int32_t *k_ptr,
                           const int32_t *k_ops, const double *op_scale, double shift,
                           int rayleigh, double *E, double *grad) {
+    if (grad && tile_stride <= kReduceSerialMax) {
+        dim3 grid(std::max(1, (K + kThreads - 1) / kThreads), cfg.B);
+        reduce_serial_kernel<<<grid, kThreads, 0, cfg.stream>>>(Epart, n_tiles_h, gpart, tile_stride,
+                                                                op_tiles, cfg.n_ops, K, k_ptr, k_ops,
+                                                                op_scale, shift, rayleigh, E, grad);
+        return cudaGetLastError();
+    }
     int gx = grad ? std::max(1, std::min(64, (K + 7) / 8)) : 1;
     dim3 grid(gx, cfg.B);
     reduce_kernel<<<grid, kThreads, 0, cfg.stream>>>(Epart, n_tiles_h, gpart, tile_stride, op_tiles,
