@@ -542,11 +542,14 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     // the next in the compact sector order instead of scattering them into
     // the 2^n vectors and gathering them back (every run writes all sector
     // entries of its tiles before the next one reads them, so no clearing).
+    // The forward's runs hand the state on the same way (the forward is done
+    // before the adjoint starts, so the two share the first array).
     c->adj_compact = !c->layout && c->adj.runs.size() > 1;
-    if (c->adj_compact) {
+    c->fwd_compact = !c->layout && c->fwd.runs.size() > 1;
+    if (c->adj_compact || c->fwd_compact) {
         const size_t D = size_t(c->hsec.Da) * size_t(c->hsec.Db);
         if ((st = dalloc(c, "phic", B * D * amp_bytes(c), &p))) return st;
-        if ((st = dalloc(c, "lamc", B * D * amp_bytes(c), &p))) return st;
+        if (c->adj_compact && (st = dalloc(c, "lamc", B * D * amp_bytes(c), &p))) return st;
     }
     if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
@@ -651,9 +654,35 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     }
     const COpDev *fops = static_cast<const COpDev *>(dptr(c, "fwd_ops"));
     mk.begin(UCCSD_K_FORWARD);
-    for (size_t r = 0; r < c->fwd.runs.size(); ++r) {
-        if ((e = launch_forward_sweep<R>(cfg, psi, c->fwd.runs[r], fops, cs, c->fwd_args,
-                                         r == 0 ? 1 : 0, c->hf_addr)) != cudaSuccess)
+    const size_t Dsec = size_t(c->hsec.Da) * size_t(c->hsec.Db);
+    void *phic = (c->fwd_compact || c->adj_compact) ? dptr(c, "phic") : nullptr;
+    const int Rf = int(c->fwd.runs.size());
+    for (int r = 0; r < Rf; ++r) {
+        // full layout, several runs: the runs hand the state to each other in
+        // the compact sector order; the last one writes psi
+        LaunchCfg fcfg = cfg;
+        SweepArgs in = c->fwd_args;
+        void *psi_in = psi;
+        if (c->fwd_compact && r > 0) {
+            psi_in = phic;
+            fcfg.N = Dsec;
+            in.aoff = c->sec_aoff;
+            in.boff = c->sec_boff;
+        }
+        SweepOut out;
+        if (c->fwd_compact && r + 1 < Rf) {
+            out.phi = phic;
+            out.N = Dsec;
+            out.aoff = c->sec_aoff;
+            out.boff = c->sec_boff;
+        } else {
+            out.phi = psi;
+            out.N = N;
+            out.aoff = c->fwd_args.aoff;
+            out.boff = c->fwd_args.boff;
+        }
+        if ((e = launch_forward_sweep<R>(fcfg, psi_in, c->fwd.runs[r], fops, cs, in, r == 0 ? 1 : 0,
+                                         c->hf_addr, out)) != cudaSuccess)
             return cuda_fail(c, e, "forward kernel");
         ++c->launches;
         c->prof.launches[UCCSD_K_FORWARD]++;
@@ -676,8 +705,6 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
         // the last run (first in the schedule) leaves phi and lambda nowhere:
         // nothing reads them after the gradient
         const int R_ = int(c->adj.runs.size());
-        const size_t Dsec = size_t(c->hsec.Da) * size_t(c->hsec.Db);
-        void *phic = c->adj_compact ? dptr(c, "phic") : nullptr;
         void *lamc = c->adj_compact ? dptr(c, "lamc") : nullptr;
         for (int r = R_ - 1; r >= 0; --r) {
             LaunchCfg acfg = cfg;

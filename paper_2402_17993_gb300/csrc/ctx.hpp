@@ -54,9 +54,10 @@ struct uccsd_ctx {
     int layout = 0;        // 0 full 2^n vector, 1 electron-sector array (UCCSD_LAYOUT_*)
     uint32_t hf_addr = 0;  // address of the reference amplitude in a slot
     // electron-sector addressing (rank(sa) * Db, rank(sb)) in any layout, and
-    // whether the adjoint's runs pass phi and lambda on in that compact order
+    // whether the forward's runs pass the state, and the adjoint's runs phi
+    // and lambda, on in that compact order
     const uint32_t *sec_aoff = nullptr, *sec_boff = nullptr;
-    bool adj_compact = false;
+    bool adj_compact = false, fwd_compact = false;
     uccsd::CompiledH H;
     std::vector<int32_t> spec_s1a, spec_s1b;  // spectator row of each alpha / beta pair group
     int K = 0, order = 1, M = 1;

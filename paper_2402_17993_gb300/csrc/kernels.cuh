@@ -104,20 +104,23 @@ struct SweepArgs {
     int n_alpha = 0, n_beta = 0;
 };
 
-template <typename R>
-cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev &run,
-                                 const COpDev *ops, const void *cs, const SweepArgs &sa,
-                                 int init_hf, uint32_t hf);
-
-// Where an adjoint run leaves phi and lambda after its factors: slot b of
-// each at phi + b * N (same for lam), amplitude of determinant (alpha string
-// sa, beta string sb) at aoff[sa] + boff[sb].  phi == nullptr: nowhere (the
-// last run of a sweep; nothing reads the vectors afterwards).
+// Where a sweep run leaves its vectors after its factors (the forward: the
+// state in phi; the adjoint: phi and lambda): slot b of each at phi + b * N
+// (same for lam), amplitude of determinant (alpha string sa, beta string sb)
+// at aoff[sa] + boff[sb].  phi == nullptr (adjoint only): nowhere, after the
+// last run of the sweep, since nothing reads the vectors afterwards.
 struct SweepOut {
     void *phi = nullptr, *lam = nullptr;
     size_t N = 0;
     const uint32_t *aoff = nullptr, *boff = nullptr;
 };
+
+// psi, cfg.N and sa.aoff / sa.boff address the state the run reads (unused
+// when init_hf is set: the run starts from the reference determinant).
+template <typename R>
+cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev &run,
+                                 const COpDev *ops, const void *cs, const SweepArgs &sa,
+                                 int init_hf, uint32_t hf, const SweepOut &out);
 
 // phi, lam, cfg.N and sa.aoff / sa.boff address the vectors the run reads.
 template <typename R>

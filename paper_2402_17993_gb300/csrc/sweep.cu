@@ -121,6 +121,15 @@ __device__ __forceinline__ uint32_t entry_index(const TileView &v, int e) {
     return entry_index_at(v, e, v.aoff, v.boff);
 }
 
+// Write a forward tile's entries to where the next run (or the caller, after
+// the last run) reads the state.
+template <typename R, int THREADS>
+__device__ __forceinline__ void store_forward_tile(const TileView &v, int D, const V2<R> *tile,
+                                                   const SweepOut &out) {
+    V2<R> *op = static_cast<V2<R> *>(out.phi) + (size_t)blockIdx.y * out.N;
+    for (int e = threadIdx.x; e < D; e += THREADS) op[entry_index_at(v, e, out.aoff, out.boff)] = tile[e];
+}
+
 // Write an adjoint tile's phi and lambda entries to where the next run reads
 // them (nothing after the last run).
 template <typename R, int THREADS>
@@ -384,7 +393,8 @@ struct Roles {
 template <typename R, int THREADS>
 __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
     V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
-    const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf) {
+    const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf,
+    SweepOut out) {
     using RL = Roles<THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ OpHdr<R> hdr[2];
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < D; e += THREADS) st[entry_index(v, e)] = tile[e];
+    store_forward_tile<R, THREADS>(v, D, tile, out);
 }
 
 // Adjoint sweep of one run over one tile, factors in reverse: the compute
@@ -694,7 +704,8 @@ __device__ __forceinline__ void forward_list_step(int o, int nops, V2<R> *tile, 
 template <typename R, int THREADS>
 __global__ void __launch_bounds__(THREADS) forward_list_kernel(
     V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
-    const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf) {
+    const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf,
+    SweepOut out) {
     constexpr int KP = ListPre<R>::kFwd;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
@@ -738,7 +749,7 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
         if (o + 2 < nops)
             forward_list_step<R, THREADS, KP>(o + 2, nops, tile, sops, scs, spl, sa.pairs, v.rest, p2, p1);
     }
-    for (int e = threadIdx.x; e < D; e += THREADS) st[entry_index(v, e)] = tile[e];
+    store_forward_tile<R, THREADS>(v, D, tile, out);
 }
 
 // One adjoint factor over precomputed pairs: un-rotates phi and lambda and
@@ -1107,7 +1118,7 @@ __global__ void set_hf_kernel(V2<R> *psi, size_t N, uint32_t hf) {
 template <typename R>
 cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev &run,
                                  const COpDev *ops, const void *cs, const SweepArgs &sa,
-                                 int init_hf, uint32_t hf) {
+                                 int init_hf, uint32_t hf, const SweepOut &out) {
     dim3 grid(run.n_tiles, cfg.B);
     const size_t smem = sweep_smem_bytes(run.max_entries, run.max_da, run.max_db, sizeof(V2<R>), 1,
                                          run.op_end - run.op_begin, max(run.La, run.Lb));
@@ -1116,18 +1127,18 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
     if (run.pl_base >= 0 && sa.pairs) {
         if (run.max_entries >= kLargeTile)
             forward_list_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
         else
             forward_list_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
         return cudaGetLastError();
     }
     if (run.max_entries >= kLargeTile)
         forward_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
     else
         forward_sweep_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf);
+            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
     return cudaGetLastError();
 }
 
@@ -1281,7 +1292,8 @@ cudaError_t configure_sweep_kernels(size_t max_smem) {
 #define UCCSD_SWEEP_INST(R)                                                                    \
     template cudaError_t launch_forward_sweep<R>(const LaunchCfg &, void *, const CRunDev &,   \
                                                  const COpDev *, const void *,                 \
-                                                 const SweepArgs &, int, uint32_t);            \
+                                                 const SweepArgs &, int, uint32_t,             \
+                                                 const SweepOut &);            \
     template cudaError_t launch_adjoint_sweep<R>(const LaunchCfg &, void *, void *,            \
                                                  const CRunDev &, const COpDev *, const void *, \
                                                  const SweepArgs &, double *, int,             \
