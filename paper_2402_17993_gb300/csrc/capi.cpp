@@ -491,7 +491,7 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
         // sector addressing: rank of a string among the n_orb-bit strings of
         // its popcount, in ascending order (the order of astr / bstr).  The
         // sector layout stores states this way; the full layout uses it for
-        // the adjoint's hand-over between runs.
+        // the sweeps' hand-over between runs.
         std::vector<uint32_t> off(size_t(2) << no, 0u);
         std::vector<int> cnt(no + 2, 0);
         for (uint32_t sv = 0; sv < (1u << no); ++sv) {
