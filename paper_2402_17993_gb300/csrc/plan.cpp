@@ -364,12 +364,17 @@ bool build_pair_lists(int n_qubits, int n_alpha, int n_beta, size_t max_pairs, S
                         eb2[i] = rkb[sv ^ op.fb];
                         pb_[i] = uint8_t(popc(sv & op.pb) & 1);
                     }
+                    // A pair with odd string parity rotates as the pair with
+                    // its entries swapped and even parity: store it that way,
+                    // so the kernels apply no per-pair sign.
                     raw.resize(2 * size_t(Va) * Vb);
                     size_t q = 0;
                     for (int i = 0; i < Va; ++i)
                         for (int j = 0; j < Vb; ++j) {
-                            raw[q++] = (ea[i] + eb[j]) | (uint32_t(pa_[i] ^ pb_[j]) << 31);
-                            raw[q++] = ea2[i] + eb2[j];
+                            const uint32_t e = ea[i] + eb[j], e2 = ea2[i] + eb2[j];
+                            const bool odd = (pa_[i] ^ pb_[j]) & 1;
+                            raw[q++] = odd ? e2 : e;
+                            raw[q++] = odd ? e : e2;
                         }
                     const std::vector<uint32_t> g =
                         bank_groups(raw.data(), Va * Vb, bank_group, tile_scratch(r.max_entries));

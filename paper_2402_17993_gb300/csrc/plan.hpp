@@ -70,8 +70,11 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
 // Precomputed pair lists of a sweep plan.  For every run, every electron
 // count class (a, b) of its tiles (class index a * (Lb + 1) + b) and every
 // factor of the run, the factor's pairs in tile-entry coordinates: pair word
-// 2i = e | (string parity << 31) with e the occupied-side entry, word 2i + 1
-// = the partner entry e'.  The pairs of (run r, class c, factor o) start at
+// 2i = the occupied-side entry e, word 2i + 1 = the partner entry e', except
+// that a pair whose strings have odd Jordan-Wigner parity is stored as
+// (e', e): rotating that order with the even-parity sign is the same
+// rotation, so no per-pair sign is stored.  The pairs of (run r, class c,
+// factor o) start at
 // pair op_pl[2 * (runs[r].pl_base + c * n_ops_r + o)] and number
 // op_pl[2 * (...) + 1].  Within a factor the pairs come in aligned groups of
 // bank_group pairs (the lanes of one shared-memory wavefront: 16 for 8-byte,

@@ -672,14 +672,14 @@ __device__ __forceinline__ void forward_list_step(int o, int nops, V2<R> *tile, 
 #pragma unroll
         for (int k = k0; k < k0 + 2 && k < KP; ++k)
             if (t + k * THREADS < pl.y) {
-                x[k - k0] = tile[cur[k].x & 0x7FFFFFFFu];
+                x[k - k0] = tile[cur[k].x];
                 y[k - k0] = tile[cur[k].y];
             }
 #pragma unroll
         for (int k = k0; k < k0 + 2 && k < KP; ++k)
             if (t + k * THREADS < pl.y) {
-                rotate_pair<R>(ct, flip_sign(st, cur[k].x), x[k - k0], y[k - k0]);
-                tile[cur[k].x & 0x7FFFFFFFu] = x[k - k0];
+                rotate_pair<R>(ct, st, x[k - k0], y[k - k0]);
+                tile[cur[k].x] = x[k - k0];
                 tile[cur[k].y] = y[k - k0];
             }
     }
@@ -692,9 +692,9 @@ __device__ __forceinline__ void forward_list_step(int o, int nops, V2<R> *tile, 
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (j0 + k * THREADS < pl.y) {
-                V2<R> a = tile[q[k].x & 0x7FFFFFFFu], c = tile[q[k].y];
-                rotate_pair<R>(ct, flip_sign(st, q[k].x), a, c);
-                tile[q[k].x & 0x7FFFFFFFu] = a;
+                V2<R> a = tile[q[k].x], c = tile[q[k].y];
+                rotate_pair<R>(ct, st, a, c);
+                tile[q[k].x] = a;
                 tile[q[k].y] = c;
             }
     }
@@ -772,11 +772,10 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
     const R ct = csv.x, st = flip_sign(csv.y, (op.op_s0 & 0x80000000u) ^ rneg);
     R part = (R)0;
     auto one = [&](uint2 q, V2<R> &fa, V2<R> &fb, V2<R> &la0, V2<R> &lb0) {
-        const uint32_t e = q.x & 0x7FFFFFFFu, e2 = q.y;
-        part += flip_sign(pair_dot<R>(fa, fb, la0, lb0), q.x ^ rneg);
-        const R s = flip_sign(st, q.x);
-        rotate_pair<R>(ct, -s, fa, fb);
-        rotate_pair<R>(ct, -s, la0, lb0);
+        const uint32_t e = q.x, e2 = q.y;
+        part += pair_dot<R>(fa, fb, la0, lb0);
+        rotate_pair<R>(ct, -st, fa, fb);
+        rotate_pair<R>(ct, -st, la0, lb0);
         tp[e] = fa;
         tp[e2] = fb;
         tl[e] = la0;
@@ -789,7 +788,7 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
 #pragma unroll
         for (int k = k0; k < k0 + 2 && k < KP; ++k)
             if (t + k * THREADS < pl.y) {
-                const uint32_t e = cur[k].x & 0x7FFFFFFFu, e2 = cur[k].y;
+                const uint32_t e = cur[k].x, e2 = cur[k].y;
                 f[k - k0] = tp[e];
                 g[k - k0] = tp[e2];
                 l[k - k0] = tl[e];
@@ -808,17 +807,18 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             if (j0 + k * THREADS < pl.y) {
-                const uint32_t e = q[k].x & 0x7FFFFFFFu, e2 = q[k].y;
+                const uint32_t e = q[k].x, e2 = q[k].y;
                 V2<R> fa = tp[e], fb = tp[e2], la0 = tl[e], lb0 = tl[e2];
                 one(q[k], fa, fb, la0, lb0);
             }
     }
-    // warp partial in the state precision, written per (tile, warp); the
-    // reduction sums them in a fixed order in FP64
+    // warp partial in the state precision, written per (tile, warp) with the
+    // tile's rest parity and the factor's sign; the reduction sums them in a
+    // fixed order in FP64
     const R ws = warp_sum(part);
     if (lane == 0)
         gp[(size_t)(op.op_s0 & 0x7FFFFFFFu) * tile_stride + warp] =
-            flip_sign((double)ws, op.op_s0 & 0x80000000u);
+            flip_sign((double)ws, (op.op_s0 ^ rneg) & 0x80000000u);
     __syncthreads();
 }
 
