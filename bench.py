@@ -244,6 +244,26 @@ def oracle_rate(w, thetas, n_eval):
     return n_eval / dt, dt, oracle.num_threads()
 
 
+def oracle_rate_single_thread(seed: int = 1002) -> float:
+    """The oracle's rate on one host core: one 18-qubit evaluation in a
+    child process started with OMP_NUM_THREADS=1 (OpenMP reads it once, at
+    start-up)."""
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle, synth; "
+            "w = synth.workload('18q'); "
+            "ex = oracle.excitations(w['n_orb'], w['n_alpha'], w['n_beta']); "
+            "th = synth.theta_normal(len(ex), 0.05, %d); t = time.perf_counter(); "
+            "oracle.energy_grad(w['n_orb'], w['h'], w['eri'], w['e_core'], w['n_alpha'], "
+            "w['n_beta'], ex, th, sector=True); "
+            "print(time.perf_counter() - t, oracle.num_threads())") % (ROOT, seed)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                         timeout=600)
+    dt, threads = out.stdout.split()[-2:]
+    if int(threads) != 1:
+        raise RuntimeError("the oracle did not run on one thread")
+    return 1.0 / float(dt)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -510,6 +530,12 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"12 of the 64 theta vectors ({dt:.1f} s, sector-restricted "
                                           "FP64 oracle, OpenMP)"}
+        try:
+            line["cpu_baseline"]["single_core"] = {
+                "value": oracle_rate_single_thread(), "unit": UNIT, "cores": 1,
+                "sample": "1 theta vector (seed 1002), OMP_NUM_THREADS=1"}
+        except Exception as exc:  # a missing single-core figure must not cost the bench line
+            line["cpu_baseline"]["single_core"] = {"unavailable": str(exc)[:200]}
     if rank == 0 and not args.no_layout_compare and args.layout == "full":
         line["sector_layout"] = layout_compare(uc, local, w, prec, B, th_host, args, flush)
     if rank == 0 and not args.no_fp64_compare and prec == uc.FP32_STATE:
