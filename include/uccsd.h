@@ -291,6 +291,25 @@ uccsd_status uccsd_expectation_noalloc(uccsd_ctx *ctx, const void *psi, double *
 uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *eri,
                                      double e_core, int *n_groups, int *n_terms);
 
+/* Host-only check hook (no device use): the precomputed pair lists that the
+ * excitation sweeps apply for an excitation list (Eq. 5, first order, one
+ * slice), expanded to determinants.  The forward sweep's plan for nvec = 1,
+ * the adjoint's for nvec = 2, with amplitudes of amp_bytes bytes (8 for the
+ * FP32 state, 16 for FP64).  Row i of out (cap rows of 7 int32, row-major):
+ *   factor  schedule index of the factor (the excitation row here)
+ *   first, second  the determinants (bit q = occupation of spin orbital q)
+ *           whose amplitudes the sweep rotates as
+ *           first' = c first - sign s second, second' = c second + sign s first
+ *           with c, s the cosine and sine of the factor's angle; both -1 for
+ *           the padding pairs that complete a bank-conflict-free group
+ *   sign    +1 or -1
+ *   entry, partner entry  the two tile entries (shared-memory slots)
+ *   index   position of the pair in its factor's list for its tile.
+ * Writes min(count, cap) rows and *n_out = count.  UCCSD_ERR_ARG for an
+ * invalid list or arguments, or a plan too large for precomputed lists. */
+uccsd_status uccsd_plan_pairs(int n_orb, int n_alpha, int n_beta, const int32_t *ijab, int K,
+                              int amp_bytes, int nvec, int32_t *out, int cap, int *n_out);
+
 /* Host-only: the compiled Jordan-Wigner Pauli terms of Eq. 2 in the
  * X^x Z^z form: H = sum_t coef[t] X^{xmask[t]} Z^{zmask[t]}, where
  * X^x Z^z |y> = (-1)^{popcount(y & z)} |y ^ x>.  Writes min(count, cap)

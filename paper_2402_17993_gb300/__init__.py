@@ -37,7 +37,7 @@ EXPORTS = [
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
     "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
     "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
-    "uccsd_energy_grad_batched",
+    "uccsd_energy_grad_batched", "uccsd_plan_pairs",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -124,6 +124,8 @@ def lib():
         L.uccsd_energy_grad_trotter_free.argtypes = [vp, dp, ip, dp, dp, vp]
         L.uccsd_magnitude_order.argtypes = [ip, i32p, f64p, i32p, i32p]
         L.uccsd_trotter_extrapolate.argtypes = [ip, ctypes.POINTER(ctypes.c_int), f64p, f64p]
+        L.uccsd_plan_pairs.argtypes = [ip, ip, ip, i32p, ip, ip, ip, i32p, ip,
+                                       ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -153,6 +155,24 @@ def build_uccsd_list(n_orb: int, n_alpha: int, n_beta: int) -> np.ndarray:
     st = L.uccsd_build_uccsd_list(n_orb, n_alpha, n_beta, _i32p(out), n.value, ctypes.byref(n))
     if st:
         raise UCCSDError(st, "build_uccsd_list")
+    return out
+
+
+def plan_pairs(n_orb, n_alpha, n_beta, ijab, amp_bytes=8, nvec=1):
+    """Host-only: the sweep plan's precomputed pair lists in determinant
+    space, one row (factor, first, second, sign, entry, partner entry,
+    index) per pair (uccsd_plan_pairs)."""
+    ijab = np.ascontiguousarray(ijab, dtype=np.int32).reshape(-1, 4)
+    n = ctypes.c_int(0)
+    st = lib().uccsd_plan_pairs(n_orb, n_alpha, n_beta, _i32p(ijab), ijab.shape[0], amp_bytes,
+                                nvec, None, 0, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "plan_pairs")
+    out = np.zeros((n.value, 7), dtype=np.int32)
+    st = lib().uccsd_plan_pairs(n_orb, n_alpha, n_beta, _i32p(ijab), ijab.shape[0], amp_bytes,
+                                nvec, _i32p(out), n.value, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "plan_pairs")
     return out
 
 

@@ -1849,6 +1849,50 @@ uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *e
     return UCCSD_OK;
 }
 
+uccsd_status uccsd_plan_pairs(int n_orb, int n_alpha, int n_beta, const int32_t *ijab, int K,
+                              int amp_bytes, int nvec, int32_t *out, int cap, int *n_out) {
+    if (n_orb < 1 || n_orb > 15 || n_alpha < 0 || n_beta < 0 || n_alpha > n_orb ||
+        n_beta > n_orb || K < 1 || !ijab || (amp_bytes != 8 && amp_bytes != 16) ||
+        (nvec != 1 && nvec != 2) || cap < 0 || !n_out || (cap > 0 && !out))
+        return UCCSD_ERR_ARG;
+    const int n = 2 * n_orb;
+    const uint64_t hf = hf_bits(n_alpha, n_beta);
+    std::vector<CompiledExc> exc(K);
+    for (int k = 0; k < K; ++k) {
+        const int32_t *r = ijab + 4 * k;
+        auto occ = [&](int q) { return q >= 0 && q < n && ((hf >> q) & 1u); };
+        auto vir = [&](int q) { return q >= 0 && q < n && !((hf >> q) & 1u); };
+        const bool ok = r[1] < 0 ? r[3] < 0 && occ(r[0]) && vir(r[2]) && ((r[0] & 1) == (r[2] & 1))
+                                 : occ(r[0]) && occ(r[1]) && vir(r[2]) && vir(r[3]) && r[0] != r[1] &&
+                                       r[2] != r[3] &&
+                                       ((r[0] & 1) + (r[1] & 1) == (r[2] & 1) + (r[3] & 1));
+        std::string err;
+        if (!ok || !compile_excitation(n, r, &exc[k], &err)) return UCCSD_ERR_ARG;
+    }
+    std::vector<int32_t> op_k;
+    std::vector<double> op_scale;
+    build_schedule(K, 1, 1, &op_k, &op_scale);
+    SweepPlan plan = plan_sweep(n, n_alpha, n_beta, size_t(amp_bytes), nvec, kSweepBudget, exc, op_k);
+    PairLists L;
+    if (!build_pair_lists(n, n_alpha, n_beta, kMaxListPairs, &plan, &L, amp_bytes == 8 ? 16 : 8))
+        return UCCSD_ERR_ARG;
+    const std::vector<ExpandedPair> pairs = expand_pair_lists(n, n_alpha, n_beta, plan, L);
+    const size_t w = std::min(size_t(cap), pairs.size());
+    for (size_t i = 0; i < w; ++i) {
+        const ExpandedPair &x = pairs[i];
+        int32_t *row = out + 7 * i;
+        row[0] = x.factor;
+        row[1] = int32_t(x.first);
+        row[2] = int32_t(x.second);
+        row[3] = x.sign;
+        row[4] = x.e;
+        row[5] = x.e2;
+        row[6] = x.index;
+    }
+    *n_out = int(pairs.size());
+    return UCCSD_OK;
+}
+
 uccsd_status uccsd_pauli_terms(int n_orb, const double *h, const double *eri, double e_core,
                                uint32_t *xmask, uint32_t *zmask, double *coef, int cap, int *n_out) {
     if (cap < 0 || !n_out || (cap > 0 && (!xmask || !zmask || !coef))) return UCCSD_ERR_ARG;

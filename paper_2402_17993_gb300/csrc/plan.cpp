@@ -389,6 +389,56 @@ bool build_pair_lists(int n_qubits, int n_alpha, int n_beta, size_t max_pairs, S
     return true;
 }
 
+std::vector<ExpandedPair> expand_pair_lists(int n_qubits, int n_alpha, int n_beta,
+                                            const SweepPlan &plan, const PairLists &L) {
+    std::vector<uint16_t> combos, rank;
+    std::vector<int32_t> offs;
+    build_comb_tables(&combos, &rank, &offs);
+    auto cnt = [&](int m, int k) { return (k < 0 || k > m) ? 0 : offs[m * 17 + k + 1] - offs[m * 17 + k]; };
+    auto strings = [&](int m, int k) { return &combos[((size_t(1) << m) - 1) + offs[m * 17 + k]]; };
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
+    std::vector<ExpandedPair> out;
+    for (const CRunDev &r : plan.runs) {
+        if (r.pl_base < 0) continue;
+        const int nops = r.op_end - r.op_begin;
+        const uint32_t Ta = r.tmask & amask, Tb = r.tmask & ~amask;
+        const uint32_t scratch = uint32_t(tile_scratch(r.max_entries));
+        for (int t = 0; t < r.n_tiles; ++t) {
+            const uint32_t rest = deposit_bits(uint32_t(t), r.rmask);
+            const int a = n_alpha - popc(rest & amask), b = n_beta - popc(rest & ~amask);
+            if (a < 0 || a > r.La || b < 0 || b > r.Lb) continue;
+            const int cls = a * (r.Lb + 1) + b;
+            const uint32_t Db = uint32_t(cnt(r.Lb, b));
+            const uint16_t *sa = strings(r.La, a), *sb = strings(r.Lb, b);
+            auto det = [&](uint32_t e) {
+                return rest | deposit_bits(sa[e / Db], Ta) | deposit_bits(sb[e % Db], Tb);
+            };
+            for (int o = 0; o < nops; ++o) {
+                const COpDev &op = plan.ops[r.op_begin + o];
+                const size_t slot = size_t(r.pl_base) + size_t(cls) * nops + o;
+                const int32_t pos = L.op_pl[2 * slot], n = L.op_pl[2 * slot + 1];
+                int sign = (op.op_s0 & 0x80000000u) ? -1 : 1;
+                if (popc(rest & op.par_rest) & 1) sign = -sign;
+                for (int j = 0; j < n; ++j) {
+                    const uint32_t w0 = L.pairs[2 * (size_t(pos) + j)], w1 = L.pairs[2 * (size_t(pos) + j) + 1];
+                    ExpandedPair x;
+                    x.factor = int32_t(op.op_s0 & 0x7FFFFFFFu);
+                    x.sign = sign;
+                    x.e = int32_t(w0);
+                    x.e2 = int32_t(w1);
+                    x.index = j;
+                    const bool pad = w0 >= scratch || w1 >= scratch;
+                    x.first = pad ? 0xFFFFFFFFu : det(w0);
+                    x.second = pad ? 0xFFFFFFFFu : det(w1);
+                    out.push_back(x);
+                }
+            }
+        }
+    }
+    return out;
+}
+
 void build_comb_tables(std::vector<uint16_t> *combos, std::vector<uint16_t> *rank,
                        std::vector<int32_t> *offs) {
     combos->assign((size_t(1) << (kCombMax + 1)) - 1, 0);

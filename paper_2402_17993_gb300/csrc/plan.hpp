@@ -93,6 +93,22 @@ struct PairLists {
 bool build_pair_lists(int n_qubits, int n_alpha, int n_beta, size_t max_pairs, SweepPlan *plan,
                       PairLists *out, int bank_group);
 
+// One pair of a plan's lists in determinant space: the sweep loads the
+// amplitudes of `first` and `second` and rotates
+//   first' = c first - sign s second,  second' = c second + sign s first
+// (c, s the factor's cos and sin).  Padding pairs have first = second =
+// 0xFFFFFFFF.  e, e2: tile entries; index: position in the factor's list.
+struct ExpandedPair {
+    int32_t factor;
+    uint32_t first, second;
+    int32_t sign;
+    int32_t e, e2, index;
+};
+// Every pair of every run, tile and factor of `plan` with lists L (host
+// check of the lists against an independent generator action).
+std::vector<ExpandedPair> expand_pair_lists(int n_qubits, int n_alpha, int n_beta,
+                                            const SweepPlan &plan, const PairLists &L);
+
 // Combinatorial tables for bit strings of m <= kCombMax bits: for each m,
 // the 2^m strings sorted by (popcount, value) at combos[2^m - 1 ...], the
 // rank of each string among those of equal popcount at rank[2^m - 1 + s],
