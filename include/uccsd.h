@@ -67,7 +67,12 @@ typedef enum {
 
 typedef enum {
     UCCSD_FP64 = 0,       /* complex128 state, FP64 arithmetic throughout */
-    UCCSD_FP32_STATE = 1  /* complex64 state and rotations; FP64 energy/gradient reductions */
+    UCCSD_FP32_STATE = 1  /* 8-byte FP32 state slots and FP32 rotations; FP64 energy and
+                             gradient reductions.  The method's amplitudes are real (real
+                             integrals, real generators, real reference), so a slot holds
+                             one real amplitude as the unevaluated sum hi + lo of two FP32
+                             words, lo the rounding error of hi kept by error-free
+                             transformations (TwoSum, FMA) */
 } uccsd_prec;
 
 typedef enum {
@@ -223,7 +228,7 @@ uccsd_status uccsd_replay(uccsd_ctx *ctx, void *stream);
 
 /* Copy the state vector of slot `slot` after the last uccsd_energy or
  * energies-only batch call to host memory as 2*2^n interleaved (re, im)
- * doubles.  len must be >= 2*2^n.  Synchronises the context's last stream.
+ * doubles (UCCSD_FP32_STATE: re = hi + lo, im = 0).  len must be >= 2*2^n.  Synchronises the context's last stream.
  * After a gradient call the slot's content is unspecified (the adjoint
  * sweep may leave it partly swept back). */
 uccsd_status uccsd_get_state(uccsd_ctx *ctx, int slot, double *out_re_im, size_t len);
@@ -275,8 +280,11 @@ uccsd_status uccsd_get_profile(const uccsd_ctx *ctx, uccsd_profile_t *out);
  *
  * Scratch: a fixed device array of 2 * UCCSD_NOALLOC_MAX_TILES doubles
  * (64 KiB) inside the library, held by every GPU that loads the library
- * until the process exits.  States above 26 qubits need more partials and
- * are rejected with UCCSD_ERR_ARG.  The first call on a device looks up
+ * until the process exits: two partials per H-apply tile, and a state has
+ * C(n_orb, n_alpha) * ceil(C(n_orb, n_beta) / 2048) tiles.  That covers
+ * every closed-shell state up to 26 qubits (1716 tiles at 13 orbitals and
+ * 6 + 6 electrons); a state with more tiles (28 qubits at 7 + 7 electrons:
+ * 6864) is rejected with UCCSD_ERR_ARG.  The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress); make that first call
  * before any stream capture.  All calls in the process share the array and
  * it keeps the last call's partials; each call overwrites what it reads, so

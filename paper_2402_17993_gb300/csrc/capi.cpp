@@ -1657,7 +1657,11 @@ uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {
         std::vector<float> tmp(2 * N);
         e = cudaMemcpyAsync(tmp.data(), src, N * 8, cudaMemcpyDeviceToHost, c->setup);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
-        for (size_t i = 0; i < 2 * N; ++i) dst[i] = tmp[i];
+        // real amplitudes held as hi + lo (two FP32 words per slot)
+        for (size_t i = 0; i < N; ++i) {
+            dst[2 * i] = (double)tmp[2 * i] + (double)tmp[2 * i + 1];
+            dst[2 * i + 1] = 0.0;
+        }
     } else {
         e = cudaMemcpyAsync(dst, src, N * 16, cudaMemcpyDeviceToHost, c->setup);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);

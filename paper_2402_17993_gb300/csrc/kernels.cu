@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "amp.cuh"
 #include "kernels.cuh"
 
 namespace uccsd {
@@ -85,7 +86,14 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
     double s, c;
     sincos(a, &s, &c);
     V2<R> v;
-    v.x = (R)c;
+    if constexpr (sizeof(R) == 4) {
+        // the FP32 rotation takes d = 1 - cos = 2 sin^2(a / 2), exact to FP32
+        // rounding for small angles (1 - cos would cancel)
+        const double h = sin(0.5 * a);
+        v.x = (R)(2.0 * h * h);
+    } else {
+        v.x = (R)c;
+    }
     v.y = (R)s;
     cs[(size_t)b * n_ops + o] = v;
 }
@@ -179,7 +187,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                                                              V2<R> *__restrict__ sig, size_t N,
                                                              DevHam<R> H, HSector hs,
                                                              double *__restrict__ Epart,
-                                                             int store_sigma) {
+                                                             int flags) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *src = reinterpret_cast<V2<R> *>(smem_raw);                  // one source row
     uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
@@ -447,10 +455,19 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     for (int i = 0; i < EPT; ++i) {
         if (cix[i] < 0) continue;
         const V2<R> p = own[i];
-        e += (double)p.x * (double)acc[i].x + (double)p.y * (double)acc[i].y;
-        nrm += (double)p.x * (double)p.x + (double)p.y * (double)p.y;
-        if (store_sigma)
-            sig[(size_t)b * N + (hs.aoff[sR] + hs.boff[sc[i]])] = acc[i];
+        V2<R> out = acc[i];
+        if (sizeof(R) == 8 || (flags & kHApplyComplex32)) {
+            e += amp::re_dot(p, out);
+            nrm += amp::re_dot(p, p);
+        } else {
+            // FP32 state, real amplitudes as hi + lo: the Kahan terms of both
+            // words join lo (true sum = acc - comp)
+            out.y = out.y - comp[i].y - comp[i].x;
+            const double pv = (double)p.x + (double)p.y;
+            e += pv * ((double)out.x + (double)out.y);
+            nrm += pv * pv;
+        }
+        if (flags & kHApplyStoreSigma) sig[(size_t)b * N + (hs.aoff[sR] + hs.boff[sc[i]])] = out;
     }
     e = block_sum(e, red);
     nrm = block_sum(nrm, red);
@@ -688,7 +705,7 @@ cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const in
 
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
-                          const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma) {
+                          const DevHam<R> &H, const HSector &hs, double *Epart, int flags) {
     (void)LH;
     dim3 grid(hs.Da * hs.ncb, cfg.B);
     const int threads = std::min(kRowThreads, std::max(32, ((hs.colblock + 31) / 32) * 32));
@@ -697,10 +714,10 @@ cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int 
     const V2<R> *p = static_cast<const V2<R> *>(psi);
     V2<R> *s = static_cast<V2<R> *>(sig);
     switch (ept <= 1 ? 1 : ept <= 2 ? 2 : ept <= 4 ? 4 : ept <= 8 ? 8 : 0) {
-        case 1: happly_kernel<R, 1><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
-        case 2: happly_kernel<R, 2><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
-        case 4: happly_kernel<R, 4><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
-        case 8: happly_kernel<R, 8><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, store_sigma); break;
+        case 1: happly_kernel<R, 1><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
+        case 2: happly_kernel<R, 2><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
+        case 4: happly_kernel<R, 4><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
+        case 8: happly_kernel<R, 8><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

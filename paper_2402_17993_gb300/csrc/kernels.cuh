@@ -83,8 +83,9 @@ struct LaunchCfg {
     cudaStream_t stream = nullptr;
 };
 
-// cs[b][o] = (cos, sin)(theta[b][op_k[o]] * op_scale[o]) computed in FP64,
-// stored in R.
+// cs[b][o] = (cos, sin)(a) with a = theta[b][op_k[o]] * op_scale[o],
+// computed in FP64 and stored in R; the FP32 state stores (1 - cos, sin)(a)
+// (its rotation form, see sweep.cu).
 template <typename R>
 cudaError_t launch_cs(const LaunchCfg &cfg, const double *theta, int K, const int32_t *op_k,
                       const double *op_scale, void *cs);
@@ -168,9 +169,14 @@ int adjoint_partials_per_tile(const CRunDev &run, bool lists);
 // Dynamic shared memory opt-in of the sweep kernels.
 cudaError_t configure_sweep_kernels(size_t max_smem);
 
+// H-apply flags: store sigma (energy-only calls skip it); the FP32 slots
+// hold complex (re, im) amplitudes (a caller's state) instead of the real
+// hi + lo amplitudes of the library's FP32 state (see amp.cuh).
+constexpr int kHApplyStoreSigma = 1;
+constexpr int kHApplyComplex32 = 2;
 template <typename R>
 cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int LH,
-                          const DevHam<R> &H, const HSector &hs, double *Epart, int store_sigma);
+                          const DevHam<R> &H, const HSector &hs, double *Epart, int flags);
 
 // E[b] from the per-tile partials (e', n) of sum Re(conj psi (H - shift) psi)
 // and sum |psi|^2: E = shift * n + e' (rayleigh = 0) or shift + e'/n

@@ -64,10 +64,10 @@ extern "C" uccsd_status uccsd_expectation_noalloc(uccsd_ctx *c, const void *psi,
     }
     const int tiles = c->hsec.Da * c->hsec.ncb;
     if (tiles > UCCSD_NOALLOC_MAX_TILES) {
-        c->err = "uccsd_expectation_noalloc: " + std::to_string(c->n) +
-                 " qubits need " + std::to_string(tiles) +
-                 " energy partials, above the fixed scratch of " +
-                 std::to_string(UCCSD_NOALLOC_MAX_TILES) + " (at most 26 qubits)";
+        c->err = "uccsd_expectation_noalloc: the state needs " + std::to_string(tiles) +
+                 " H-apply tiles (C(n_orb, n_alpha) x ceil(C(n_orb, n_beta) / " +
+                 std::to_string(uccsd::kHColBlock) + ")), above the fixed scratch of " +
+                 std::to_string(UCCSD_NOALLOC_MAX_TILES) + " tiles";
         return UCCSD_ERR_ARG;
     }
     if (c->device < 0 || c->device >= kMaxDevices) {
@@ -90,9 +90,11 @@ extern "C" uccsd_status uccsd_expectation_noalloc(uccsd_ctx *c, const void *psi,
     // The H-apply writes both partials of every tile before the reduction
     // reads them, so nothing in the scratch has to start at zero.
     if (c->prec)
-        e = uccsd::launch_happly<float>(cfg, psi, nullptr, c->LH, c->hf32, c->hsec_full, partials, 0);
+        e = uccsd::launch_happly<float>(cfg, psi, nullptr, c->LH, c->hf32, c->hsec_full, partials,
+                                         uccsd::kHApplyComplex32);
     else
-        e = uccsd::launch_happly<double>(cfg, psi, nullptr, c->LH, c->hf64, c->hsec_full, partials, 0);
+        e = uccsd::launch_happly<double>(cfg, psi, nullptr, c->LH, c->hf64, c->hsec_full, partials,
+                                         uccsd::kHApplyComplex32);
     if (e == cudaSuccess)
         e = uccsd::launch_reduce(cfg, partials, tiles, nullptr, 1, nullptr, 0, nullptr, nullptr,
                                  nullptr, c->shift, c->prec ? 1 : 0, E, nullptr);

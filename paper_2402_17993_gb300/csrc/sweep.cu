@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "amp.cuh"
 #include "kernels.cuh"
 #include "plan.hpp"
 
@@ -318,7 +319,15 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-// (c x - s y, c y + s x) for the pair (x occupied side, y partner).
+// Rotation of the pair (x occupied side, y partner) by the factor's angle:
+// (c x - s y, c y + s x).
+//   FP64 state: c = cos, complex amplitudes.
+//   FP32 state (real amplitudes as hi + lo, see amp.cuh): the first
+//   argument is d = 1 - cos = 2 sin^2(angle / 2), and the rotation is
+//   x' = x - (d x + s y), y' = y - (d y - s x).  c never appears, so its
+//   FP32 rounding (up to 3e-8 for a small angle, a norm change of each
+//   factor's pairs) does not either; the rounding error of the large
+//   subtraction goes to lo (TwoSum), lo itself is updated by the same map.
 template <typename R>
 __device__ __forceinline__ void rotate_pair(R c, R s, V2<R> &x, V2<R> &y) {
     const V2<R> x0 = x, y0 = y;
@@ -327,12 +336,86 @@ __device__ __forceinline__ void rotate_pair(R c, R s, V2<R> &x, V2<R> &y) {
     y.x = fma_rn(c, y0.x, mul_rn(s, x0.x));
     y.y = fma_rn(c, y0.y, mul_rn(s, x0.y));
 }
+template <>
+__device__ __forceinline__ void rotate_pair<float>(float d, float s, float2 &x, float2 &y) {
+    const float2 x0 = x, y0 = y;
+    const float tx = fma_rn(d, x0.x, mul_rn(s, y0.x));
+    const float ty = fma_rn(d, y0.x, -mul_rn(s, x0.x));
+    float ex, ey;
+    amp::two_sum(x0.x, -tx, x.x, ex);
+    amp::two_sum(y0.x, -ty, y.x, ey);
+    x.y = fma_rn(-d, x0.y, fma_rn(-s, y0.y, __fadd_rn(x0.y, ex)));
+    y.y = fma_rn(-d, y0.y, fma_rn(s, x0.y, __fadd_rn(y0.y, ey)));
+}
 
-// Re(conj(l_x) (G phi)_x + conj(l_x') (G phi)_x') / s for the pair, with
-// (G phi)_x = -s phi_x', (G phi)_x' = s phi_x.
+// Gradient partials.  A pair contributes Re(conj(l_x) (G phi)_x +
+// conj(l_x') (G phi)_x') / s with (G phi)_x = -s phi_x', (G phi)_x' =
+// s phi_x (pair_dot); the partials of a thread and of a warp are summed in
+// Part<R>:
+//   FP64 state: double;
+//   FP32 state: a float2 (hi, lo) unevaluated sum.  pair_dot forms the dot
+//   of the real values hi + lo with the rounding errors of its two main
+//   products (FMA) and of their difference (TwoSum) in lo, and the sums
+//   carry their rounding errors in lo as well, so the partial reaches FP64
+//   through FP32 instructions only (GB300's FP64 rate is 1/64 of its FP32
+//   rate, and these sums run once per pair).
 template <typename R>
-__device__ __forceinline__ R pair_dot(V2<R> fx, V2<R> fy, V2<R> lx, V2<R> ly) {
+struct PartOf {
+    using T = R;
+};
+template <>
+struct PartOf<float> {
+    using T = float2;
+};
+template <typename R>
+using Part = typename PartOf<R>::T;
+
+template <typename R>
+__device__ __forceinline__ Part<R> part_zero() {
+    return (R)0;
+}
+template <>
+__device__ __forceinline__ float2 part_zero<float>() {
+    return make_float2(0.f, 0.f);
+}
+__device__ __forceinline__ void part_add(double &acc, double d) { acc += d; }
+__device__ __forceinline__ void part_add(float2 &acc, float2 d) {
+    float s, e;
+    amp::two_sum(acc.x, d.x, s, e);
+    acc.y = __fadd_rn(acc.y, __fadd_rn(d.y, e));
+    acc.x = s;
+}
+__device__ __forceinline__ double part_flip(double v, uint32_t neg) { return flip_sign(v, neg); }
+__device__ __forceinline__ float2 part_flip(float2 v, uint32_t neg) {
+    return make_float2(flip_sign(v.x, neg), flip_sign(v.y, neg));
+}
+__device__ __forceinline__ double part_value(double v) { return v; }
+__device__ __forceinline__ double part_value(float2 v) { return amp::value(v); }
+__device__ __forceinline__ double part_warp_sum(double v) { return warp_sum(v); }
+__device__ __forceinline__ float2 part_warp_sum(float2 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float2 w;
+        w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+        w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+        part_add(v, w);
+    }
+    return v;
+}
+
+template <typename R>
+__device__ __forceinline__ Part<R> pair_dot(V2<R> fx, V2<R> fy, V2<R> lx, V2<R> ly) {
     return fma_rn(ly.x, fx.x, fma_rn(ly.y, fx.y, -fma_rn(lx.x, fy.x, mul_rn(lx.y, fy.y))));
+}
+template <>
+__device__ __forceinline__ float2 pair_dot<float>(float2 fx, float2 fy, float2 lx, float2 ly) {
+    // l_x' phi_x - l_x phi_x' of the real values hi + lo
+    const float p1 = mul_rn(ly.x, fx.x), e1 = fma_rn(ly.x, fx.x, -p1);
+    const float p2 = mul_rn(lx.x, fy.x), e2 = fma_rn(lx.x, fy.x, -p2);
+    float h, e;
+    amp::two_sum(p1, -p2, h, e);
+    const float cross = fma_rn(ly.x, fx.y, fma_rn(ly.y, fx.x, -fma_rn(lx.x, fy.y, mul_rn(lx.y, fy.x))));
+    return make_float2(h, __fadd_rn(__fadd_rn(e, __fsub_rn(e1, e2)), cross));
 }
 
 // Per-factor header written by the builder warp: pair-set sizes, cos, the
@@ -547,7 +630,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
             const int P = h.Va * h.Vb;
             const int2 *A = lists + buf * lstride;
             const int2 *B = A + h.Va;
-            R part = (R)0;
+            Part<R> part = part_zero<R>();
             if ((int)threadIdx.x < P) {
                 PairWalk wk;
                 wk.init(threadIdx.x, RL::kCompute, h.Vb);
@@ -565,8 +648,8 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
                     pair_offsets(A[ja1], B[jb1], &e1, &f1, &q1);
                     V2<R> fa = tp[e0], fb = tp[f0], la0 = tl[e0], lb0 = tl[f0];
                     V2<R> ga = tp[e1], gb = tp[f1], ma = tl[e1], mb = tl[f1];
-                    part += flip_sign(pair_dot<R>(fa, fb, la0, lb0), q0 ^ h.rneg);
-                    part += flip_sign(pair_dot<R>(ga, gb, ma, mb), q1 ^ h.rneg);
+                    part_add(part, part_flip(pair_dot<R>(fa, fb, la0, lb0), q0 ^ h.rneg));
+                    part_add(part, part_flip(pair_dot<R>(ga, gb, ma, mb), q1 ^ h.rneg));
                     const R s0 = flip_sign(h.st, q0), s1 = flip_sign(h.st, q1);
                     // U(-theta): rotate with -s
                     rotate_pair<R>(h.ct, -s0, fa, fb);
@@ -590,7 +673,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
                     uint32_t q0;
                     pair_offsets(A[ja], B[jb], &e0, &f0, &q0);
                     V2<R> fa = tp[e0], fb = tp[f0], la0 = tl[e0], lb0 = tl[f0];
-                    part += flip_sign(pair_dot<R>(fa, fb, la0, lb0), q0 ^ h.rneg);
+                    part_add(part, part_flip(pair_dot<R>(fa, fb, la0, lb0), q0 ^ h.rneg));
                     const R s0 = flip_sign(h.st, q0);
                     rotate_pair<R>(h.ct, -s0, fa, fb);
                     rotate_pair<R>(h.ct, -s0, la0, lb0);
@@ -600,10 +683,10 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
                     tl[f0] = lb0;
                 }
             }
-            // per-warp partial in the state precision (a few products per
-            // thread), then FP64 across the compute warps
-            const R ws = warp_sum(part);
-            if (lane == 0) wring[buf][warp] = flip_sign((double)ws, h.opneg);
+            // per-warp partial (FP64, or FP32 hi + lo for the FP32 state),
+            // then FP64 across the compute warps
+            const Part<R> ws = part_warp_sum(part);
+            if (lane == 0) wring[buf][warp] = flip_sign(part_value(ws), h.opneg);
         }
         __syncthreads();
     }
@@ -752,17 +835,35 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
     store_forward_tile<R, THREADS>(v, D, tile, out);
 }
 
+// A thread's gradient partial of one factor waiting for its warp sum: the
+// sum runs during the next factor's step (its shuffles overlap that step's
+// shared-memory loads instead of delaying the barrier) and lane 0 writes it
+// to the factor's (tile, warp) slot with the tile's rest parity and the
+// factor's sign applied.
+template <typename R>
+struct PendingPart {
+    Part<R> part;
+    double *dst;  // nullptr: nothing pending
+    uint32_t neg;
+};
+template <typename R>
+__device__ __forceinline__ void flush_pending(const PendingPart<R> &p) {
+    if (!p.dst) return;  // uniform over the block
+    const Part<R> ws = part_warp_sum(p.part);
+    if ((threadIdx.x & 31) == 0) *p.dst = flip_sign(part_value(ws), p.neg);
+}
+
 // One adjoint factor over precomputed pairs: un-rotates phi and lambda and
-// writes each warp's partial of Re <lambda|G|phi> (string and rest parities
-// and the factor's sign applied) to its (tile, warp) slot of the gradient
-// partials.
+// forms this thread's partial of Re <lambda|G|phi>, left pending in `pend`
+// (the previous factor's pending partial is written during this step).
 template <typename R, int THREADS, int KP>
 __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2<R> *tl,
                                                   const COpDev *sops, const V2<R> *scs,
                                                   const int2 *spl, const uint2 *__restrict__ pairs,
                                                   uint32_t rest, uint2 (&cur)[KP], uint2 (&nxt)[KP],
-                                                  double *__restrict__ gp, int tile_stride) {
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+                                                  double *__restrict__ gp, int tile_stride,
+                                                  PendingPart<R> &pend) {
+    const int t = threadIdx.x, warp = t >> 5;
     if (t == 0 && o - kListAhead >= 0) prefetch_list_l2(pairs, spl[o - kListAhead]);
     if (o - 2 >= 0) fetch_pairs<KP>(nxt, pairs, spl[o - 2], t, THREADS);
     const int2 pl = spl[o];
@@ -770,10 +871,10 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
     const V2<R> csv = scs[o];
     const uint32_t rneg = (uint32_t)(__popc(rest & op.par_rest) & 1) << 31;
     const R ct = csv.x, st = flip_sign(csv.y, (op.op_s0 & 0x80000000u) ^ rneg);
-    R part = (R)0;
+    Part<R> part = part_zero<R>();
     auto one = [&](uint2 q, V2<R> &fa, V2<R> &fb, V2<R> &la0, V2<R> &lb0) {
         const uint32_t e = q.x, e2 = q.y;
-        part += pair_dot<R>(fa, fb, la0, lb0);
+        part_add(part, pair_dot<R>(fa, fb, la0, lb0));
         rotate_pair<R>(ct, -st, fa, fb);
         rotate_pair<R>(ct, -st, la0, lb0);
         tp[e] = fa;
@@ -781,7 +882,9 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
         tl[e] = la0;
         tl[e2] = lb0;
     };
-    // the prefetched pairs in chunks of two: loads of a chunk before its stores
+    // the prefetched pairs in chunks of two: loads of a chunk before its
+    // stores; the previous factor's warp sum between the first loads and
+    // their use
 #pragma unroll
     for (int k0 = 0; k0 < KP; k0 += 2) {
         V2<R> f[2], g[2], l[2], m[2];
@@ -794,6 +897,7 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
                 l[k - k0] = tl[e];
                 m[k - k0] = tl[e2];
             }
+        if (k0 == 0) flush_pending<R>(pend);
 #pragma unroll
         for (int k = k0; k < k0 + 2 && k < KP; ++k)
             if (t + k * THREADS < pl.y) one(cur[k], f[k - k0], g[k - k0], l[k - k0], m[k - k0]);
@@ -812,13 +916,12 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
                 one(q[k], fa, fb, la0, lb0);
             }
     }
-    // warp partial in the state precision, written per (tile, warp) with the
-    // tile's rest parity and the factor's sign; the reduction sums them in a
+    // the warp partial (FP64, or FP32 hi + lo for the FP32 state) goes to
+    // the factor's (tile, warp) slot; the reduction sums the slots in a
     // fixed order in FP64
-    const R ws = warp_sum(part);
-    if (lane == 0)
-        gp[(size_t)(op.op_s0 & 0x7FFFFFFFu) * tile_stride + warp] =
-            flip_sign((double)ws, (op.op_s0 ^ rneg) & 0x80000000u);
+    pend.part = part;
+    pend.dst = gp + (size_t)(op.op_s0 & 0x7FFFFFFFu) * tile_stride + warp;
+    pend.neg = (op.op_s0 ^ rneg) & 0x80000000u;
     __syncthreads();
 }
 
@@ -871,17 +974,19 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     if (nops > 0) fetch_pairs<KP>(p0, sa.pairs, spl[nops - 1], threadIdx.x, THREADS);
     if (nops > 1) fetch_pairs<KP>(p1, sa.pairs, spl[nops - 2], threadIdx.x, THREADS);
     __syncthreads();
+    PendingPart<R> pend{part_zero<R>(), nullptr, 0u};
     for (int it = 0; it < nops; it += 3) {
         const int o = nops - 1 - it;
         adjoint_list_step<R, THREADS, KP>(o, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest, p0, p2,
-                                          gp, tile_stride);
+                                          gp, tile_stride, pend);
         if (it + 1 < nops)
             adjoint_list_step<R, THREADS, KP>(o - 1, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
-                                              p1, p0, gp, tile_stride);
+                                              p1, p0, gp, tile_stride, pend);
         if (it + 2 < nops)
             adjoint_list_step<R, THREADS, KP>(o - 2, nops, tp, tl, sops, scs, spl, sa.pairs, v.rest,
-                                              p2, p1, gp, tile_stride);
+                                              p2, p1, gp, tile_stride, pend);
     }
+    flush_pending<R>(pend);
     store_adjoint_tile<R, THREADS>(v, D, tp, tl, out);
 }
 
@@ -1012,7 +1117,7 @@ __global__ void __launch_bounds__(THREADS) gen_dot_kernel(
         }
         const int P = p.Va * p.Vb;
         const int opi = (int)(op.op_s0 & 0x7FFFFFFFu);
-        R part = (R)0;
+        double part = 0.0;
         if (P > 0) {
             const int rpar = __popc(v.rest & op.par_rest) & 1;
             const float inv = 1.0f / (float)p.Vb;
@@ -1026,11 +1131,11 @@ __global__ void __launch_bounds__(THREADS) gen_dot_kernel(
                 const V2<R> fa = tp[e], fb = tp[e2];
                 const V2<R> lx = tl[e], ly = tl[e2];
                 // (G phi)_x = -s phi_x', (G phi)_x' = s phi_x
-                const R d = (ly.x * fa.x + ly.y * fa.y) - (lx.x * fb.x + lx.y * fb.y);
+                const double d = amp::re_dot(ly, fa) - amp::re_dot(lx, fb);
                 part += neg ? -d : d;
             }
         }
-        const double dp = (op.op_s0 >> 31) ? -(double)warp_sum(part) : (double)warp_sum(part);
+        const double dp = (op.op_s0 >> 31) ? -warp_sum(part) : warp_sum(part);
         const int rb = o & 1;
         if (lane == 0) wring[rb][warp] = dp;
         __syncthreads();
