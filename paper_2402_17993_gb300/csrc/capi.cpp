@@ -505,6 +505,10 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
         if (st) return st;
         c->sec_aoff = p4;
         c->sec_boff = p4 + (size_t(1) << no);
+        c->hsec_sec = c->hsec;
+        c->hsec_sec.aoff = c->sec_aoff;
+        c->hsec_sec.boff = c->sec_boff;
+        c->hf_sec = off[hfa] + off[(size_t(1) << no) + hfb];
         if (c->layout) {
             c->hsec.aoff = c->sec_aoff;
             c->hsec.boff = c->sec_boff;
@@ -546,10 +550,18 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     // before the adjoint starts, so the two share the first array).
     c->adj_compact = !c->layout && c->adj.runs.size() > 1;
     c->fwd_compact = !c->layout && c->fwd.runs.size() > 1;
+    const size_t D = size_t(c->hsec.Da) * size_t(c->hsec.Db);
     if (c->adj_compact || c->fwd_compact) {
-        const size_t D = size_t(c->hsec.Da) * size_t(c->hsec.Db);
         if ((st = dalloc(c, "phic", B * D * amp_bytes(c), &p))) return st;
         if (c->adj_compact && (st = dalloc(c, "lamc", B * D * amp_bytes(c), &p))) return st;
+    }
+    // Full layout, energy and gradient: the forward leaves psi, and the
+    // H-apply sigma, in the compact sector order, where the H-apply and the
+    // adjoint read them (nothing reads the 2^n vectors after a gradient
+    // call; energy-only calls keep psi in the 2^n vector for uccsd_get_state).
+    if (!c->layout) {
+        if ((st = dalloc(c, "psic", B * D * amp_bytes(c), &p))) return st;
+        if ((st = dalloc(c, "sigc", B * D * amp_bytes(c), &p))) return st;
     }
     if ((st = dalloc(c, "cs", B * n_ops * amp_bytes(c), &p))) return st;
     if ((st = dalloc(c, "theta", B * std::max(c->K, 1) * sizeof(double), &p))) return st;
@@ -656,6 +668,11 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     mk.begin(UCCSD_K_FORWARD);
     const size_t Dsec = size_t(c->hsec.Da) * size_t(c->hsec.Db);
     void *phic = (c->fwd_compact || c->adj_compact) ? dptr(c, "phic") : nullptr;
+    // full layout with a gradient: psi and sigma stay in the compact sector
+    // order from the forward's last run to the adjoint's first
+    const bool compact_path = !c->layout && grad;
+    void *psi_h = compact_path ? dptr(c, "psic") : psi;  // psi as the H-apply reads it
+    void *sig_h = compact_path ? dptr(c, "sigc") : sig;
     const int Rf = int(c->fwd.runs.size());
     for (int r = 0; r < Rf; ++r) {
         // full layout, several runs: the runs hand the state to each other in
@@ -670,8 +687,8 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
             in.boff = c->sec_boff;
         }
         SweepOut out;
-        if (c->fwd_compact && r + 1 < Rf) {
-            out.phi = phic;
+        if ((c->fwd_compact && r + 1 < Rf) || (compact_path && r + 1 == Rf)) {
+            out.phi = r + 1 < Rf ? phic : psi_h;
             out.N = Dsec;
             out.aoff = c->sec_aoff;
             out.boff = c->sec_boff;
@@ -688,15 +705,27 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
         c->prof.launches[UCCSD_K_FORWARD]++;
     }
     if (c->fwd.runs.empty()) {
-        if ((e = launch_set_hf<R>(cfg, psi, c->hf_addr)) != cudaSuccess) return cuda_fail(c, e, "hf kernel");
+        LaunchCfg hcfg = cfg;
+        if (compact_path) {  // the compact array holds the last call's state: clear it first
+            hcfg.N = Dsec;
+            e = cudaMemsetAsync(psi_h, 0, size_t(B) * Dsec * amp_bytes(c), stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "state clear");
+        }
+        if ((e = launch_set_hf<R>(hcfg, psi_h, compact_path ? c->hf_sec : c->hf_addr)) != cudaSuccess)
+            return cuda_fail(c, e, "hf kernel");
         ++c->launches;
         c->prof.launches[UCCSD_K_FORWARD]++;
     }
     const DevHam<R> &H = *reinterpret_cast<const DevHam<R> *>(sizeof(R) == 4 ? (const void *)&c->hf32
                                                                              : (const void *)&c->hf64);
     mk.begin(UCCSD_K_HAPPLY);
-    if ((e = launch_happly<R>(cfg, psi, sig, c->LH, H, c->hsec, Epart, grad ? 1 : 0)) != cudaSuccess)
-        return cuda_fail(c, e, "H-apply kernel");
+    {
+        LaunchCfg hcfg = cfg;
+        if (compact_path) hcfg.N = Dsec;
+        if ((e = launch_happly<R>(hcfg, psi_h, sig_h, c->LH, H, compact_path ? c->hsec_sec : c->hsec,
+                                  Epart, grad ? kHApplyStoreSigma : 0)) != cudaSuccess)
+            return cuda_fail(c, e, "H-apply kernel");
+    }
     ++c->launches;
     c->prof.launches[UCCSD_K_HAPPLY]++;
     if (grad) {
@@ -709,10 +738,12 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
         for (int r = R_ - 1; r >= 0; --r) {
             LaunchCfg acfg = cfg;
             SweepArgs in = c->adj_args;
-            void *phi_in = psi, *lam_in = sig;
+            void *phi_in = psi_h, *lam_in = sig_h;
             if (c->adj_compact && r != R_ - 1) {  // read what the previous run handed over
                 phi_in = phic;
                 lam_in = lamc;
+            }
+            if (compact_path) {
                 acfg.N = Dsec;
                 in.aoff = c->sec_aoff;
                 in.boff = c->sec_boff;

@@ -90,6 +90,8 @@ struct uccsd_ctx {
     uccsd::DevHam<double> hf64;
     uccsd::HSector hsec;
     uccsd::HSector hsec_full;  // hsec with full-layout addressing (caller states)
+    uccsd::HSector hsec_sec;   // hsec with the compact sector addressing (any layout)
+    uint32_t hf_sec = 0;       // address of the reference amplitude in the compact order
     // combinatorial rank tables (shared by the sweeps and the H-apply)
     const uint16_t *comb_combos = nullptr, *comb_ranks = nullptr;
     const int32_t *comb_offs = nullptr;
