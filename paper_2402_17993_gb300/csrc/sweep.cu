@@ -849,8 +849,22 @@ struct PendingPart {
 template <typename R>
 __device__ __forceinline__ void flush_pending(const PendingPart<R> &p) {
     if (!p.dst) return;  // uniform over the block
-    const Part<R> ws = part_warp_sum(p.part);
-    if ((threadIdx.x & 31) == 0) *p.dst = flip_sign(part_value(ws), p.neg);
+    if constexpr (sizeof(R) == 4) {
+        // FP32 state: the thread's hi + lo partial as a 64-bit fixed-point
+        // integer (unit 2^-40), summed exactly over the warp: integer sums
+        // are exact and order-free, and cost 2 shuffles and 2 integer adds
+        // per level against 2 shuffles and 8 FP32 operations of a float-float
+        // tree.  A partial is a sum of products of normalised amplitudes and
+        // components of (H - shift) psi, far inside the +-2^23 range.
+        const float2 v = p.part;
+        long long q = __float2ll_rn(v.x * 1099511627776.0f) + __float2ll_rn(v.y * 1099511627776.0f);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if ((threadIdx.x & 31) == 0) *p.dst = flip_sign((double)q * 9.094947017729282e-13, p.neg);
+    } else {
+        const Part<R> ws = part_warp_sum(p.part);
+        if ((threadIdx.x & 31) == 0) *p.dst = flip_sign(part_value(ws), p.neg);
+    }
 }
 
 // One adjoint factor over precomputed pairs: un-rotates phi and lambda and
@@ -898,9 +912,12 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
                 m[k - k0] = tl[e2];
             }
         if (k0 == 0) flush_pending<R>(pend);
-#pragma unroll
-        for (int k = k0; k < k0 + 2 && k < KP; ++k)
-            if (t + k * THREADS < pl.y) one(cur[k], f[k - k0], g[k - k0], l[k - k0], m[k - k0]);
+        if (t + k0 * THREADS < pl.y) one(cur[k0], f[0], g[0], l[0], m[0]);
+        // the second slot behind a warp-uniform branch: warps past the
+        // factor's pairs skip it instead of issuing it predicated off
+        if (k0 + 1 < KP && (int)(t & ~31) + (k0 + 1) * THREADS < pl.y) {
+            if (t + (k0 + 1) * THREADS < pl.y) one(cur[k0 + 1], f[1], g[1], l[1], m[1]);
+        }
     }
     // further pairs: loads issued four at a time
     for (int j0 = t + KP * THREADS; j0 < pl.y; j0 += 4 * THREADS) {
