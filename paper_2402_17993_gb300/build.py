@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libuccsd_gb300.so")
 BUILD = os.path.join(ROOT, "_build", "uccsd")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["jw.cpp", "plan.cpp", "capi.cpp", "trotter.cpp", "tapering.cpp", "kernels.cu", "sweep.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "gate.cu"]
 
 
 def _nvcc() -> str:

@@ -107,6 +107,12 @@ struct uccsd_ctx {
     int opt_m = 0, opt_steps = 0;
     double opt_max_step = 0.0, opt_first = 0.0;
 
+    // gate of the serving loop (uccsd_gate_enqueue): its status word in
+    // mapped pinned memory (1 released, 2 gave up), the event after the gate
+    uint32_t *gate_status = nullptr;
+    cudaEvent_t gate_ev = nullptr;
+    bool gate_pending = false;
+
     // captured evaluation graph
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
