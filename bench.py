@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--no-small", action="store_true",
                     help="skip the 8- and 12-qubit workloads (sweep, VQE)")
     ap.add_argument("--serving-requests", type=int, default=512)
-    ap.add_argument("--serving-fp64-requests", type=int, default=48)
+    ap.add_argument("--serving-fp64-requests", type=int, default=None,
+                    help="requests of the one-at-a-time FP64 arm (default: the same stream "
+                         "as the batched arm)")
     return ap.parse_args()
 
 
@@ -769,28 +771,72 @@ def scaleup_26q(uc, device, dev_pk):
 def serving_stream(uc, device, n_req, n_req_fp64):
     """FMO fragment stream (60% monomers at 8-12 qubits, 40% dimers at 16-18
     qubits, 40 fixed-step L-BFGS evaluations per solve): capacity of the
-    batched FP32 server (closed loop), latency percentiles at 0.5x, 0.8x and 1.2x that
-    capacity with Poisson arrivals (seed 7), and the one-request-at-a-time
-    FP64 form on the first requests of the same stream."""
+    batched FP32 server (closed loop), latency percentiles at 0.5x, 0.8x and
+    1.2x that capacity with Poisson arrivals (seed 7), and the
+    one-request-at-a-time FP64 form on the same requests, with the final
+    energy of every fragment compared between the two forms."""
     from paper_2402_17993_gb300.serving import FragmentServer, Request, capacity_rate
     frags = synth.stream_fragments(n_req, 7)
     reqs = [Request(d["r"], d["t_unit"], d["n_orb"], d["n_alpha"], d["n_beta"], d["h"], d["eri"],
                     d["e_core"]) for d in frags]
+    n64 = n_req if n_req_fp64 is None else min(n_req_fp64, n_req)
     out = {}
     srv = FragmentServer(precision=uc.FP32_STATE, device=device, max_active=64)
     srv.run(reqs[:64])  # warm the context pool and graph paths
-    _, cap = srv.run(reqs)
+    res32, cap = srv.run(reqs, keep_theta=True)
     rate = capacity_rate(cap)
     out["batched_fp32"] = {"closed_loop": cap}
     for f in (0.5, 0.8, 1.2):
         _, op = srv.run(reqs, rate=f * rate)
         out["batched_fp32"][f"open_loop_{f}x"] = dict(op, rate_req_per_s=f * rate)
+    # the same arrivals with the next 8 requests prepared ahead of their
+    # arrival, each solve waiting behind a device gate that the serving
+    # thread releases at the arrival (instead of being set up and launched
+    # then)
+    srv.lookahead = 8
+    for f in (0.5, 0.8):
+        _, op = srv.run(reqs, rate=f * rate)
+        out["batched_fp32"][f"open_loop_{f}x_gated_lookahead8"] = dict(op, rate_req_per_s=f * rate)
+    srv.lookahead = 0
     srv.close()
     one = FragmentServer(precision=uc.FP64, device=device, max_active=1, n_streams=1,
                          use_graphs=False)
-    _, st1 = one.run(reqs[:n_req_fp64])
+    res64, st1 = one.run(reqs[:n64])
     one.close()
-    out["one_at_a_time_fp64"] = dict(st1, note=f"first {n_req_fp64} requests of the stream")
+    e32 = {r.r: r.energy for r in res32}
+    dE = np.array([abs(e32[r.r] - r.energy) for r in res64])
+    out["one_at_a_time_fp64"] = dict(st1, note=f"the first {n64} requests of the same stream "
+                                               f"(closed loop)")
+    # evaluation precision: both forms at the same amplitudes (each
+    # fragment's final theta of the batched run)
+    by_r = {q.r: q for q in reqs}
+    ctxs = {}
+    same = []
+    for r in res32[:n64]:
+        q = by_r[r.r]
+        key = (q.n_orb, q.n_alpha, q.n_beta)
+        if key not in ctxs:
+            ctxs[key] = [uc.Context(device, p) for p in (uc.FP32_STATE, uc.FP64)]
+        es = []
+        for c in ctxs[key]:
+            c.set_hamiltonian(q.n_orb, q.h, q.eri, q.e_core).set_reference(q.n_alpha, q.n_beta)
+            c.set_excitations(uc.build_uccsd_list(q.n_orb, q.n_alpha, q.n_beta))
+            es.append(c.energy(r.theta))
+        same.append(abs(es[0] - es[1]))
+    for cs in ctxs.values():
+        for c in cs:
+            c.close()
+    same = np.array(same)
+    out["fp32_batched_vs_fp64_one_at_a_time"] = {
+        "fragments": int(len(dE)),
+        "same_theta_max_abs_dE": float(same.max()),
+        "same_theta_median_abs_dE": float(np.median(same)),
+        "final_max_abs_dE": float(dE.max()), "final_median_abs_dE": float(np.median(dE)),
+        "final_within_1e-5": int(np.sum(dE <= 1e-5)),
+        "note": "same_theta: both precisions evaluated at each fragment's final amplitudes "
+                "(the evaluation error); final: the last energy of each form's own 40-step "
+                "fixed-step L-BFGS run (device optimiser for the batched form, host optimiser "
+                "for the other), where the two trajectories may separate"}
     return out
 
 

@@ -17,7 +17,15 @@ qubits, each with its own integrals) and share one GPU:
   fragments overlap on the device, and the host only admits arrivals into
   freed slots and collects finished solves;
 * each solve runs a fixed number of optimiser steps (one evaluation each);
-  its latency is arrival -> last step done.
+  its latency is arrival -> last step done;
+* preparation off the serving thread: the host work of an admission (the
+  Jordan-Wigner compile and tables, the sweep plans, the graph capture and
+  the enqueue of the solve) runs on a pool of worker threads, each on the
+  fragment's own context and stream.  A context belongs to one thread at a
+  time: the pool hands it to a worker, the worker hands the prepared
+  fragment to the serving thread, and the serving thread returns the
+  context to the pool only after it has read the results (the library's
+  contexts are independent of each other, but not thread-safe each).
 
 The plain form (max_active = 1, use_graphs = False) steps one request at a
 time from the host: evaluation, download, host L-BFGS update.
@@ -27,9 +35,12 @@ does not depend on what else is in flight (checked by the GPU tests).
 """
 from __future__ import annotations
 
+import bisect
 import functools
 import math
+import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -97,8 +108,10 @@ def footprint_bytes(n_orb: int, n_alpha: int, n_beta: int, precision: int,
     K = len(build_uccsd_list(n_orb, n_alpha, n_beta))
     tiles = max(1, N >> 10)
     tables = 200 * (n_orb ** 4) + (4 << 20)
-    sector = math.comb(n_orb, n_alpha) * math.comb(n_orb, n_beta)  # adjoint hand-over vectors
-    own = 2 * N * A + 2 * sector * A + K * tiles * 8 + K * 256 + tables
+    # compact sector vectors: psi and sigma between the kernels, phi and
+    # lambda between the adjoint's runs
+    sector = math.comb(n_orb, n_alpha) * math.comb(n_orb, n_beta)
+    own = 2 * N * A + 4 * sector * A + K * tiles * 8 + K * 256 + tables
     return own + (list_bytes(n_orb, n_alpha, n_beta) if lists else 0)
 
 
@@ -156,7 +169,7 @@ class _DevSlot:
     """A fragment whose whole solve is enqueued on its stream at admission:
     `steps` replays of one captured graph (evaluation + device L-BFGS step)."""
 
-    def __init__(self, req, ctx, stream, t_admit, steps):
+    def __init__(self, req, ctx, stream, t_admit, steps, gate_flag=None, gate_timeout_s=5.0):
         import torch
         self.req = req
         self.ctx = ctx
@@ -164,6 +177,7 @@ class _DevSlot:
         self.K = ctx.K
         self.t_admit = t_admit
         self.steps = steps
+        self.gate_flag = gate_flag
         dev = torch.device("cuda", ctx.device)
         k = max(self.K, 1)
         ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=steps)
@@ -172,10 +186,23 @@ class _DevSlot:
             buf = torch.zeros(2 * k + 1, dtype=torch.float64, device=dev)  # theta | grad | E
             self.th_dev, self.g_dev, self.E_dev = buf[:k], buf[k:2 * k], buf[2 * k:]
             ctx.capture_vqe_step(self.th_dev, self.E_dev, self.g_dev, stream)
+            if gate_flag is not None:
+                # prepared ahead of its arrival: the solve waits on the device
+                # until the serving thread releases the flag
+                ctx.gate(gate_flag, 1, gate_timeout_s, stream)
             for _ in range(steps):
                 ctx.replay(stream)  # evaluation + device L-BFGS step
             self.done = torch.cuda.Event()
             self.done.record(stream)
+
+    def release(self):
+        self.gate_flag[0] = 1
+
+    def check_gate(self):
+        """Raise if the gate gave up before its release (the solve then ran
+        early and its timing is void)."""
+        if self.gate_flag is not None:
+            self.ctx.gate_status(wait=True)
 
     def result(self, keep_theta):
         energies = [float(e) for e in self.ctx.opt_history(self.steps)]
@@ -190,7 +217,7 @@ class FragmentServer:
     use_graphs = False gives the plain one-request-at-a-time form."""
 
     def __init__(self, precision=FP32_STATE, device=0, hbm_budget=8 << 30, max_active=48,
-                 n_streams=None, steps=40, use_graphs=True):
+                 n_streams=None, steps=40, use_graphs=True, prep_workers=4, lookahead=0):
         import torch
         self.precision = precision
         self.device = device
@@ -199,10 +226,18 @@ class FragmentServer:
         self.steps = steps
         self.use_graphs = use_graphs
         n_streams = max_active if n_streams is None else n_streams
-        self.streams = [torch.cuda.Stream(device=device) for _ in range(n_streams)]
+        self.streams = _distinct_streams(device, n_streams)
         self.pool = {}
+        self._pool_lock = threading.Lock()
         # pair lists held for each shape class seen (one shared copy per class)
         self.shared = {}
+        # host threads that prepare admitted fragments (0: the serving thread)
+        self.prep_workers = prep_workers
+        self._exec = (ThreadPoolExecutor(prep_workers, thread_name_prefix="uccsd-prep")
+                      if prep_workers > 0 and use_graphs else None)
+        # requests prepared before their arrival, each behind a device gate
+        # that the serving thread releases at the arrival (open-loop runs)
+        self.lookahead = lookahead
 
     def _context(self, req, used, stream=None):
         """A context for the request: a recycled one of the same shape class
@@ -211,8 +246,9 @@ class FragmentServer:
         set-up transfers are enqueued on it and nothing waits for them, so
         the host never stalls behind another fragment's solve."""
         key = (req.n_orb, req.n_alpha, req.n_beta)
-        pool = self.pool.get(key)
-        ctx = pool.pop() if pool else None
+        with self._pool_lock:
+            pool = self.pool.get(key)
+            ctx = pool.pop() if pool else None
         if ctx is None:
             ctx = Context(self.device, self.precision, max(1, self.hbm_budget - used))
         ctx.set_setup_stream(stream)
@@ -229,9 +265,25 @@ class FragmentServer:
         return need, (0 if key in self.shared else list_bytes(*key))
 
     def _release(self, req, ctx):
-        self.pool.setdefault((req.n_orb, req.n_alpha, req.n_beta), []).append(ctx)
+        with self._pool_lock:
+            self.pool.setdefault((req.n_orb, req.n_alpha, req.n_beta), []).append(ctx)
+
+    def _prepare(self, q, used, stream, t0, gate_flag=None):
+        """Host work of one admission (on a worker thread or the serving
+        thread): the context's set-up on the fragment's stream, then the
+        capture of its evaluation and optimiser step and the enqueue of the
+        whole solve (behind a gate when it is prepared ahead of arrival)."""
+        import torch
+        torch.cuda.set_device(self.device)
+        ctx = self._context(q, used, stream)
+        slot = _DevSlot(q, ctx, stream, time.perf_counter() - t0, self.steps, gate_flag)
+        slot.dev_bytes = ctx.info()["device_bytes"]
+        return slot
 
     def close(self):
+        if self._exec is not None:
+            self._exec.shutdown(wait=True)
+            self._exec = None
         for lst in self.pool.values():
             for ctx in lst:
                 ctx.close()
@@ -257,51 +309,83 @@ class FragmentServer:
             "peak_hbm_device_bytes": int(peak_dev),
             "precision": "fp32" if self.precision == FP32_STATE else "fp64",
             "max_active": self.max_active, "graphs": self.use_graphs,
+            "streams": len(self.streams),
         }
 
     def _run_device(self, requests, rate, keep_theta):
-        """Arrived requests are admitted in arrival order while slots and the
-        HBM budget allow, one per pass of the loop between completion checks:
-        the context is prepared with its set-up transfers enqueued on a free
-        stream (host work, no host waits), then the evaluation graph is
-        captured and the whole solve enqueued behind them on that stream."""
+        """Arrived requests are admitted in arrival order while slots, streams
+        and the HBM budget allow; each admission reserves its budget and a
+        free stream on the serving thread and hands the host work (context
+        set-up, capture, enqueue of the whole solve on that stream) to a
+        worker thread.  The serving thread collects prepared fragments and
+        finished solves."""
+        import torch
         reqs = sorted(requests, key=lambda q: q.t_unit)
         arrive = [0.0 if rate is None else q.t_unit / rate for q in reqs]
         t0 = time.perf_counter()
         pending = 0
         active: list[_DevSlot] = []
+        preparing = []  # (future, request, reserved bytes, arrival time)
+        gated = []      # (arrival time, gate flag) not yet released, in arrival order
         free_streams = list(self.streams)
         results: list[Result] = []
         used = peak_used = sum(self.shared.values())
         dev_used = peak_dev = 0
         n_evals = 0
-        while pending < len(reqs) or active:
+        while pending < len(reqs) or active or preparing:
             now = time.perf_counter() - t0
             progressed = False
-            if (pending < len(reqs) and arrive[pending] <= now
-                    and len(active) < self.max_active and free_streams):
+            # requests up to `lookahead` past the arrived ones are prepared
+            # early, behind a gate
+            n_arrived = bisect.bisect_right(arrive, now)
+            while (pending < len(reqs) and pending < n_arrived + (self.lookahead if rate else 0)
+                   and len(active) + len(preparing) < self.max_active and free_streams):
                 q = reqs[pending]
                 need, extra = self._need(q)
-                if used + need + extra <= self.hbm_budget or not active:
-                    st = free_streams.pop()
-                    ctx = self._context(q, used, st)
-                    slot = _DevSlot(q, ctx, st, time.perf_counter() - t0, self.steps)
+                if used + need + extra > self.hbm_budget and (active or preparing):
+                    break
+                st = free_streams.pop()
+                if extra:
+                    self.shared[(q.n_orb, q.n_alpha, q.n_beta)] = extra
+                before = used  # the context's own budget: what the others leave
+                used += need + extra
+                peak_used = max(peak_used, used)
+                flag = None
+                if arrive[pending] > now:
+                    flag = torch.zeros(1, dtype=torch.int32).pin_memory()
+                    gated.append((arrive[pending], flag))
+                if self._exec is not None:
+                    fut = self._exec.submit(self._prepare, q, before, st, t0, flag)
+                else:
+                    fut = _Done(self._prepare(q, before, st, t0, flag))
+                preparing.append((fut, q, need, arrive[pending]))
+                pending += 1
+                progressed = True
+                if self._exec is None:
+                    break  # one admission per pass when the serving thread prepares
+            # release the gates of the requests that have arrived
+            now = time.perf_counter() - t0
+            while gated and gated[0][0] <= now:
+                gated.pop(0)[1][0] = 1
+                progressed = True
+            still_prep = []
+            for fut, q, need, t_arr in preparing:
+                if fut.done():
+                    slot = fut.result()
                     slot.reserved = need
-                    slot.dev_bytes = ctx.info()["device_bytes"]
-                    slot.t_arrive = arrive[pending]
-                    if extra:
-                        self.shared[(q.n_orb, q.n_alpha, q.n_beta)] = extra
-                    used += need + extra
+                    slot.t_arrive = t_arr
                     dev_used += slot.dev_bytes
-                    peak_used = max(peak_used, used)
                     peak_dev = max(peak_dev, dev_used)
                     active.append(slot)
-                    pending += 1
                     progressed = True
+                else:
+                    still_prep.append((fut, q, need, t_arr))
+            preparing = still_prep
             still = []
             for s in active:
                 if s.done.query():
                     t_done = time.perf_counter() - t0
+                    s.check_gate()
                     energies, theta = s.result(keep_theta)
                     results.append(Result(s.req.r, 2 * s.req.n_orb, s.t_arrive, s.t_admit,
                                           t_done, energies[-1], energies, theta))
@@ -316,14 +400,16 @@ class FragmentServer:
             active = still
             if not progressed:
                 wait = 50e-6
-                if pending < len(reqs) and not active:
+                if pending < len(reqs) and not active and not preparing and not gated:
                     wait = max(0.0, min(arrive[pending] - (time.perf_counter() - t0), 0.01))
                 time.sleep(wait)
         makespan = time.perf_counter() - t0
         stats = self._stats(results, n_evals, makespan, [], peak_used, peak_dev)
+        stats["lookahead"] = self.lookahead if rate else 0
         # time average of the number of admitted, unfinished fragments
         stats["mean_active"] = (sum(r.t_done - r.t_admit for r in results) / makespan
                                 if makespan > 0 else 0.0)
+        stats["prep_workers"] = self.prep_workers if self._exec is not None else 0
         return sorted(results, key=lambda r: r.r), stats
 
     def _run_host(self, requests, rate, keep_theta):
@@ -391,10 +477,88 @@ class FragmentServer:
                 self._stats(results, n_evals, makespan, active_hist, peak_used, peak_dev))
 
 
+def _distinct_streams(device, n):
+    """Up to n CUDA streams with distinct handles.  torch.cuda.Stream() draws
+    from a fixed pool (32 streams per priority), so asking for more repeats
+    handles; two fragments on one handle would share a stream (their solves
+    serialise), and a capture on it by one preparing thread would collide
+    with another thread's launches.  All at the default priority, so no
+    fragment is preferred: the server then runs at most as many fragments at
+    once as there are distinct streams."""
+    import torch
+    seen, out = set(), []
+    for _ in range(2 * n + 64):
+        st = torch.cuda.Stream(device=device)
+        if st.cuda_stream not in seen:
+            seen.add(st.cuda_stream)
+            out.append(st)
+            if len(out) == n:
+                break
+    return out
+
+
+class _Done:
+    """A finished result in the shape of a future (preparation on the
+    serving thread)."""
+
+    def __init__(self, value):
+        self.value = value
+
+    def done(self):
+        return True
+
+    def result(self):
+        return self.value
+
+
 def fmo2_sum(monomer_E, dimer_E, n_frag):
     """Two-body FMO total (Eq. 1): sum over dimers minus (N_f - 2) times the
     sum over monomers."""
     return float(np.sum(dimer_E) - (n_frag - 2) * np.sum(monomer_E))
+
+
+def fmo_fragment_integrals(h, eri, frag_orbs, frag_nocc, members):
+    """Integrals of a monomer (members = (I,)) or dimer ((I, J)) of a
+    supersystem in localised orbitals (Section 2.1): the members' orbitals,
+    ordered [occupied of each member, then virtual of each member] so that
+    the reference determinant is the lowest orbitals, with the one-electron
+    part embedded in the mean field of the other fragments' closed-shell
+    reference determinants,
+        h_pq + sum_{j occupied in the environment} (2 (pq|jj) - (pj|jq)).
+    Returns (h, eri, n_occ) with n_occ = occupied spatial orbitals."""
+    occ = [o for f in members for o in frag_orbs[f][:frag_nocc[f]]]
+    vir = [o for f in members for o in frag_orbs[f][frag_nocc[f]:]]
+    sel = np.array(occ + vir)
+    env = np.array([o for f in range(len(frag_orbs)) if f not in members
+                    for o in frag_orbs[f][:frag_nocc[f]]], dtype=int)
+    hs = h[np.ix_(sel, sel)].copy()
+    if env.size:
+        coul = eri[np.ix_(sel, sel, env, env)]
+        exch = eri[np.ix_(sel, env, env, sel)]
+        hs += 2.0 * np.einsum("pqjj->pq", coul) - np.einsum("pjjq->pq", exch)
+    es = np.ascontiguousarray(eri[np.ix_(sel, sel, sel, sel)])
+    return np.ascontiguousarray(0.5 * (hs + hs.T)), es, len(occ)
+
+
+def fmo2_requests(h, eri, frag_orbs, frag_nocc):
+    """Requests of a two-body FMO job: every monomer and every dimer of the
+    supersystem (Eq. 1 needs E_I and E_IJ).  Returns (requests, keys) with
+    keys[i] = the members of request i."""
+    n_frag = len(frag_orbs)
+    keys = [(i,) for i in range(n_frag)] + [(i, j) for i in range(n_frag)
+                                             for j in range(i + 1, n_frag)]
+    reqs = []
+    for r, key in enumerate(keys):
+        hf, ef, nocc = fmo_fragment_integrals(h, eri, frag_orbs, frag_nocc, key)
+        reqs.append(Request(r, 0.0, hf.shape[0], nocc, nocc, hf, ef, 0.0))
+    return reqs, keys
+
+
+def fmo2_total(energies, keys, n_frag):
+    """Eq. 1 from the energies of fmo2_requests' fragments (same order)."""
+    mono = [e for e, k in zip(energies, keys) if len(k) == 1]
+    dim = [e for e, k in zip(energies, keys) if len(k) == 2]
+    return fmo2_sum(mono, dim, n_frag)
 
 
 def capacity_rate(stats) -> float:

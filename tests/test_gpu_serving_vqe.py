@@ -193,3 +193,67 @@ def test_captured_vqe_step_is_the_eager_step(uc):
         ctx.close()
     assert len(res[0][1]) == 6
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_contexts_prepared_on_many_threads_are_independent(uc):
+    # distinct contexts on distinct host threads: set-up (Jordan-Wigner
+    # compile, plans, shared pair lists), capture and evaluation run
+    # concurrently and give bitwise the results of one thread doing the same
+    import threading
+
+    import torch
+    reqs = _requests(16, seed=5)
+
+    def solve(q, out, i):
+        torch.cuda.set_device(0)
+        ctx = uc.Context(0, 1)
+        ctx.set_hamiltonian(q.n_orb, q.h, q.eri, q.e_core)
+        ctx.set_reference(q.n_alpha, q.n_beta)
+        ctx.set_excitations(uc.build_uccsd_list(q.n_orb, q.n_alpha, q.n_beta))
+        th = synth.theta_normal(ctx.K, 0.05, 300 + i)
+        out[i] = [ctx.energy_grad(th) for _ in range(3)]
+        ctx.close()
+
+    serial = {}
+    for i, q in enumerate(reqs):
+        solve(q, serial, i)
+    conc = {}
+    for _ in range(3):
+        ths = [threading.Thread(target=solve, args=(q, conc, i)) for i, q in enumerate(reqs)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for i in range(len(reqs)):
+            for (e1, g1), (e2, g2) in zip(serial[i], conc[i]):
+                assert e1 == e2 and np.array_equal(g1, g2), i
+
+
+def test_threaded_preparation_gives_the_serial_results(uc):
+    from paper_2402_17993_gb300.serving import FragmentServer
+    reqs = _requests(20, seed=13)
+    res = {}
+    for workers in (0, 8):
+        srv = FragmentServer(precision=1, steps=5, max_active=16, prep_workers=workers)
+        res[workers], stats = srv.run(reqs, keep_theta=True)
+        assert stats["requests"] == 20 and stats["prep_workers"] == workers
+        srv.close()
+    for a, b in zip(res[0], res[8]):
+        assert a.r == b.r and a.energies == b.energies and np.array_equal(a.theta, b.theta)
+
+
+def test_gated_lookahead_gives_the_same_solves(uc):
+    # open loop: the next requests are prepared before they arrive and wait
+    # behind device gates released at their arrival; every solve is bitwise
+    # the one prepared at arrival
+    from paper_2402_17993_gb300.serving import FragmentServer
+    reqs = _requests(12, seed=17)
+    srv = FragmentServer(precision=1, steps=4, max_active=12)
+    plain, _ = srv.run(reqs, rate=400.0, keep_theta=True)
+    srv.lookahead = 6
+    gated, stats = srv.run(reqs, rate=400.0, keep_theta=True)
+    assert stats["lookahead"] == 6 and stats["requests"] == 12
+    for a, b in zip(plain, gated):
+        assert a.r == b.r and a.energies == b.energies and np.array_equal(a.theta, b.theta)
+        assert b.t_done >= b.t_arrive
+    srv.close()
