@@ -77,8 +77,14 @@ typedef enum {
 
 typedef enum {
     UCCSD_LAYOUT_FULL = 0,   /* each slot is the full 2^n amplitude vector (index = occupation bits) */
-    UCCSD_LAYOUT_SECTOR = 1  /* each slot holds only the (n_alpha, n_beta) sector: C(n_orb, n_alpha) x
+    UCCSD_LAYOUT_SECTOR = 1, /* each slot holds only the (n_alpha, n_beta) sector: C(n_orb, n_alpha) x
                                 C(n_orb, n_beta) amplitudes, alpha-string rank major, strings ascending */
+    UCCSD_LAYOUT_SCBK = 2    /* each slot is the 2^(n-2) vector of the symmetry-conserving
+                                Bravyi-Kitaev encoding with its two parity qubits tapered off
+                                (the paper's qubit counts, Section 2.3), in the qubit order of
+                                uccsd_pauli_terms_scbk: the determinant (alpha string sa, beta
+                                string sb) sits at the tapered Bravyi-Kitaev image of its
+                                up-then-down occupation vector, which splits as f(sa) + g(sb) */
 } uccsd_layout;
 
 typedef struct {
@@ -150,9 +156,13 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *ctx, int n_orb, const double *h,
  * kernel touches only those.  UCCSD_LAYOUT_FULL keeps them at their place in
  * the 2^n vector (the rest stays zero); UCCSD_LAYOUT_SECTOR stores them as a
  * dense C(n_orb, n_alpha) x C(n_orb, n_beta) array (4.4% of 2^n at 26
- * qubits), with identical arithmetic in the same order, so energies and
- * gradients are bitwise the same in both layouts.  uccsd_get_state returns
- * the 2^n vector in both.  Must come before uccsd_set_reference (after
+ * qubits); UCCSD_LAYOUT_SCBK keeps them at their place in the 2^(n-2)
+ * vector of the tapered symmetry-conserving Bravyi-Kitaev encoding (the
+ * paper's qubit counts: 16 qubits for an 18-qubit Jordan-Wigner fragment).
+ * The arithmetic and its order are identical, so energies and gradients are
+ * bitwise the same in all three layouts.  uccsd_get_state returns the 2^n
+ * vector in the first two and the tapered vector in the third.  Must come
+ * before uccsd_set_reference (after
  * uccsd_set_hamiltonian, which clears the reference, it may be called again);
  * otherwise UCCSD_ERR_STATE.  Unknown layout: UCCSD_ERR_ARG. */
 uccsd_status uccsd_set_layout(uccsd_ctx *ctx, int layout);
@@ -228,7 +238,10 @@ uccsd_status uccsd_replay(uccsd_ctx *ctx, void *stream);
 
 /* Copy the state vector of slot `slot` after the last uccsd_energy or
  * energies-only batch call to host memory as 2*2^n interleaved (re, im)
- * doubles (UCCSD_FP32_STATE: re = hi + lo, im = 0).  len must be >= 2*2^n.  Synchronises the context's last stream.
+ * doubles (UCCSD_FP32_STATE: re = hi + lo, im = 0); in UCCSD_LAYOUT_SCBK
+ * the 2*2^(n-2) doubles of the tapered encoding, in the phase convention of
+ * its up-then-down orbital order (the amplitudes that
+ * uccsd_pauli_terms_scbk's Hamiltonian acts on).  len must be >= 2*2^n.  Synchronises the context's last stream.
  * After a gradient call the slot's content is unspecified (the adjoint
  * sweep may leave it partly swept back). */
 uccsd_status uccsd_get_state(uccsd_ctx *ctx, int slot, double *out_re_im, size_t len);
@@ -391,6 +404,37 @@ uccsd_status uccsd_capture_vqe_step(uccsd_ctx *ctx, double *theta_dev, double *E
  * cap) doubles); *n_out = steps recorded.  Synchronises the last stream the
  * optimiser ran on. */
 uccsd_status uccsd_opt_history(uccsd_ctx *ctx, double *E, int cap, int *n_out);
+
+/* ---- Bounded device wait of the serving loop (no counterpart in the paper,
+ *      whose fragment jobs ran one after another; Section 3.1) ---- */
+
+/* Enqueue on `stream` (not the default stream) a gate: a one-thread kernel
+ * that waits until *flag >= target and then lets the work enqueued behind
+ * it on the stream run.  A server prepares a fragment and enqueues its solve
+ * behind a gate before the request is due, then releases the flag at the
+ * request's arrival; no host launch is on that path.
+ *   flag        device-readable uint32 written by the host: pinned host
+ *               memory (readable by the device at the same address under
+ *               unified addressing) or device memory that a copy on another
+ *               stream writes.  It must not be written by a kernel that is
+ *               itself waiting.
+ *   timeout_ns  the gate's time limit, in (0, 10 s].  The gate polls about
+ *               every microsecond; when the limit passes (or an iteration
+ *               cap derived from it, should the GPU's timer stall) it gives
+ *               up, records that, and returns.  The work behind it then runs
+ *               anyway; uccsd_gate_status tells the caller to discard it.
+ * One gate per context at a time: UCCSD_ERR_STATE while the previous one is
+ * still waiting.  Errors: UCCSD_ERR_ARG for a null flag or stream or a
+ * limit out of range, UCCSD_ERR_CUDA if the launch fails. */
+uccsd_status uccsd_gate_enqueue(uccsd_ctx *ctx, const uint32_t *flag, uint32_t target,
+                                uint64_t timeout_ns, void *stream);
+
+/* State of the context's last gate.  wait != 0 blocks until the gate kernel
+ * has finished (never longer than its time limit); wait = 0 only looks.
+ * *released = 1 once the flag released it (UCCSD_OK); *released = 0 with
+ * UCCSD_OK while it is still waiting; UCCSD_ERR_TIMEOUT if it gave up.
+ * UCCSD_ERR_STATE without a gate. */
+uccsd_status uccsd_gate_status(uccsd_ctx *ctx, int wait, int *released);
 
 /* ---- Trotter-schedule helpers (Section 2.3 ordering; Section 3.2 extrapolation) ---- */
 

@@ -21,6 +21,7 @@ FP64 = 0
 FP32_STATE = 1
 LAYOUT_FULL = 0
 LAYOUT_SECTOR = 1
+LAYOUT_SCBK = 2
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "device out of memory", 3: "CUDA error",
           4: "invalid call order or failed context", 5: "device wait timed out",
@@ -37,7 +38,7 @@ EXPORTS = [
     "uccsd_trotter_extrapolate", "uccsd_energy_trotter_free", "uccsd_energy_grad_trotter_free",
     "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
     "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
-    "uccsd_energy_grad_batched", "uccsd_plan_pairs",
+    "uccsd_energy_grad_batched", "uccsd_plan_pairs", "uccsd_gate_enqueue", "uccsd_gate_status",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -126,6 +127,8 @@ def lib():
         L.uccsd_trotter_extrapolate.argtypes = [ip, ctypes.POINTER(ctypes.c_int), f64p, f64p]
         L.uccsd_plan_pairs.argtypes = [ip, ip, ip, i32p, ip, ip, ip, i32p, ip,
                                        ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_gate_enqueue.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp]
+        L.uccsd_gate_status.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -385,7 +388,10 @@ class Context:
         self._check(self._L.uccsd_replay(self._c, _stream_ptr(stream)), "replay")
 
     def state(self, slot=0):
-        N = 1 << self.n_qubits
+        """The state vector of `slot`: 2^n amplitudes, or the 2^(n-2) of the
+        tapered encoding in LAYOUT_SCBK."""
+        n = self.n_qubits - (2 if self.info()["layout"] == LAYOUT_SCBK else 0)
+        N = 1 << n
         out = np.zeros(2 * N)
         self._check(self._L.uccsd_get_state(self._c, slot, _f64p(out), out.size), "get_state")
         return out.view(np.complex128)
@@ -433,6 +439,22 @@ class Context:
         """One asynchronous optimiser step on device buffers (raw pointers)."""
         self._check(self._L.uccsd_opt_step(self._c, theta_ptr, E_ptr, grad_ptr,
                                            _stream_ptr(stream)), "opt_step")
+
+    def gate(self, flag, target, timeout_s, stream):
+        """Hold the work enqueued after this call on `stream` until the uint32
+        at `flag` (a pinned CPU tensor, or a CUDA tensor) reaches `target`,
+        at most `timeout_s` seconds (uccsd_gate_enqueue)."""
+        self._check(self._L.uccsd_gate_enqueue(self._c, ctypes.c_void_p(flag.data_ptr()),
+                                               int(target), int(timeout_s * 1e9),
+                                               _stream_ptr(stream)), "gate_enqueue")
+
+    def gate_status(self, wait=True):
+        """True once the gate was released, False while it waits; raises
+        UCCSDError (code UCCSD_ERR_TIMEOUT = 5) if its time limit passed."""
+        r = ctypes.c_int(0)
+        self._check(self._L.uccsd_gate_status(self._c, 1 if wait else 0, ctypes.byref(r)),
+                    "gate_status")
+        return bool(r.value)
 
     def opt_history(self, cap=4096):
         E = np.zeros(max(cap, 1))

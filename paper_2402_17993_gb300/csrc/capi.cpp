@@ -203,7 +203,7 @@ cudaError_t setup_sync(uccsd_ctx *c) {
 
 // Copy `nb` host bytes into the pinned staging area; *out is the staged copy.
 // The area is reused from its start once the copies staged earlier (all on
-// the current set-up stream, before the last recorded stage_ev) are done.
+// the context's own stream, before the last recorded stage_ev) are done.
 uccsd_status stage_bytes(uccsd_ctx *c, const void *src, size_t nb, const void **out) {
     const size_t need = (nb + 255) & ~size_t(255);
     cudaError_t e = cudaSuccess;
@@ -240,10 +240,14 @@ uccsd_status upload(uccsd_ctx *c, const std::string &name, const std::vector<T> 
         const size_t nb = sizeof(T) * v.size();
         cudaError_t e;
         if (c->setup_async) {
+            // the copy runs on the context's own stream and the caller's
+            // stream waits for it: the staging event is only ever recorded
+            // on a stream that no other thread captures or shares
             const void *src = nullptr;
             if ((st = stage_bytes(c, v.data(), nb, &src))) return st;
-            e = cudaMemcpyAsync(p, src, nb, cudaMemcpyHostToDevice, c->setup);
-            if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev, c->setup);
+            e = cudaMemcpyAsync(p, src, nb, cudaMemcpyHostToDevice, c->own_setup);
+            if (e == cudaSuccess) e = cudaEventRecord(c->stage_ev, c->own_setup);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(c->setup, c->stage_ev, 0);
         } else {
             e = cudaMemcpyAsync(p, v.data(), nb, cudaMemcpyHostToDevice, c->setup);
             if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
@@ -509,18 +513,32 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
         c->hsec_sec.aoff = c->sec_aoff;
         c->hsec_sec.boff = c->sec_boff;
         c->hf_sec = off[hfa] + off[(size_t(1) << no) + hfb];
-        if (c->layout) {
+        if (c->layout == UCCSD_LAYOUT_SECTOR) {
             c->hsec.aoff = c->sec_aoff;
             c->hsec.boff = c->sec_boff;
             c->hf_addr = off[hfa] + off[(size_t(1) << no) + hfb];
         }
+    }
+    if (c->layout == UCCSD_LAYOUT_SCBK) {
+        // tapered Bravyi-Kitaev positions of the sector determinants
+        std::vector<uint32_t> ta, tb;
+        scbk_addresses(no, &ta, &tb);
+        std::vector<uint32_t> off(ta);
+        off.insert(off.end(), tb.begin(), tb.end());
+        uint32_t *p4;
+        uccsd_status st = upload(c, "scbkoff", off, &p4);
+        if (st) return st;
+        c->hsec.aoff = p4;
+        c->hsec.boff = p4 + (size_t(1) << no);
+        c->hf_addr = ta[hfa] + tb[hfb];
     }
     return UCCSD_OK;
 }
 
 // Amplitudes per slot: 2^n in the full layout, Da * Db in the sector layout.
 size_t state_elems(const uccsd_ctx *c) {
-    return c->layout ? size_t(c->hsec.Da) * size_t(c->hsec.Db) : size_t(1) << c->n;
+    if (c->layout == UCCSD_LAYOUT_SECTOR) return size_t(c->hsec.Da) * size_t(c->hsec.Db);
+    return size_t(1) << (c->layout == UCCSD_LAYOUT_SCBK ? c->n - 2 : c->n);
 }
 size_t amp_bytes(const uccsd_ctx *c) { return c->prec ? 8 : 16; }
 int n_tiles_h(const uccsd_ctx *c) { return c->hsec.Da * c->hsec.ncb; }
@@ -548,8 +566,9 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     // entries of its tiles before the next one reads them, so no clearing).
     // The forward's runs hand the state on the same way (the forward is done
     // before the adjoint starts, so the two share the first array).
-    c->adj_compact = !c->layout && c->adj.runs.size() > 1;
-    c->fwd_compact = !c->layout && c->fwd.runs.size() > 1;
+    const bool vec = c->layout != UCCSD_LAYOUT_SECTOR;  // a basis vector per slot (2^n or 2^(n-2))
+    c->adj_compact = vec && c->adj.runs.size() > 1;
+    c->fwd_compact = vec && c->fwd.runs.size() > 1;
     const size_t D = size_t(c->hsec.Da) * size_t(c->hsec.Db);
     if (c->adj_compact || c->fwd_compact) {
         if ((st = dalloc(c, "phic", B * D * amp_bytes(c), &p))) return st;
@@ -559,7 +578,7 @@ uccsd_status alloc_slots(uccsd_ctx *c) {
     // H-apply sigma, in the compact sector order, where the H-apply and the
     // adjoint read them (nothing reads the 2^n vectors after a gradient
     // call; energy-only calls keep psi in the 2^n vector for uccsd_get_state).
-    if (!c->layout) {
+    if (vec) {
         if ((st = dalloc(c, "psic", B * D * amp_bytes(c), &p))) return st;
         if ((st = dalloc(c, "sigc", B * D * amp_bytes(c), &p))) return st;
     }
@@ -670,7 +689,7 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
     void *phic = (c->fwd_compact || c->adj_compact) ? dptr(c, "phic") : nullptr;
     // full layout with a gradient: psi and sigma stay in the compact sector
     // order from the forward's last run to the adjoint's first
-    const bool compact_path = !c->layout && grad;
+    const bool compact_path = c->layout != UCCSD_LAYOUT_SECTOR && grad;
     void *psi_h = compact_path ? dptr(c, "psic") : psi;  // psi as the H-apply reads it
     void *sig_h = compact_path ? dptr(c, "sigc") : sig;
     const int Rf = int(c->fwd.runs.size());
@@ -1290,6 +1309,13 @@ void uccsd_destroy(uccsd_ctx *c) {
     if (c->join_ev) cudaEventDestroy(c->join_ev);
     if (c->aux) cudaStreamDestroy(c->aux);
     if (c->own_setup) cudaStreamDestroy(c->own_setup);
+    if (c->gate_ev) {
+        // a waiting gate ends by itself (its time limit); wait for it before
+        // its status word goes away
+        cudaEventSynchronize(c->gate_ev);
+        cudaEventDestroy(c->gate_ev);
+    }
+    if (c->gate_status) cudaFreeHost(c->gate_status);
     delete c;
 }
 
@@ -1297,10 +1323,12 @@ uccsd_status uccsd_set_setup_stream(uccsd_ctx *c, void *stream) {
     if (!c) return UCCSD_ERR_ARG;
     if (c->failed) return fail(c, UCCSD_ERR_STATE, "context failed earlier: " + c->err);
     cudaError_t e = cudaSetDevice(c->device);
-    // staged copies still queued on the previous set-up stream finish first
-    if (e == cudaSuccess && c->stage_off > 0) e = cudaEventSynchronize(c->stage_ev);
-    if (e == cudaSuccess && !c->setup_async) e = cudaStreamSynchronize(c->setup);
-    if (e != cudaSuccess) return cuda_fail(c, e, "set-up stream switch");
+    if (e != cudaSuccess) return cuda_fail(c, e, "set-up stream switch: cudaSetDevice");
+    // staged copies still queued (on the context's own stream) finish first
+    if (c->stage_off > 0 && (e = cudaEventSynchronize(c->stage_ev)) != cudaSuccess)
+        return cuda_fail(c, e, "set-up stream switch: staging wait");
+    if (!c->setup_async && (e = cudaStreamSynchronize(c->setup)) != cudaSuccess)
+        return cuda_fail(c, e, "set-up stream switch: stream wait");
     c->stage_off = 0;
     c->setup_async = stream != nullptr;
     c->setup = stream ? static_cast<cudaStream_t>(stream) : c->own_setup;
@@ -1354,8 +1382,11 @@ uccsd_status uccsd_set_hamiltonian(uccsd_ctx *c, int n_orb, const double *h, con
 
 uccsd_status uccsd_set_layout(uccsd_ctx *c, int layout) {
     if (!c) return UCCSD_ERR_ARG;
-    if (layout != UCCSD_LAYOUT_FULL && layout != UCCSD_LAYOUT_SECTOR)
-        return fail(c, UCCSD_ERR_ARG, "layout must be UCCSD_LAYOUT_FULL or UCCSD_LAYOUT_SECTOR");
+    if (layout != UCCSD_LAYOUT_FULL && layout != UCCSD_LAYOUT_SECTOR && layout != UCCSD_LAYOUT_SCBK)
+        return fail(c, UCCSD_ERR_ARG,
+                    "layout must be UCCSD_LAYOUT_FULL, UCCSD_LAYOUT_SECTOR or UCCSD_LAYOUT_SCBK");
+    if (layout == UCCSD_LAYOUT_SCBK && c->have_h && c->n_orb < 2)
+        return fail(c, UCCSD_ERR_ARG, "the tapered encoding needs at least 2 orbitals");
     if (c->have_ref) return fail(c, UCCSD_ERR_STATE, "set_layout must come before set_reference");
     c->layout = layout;
     return UCCSD_OK;
@@ -1676,7 +1707,8 @@ uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {
     if (!c->have_exc) return fail(c, UCCSD_ERR_STATE, "no state yet");
     if (slot < 0 || slot >= c->B) return fail(c, UCCSD_ERR_ARG, "slot out of range");
     const size_t N = state_elems(c);
-    const size_t Nfull = size_t(1) << c->n;
+    // the 2^n vector, or the 2^(n-2) vector of the tapered encoding
+    const size_t Nfull = c->layout == UCCSD_LAYOUT_SCBK ? N : size_t(1) << c->n;
     if (!out || len < 2 * Nfull) return fail(c, UCCSD_ERR_ARG, "output buffer too small");
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
@@ -1698,7 +1730,29 @@ uccsd_status uccsd_get_state(uccsd_ctx *c, int slot, double *out, size_t len) {
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->setup);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "state download");
-    if (c->layout) {
+    if (c->layout == UCCSD_LAYOUT_SCBK) {
+        // The kernels compute with the Jordan-Wigner signs of the interleaved
+        // orbital order (qubit 2p alpha, 2p + 1 beta); the tapered encoding of
+        // uccsd_pauli_terms_scbk orders the orbitals up then down.  The two
+        // occupation bases differ by the sign of the permutation between the
+        // orders: (-1)^(number of occupied pairs beta q < alpha p).
+        std::memset(out, 0, sizeof(double) * 2 * Nfull);
+        std::vector<uint32_t> ta, tb;
+        scbk_addresses(c->n_orb, &ta, &tb);
+        for (uint32_t sa = 0; sa < (1u << c->n_orb); ++sa) {
+            if (__builtin_popcount(sa) != c->n_alpha) continue;
+            for (uint32_t sb = 0; sb < (1u << c->n_orb); ++sb) {
+                if (__builtin_popcount(sb) != c->n_beta) continue;
+                int inv = 0;
+                for (uint32_t w = sb; w; w &= w - 1u)
+                    inv += __builtin_popcount(sa >> (__builtin_ctz(w) + 1));
+                const double sg = (inv & 1) ? -1.0 : 1.0;
+                const size_t x = size_t(ta[sa]) + tb[sb];
+                out[2 * x] = sg * dense[2 * x];
+                out[2 * x + 1] = sg * dense[2 * x + 1];
+            }
+        }
+    } else if (c->layout == UCCSD_LAYOUT_SECTOR) {
         // scatter the sector array (alpha rank major, strings ascending) to 2^n
         std::memset(out, 0, sizeof(double) * 2 * Nfull);
         std::vector<uint32_t> sa, sb;

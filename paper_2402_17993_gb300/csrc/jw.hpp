@@ -49,4 +49,10 @@ struct CompiledExc {
 };
 bool compile_excitation(int n_qubits, const int32_t *row, CompiledExc *out, std::string *err);
 
+// Tapered symmetry-conserving Bravyi-Kitaev positions of the sector
+// determinants (tapering.cpp): determinant (alpha string sa, beta string sb)
+// at aoff[sa] + boff[sb] of the 2^(2 n_orb - 2) vector, in the qubit order of
+// uccsd_pauli_terms_scbk.
+void scbk_addresses(int n_orb, std::vector<uint32_t> *aoff, std::vector<uint32_t> *boff);
+
 }  // namespace uccsd

@@ -87,6 +87,29 @@ inline uint32_t drop2(uint32_t v, int t1, int t2) {
 
 }  // namespace
 
+namespace uccsd {
+
+// Positions of the electron-sector determinants in the tapered encoding
+// above, split by spin: the determinant with alpha orbital string sa and
+// beta string sb sits at aoff[sa] + boff[sb] of the 2^(n-2) vector.  The
+// tree's alpha nodes (below n/2 - 1) sum alpha orbitals only and its beta
+// nodes (n/2 .. n - 2) beta orbitals only; the two nodes that mix or fix
+// the parities are the tapered ones, so the kept alpha bits (positions
+// 0 .. n/2 - 2) depend on sa alone and the kept beta bits (n/2 - 1 ..
+// n - 3) on sb alone.
+void scbk_addresses(int n_orb, std::vector<uint32_t> *aoff, std::vector<uint32_t> *boff) {
+    const int n = 2 * n_orb, m = n_orb;
+    const std::vector<uint32_t> B = bk_tree_rows(n);
+    aoff->assign(size_t(1) << m, 0u);
+    boff->assign(size_t(1) << m, 0u);
+    for (uint32_t sv = 0; sv < (1u << m); ++sv) {
+        (*aoff)[sv] = drop2(gf2_apply(B, sv), m - 1, n - 1);
+        (*boff)[sv] = drop2(gf2_apply(B, sv << m), m - 1, n - 1);
+    }
+}
+
+}  // namespace uccsd
+
 extern "C" uccsd_status uccsd_pauli_terms_scbk(int n_orb, const double *h, const double *eri,
                                                double e_core, int n_alpha, int n_beta,
                                                uint32_t *xmask, uint32_t *zmask, double *coef,
