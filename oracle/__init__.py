@@ -12,12 +12,13 @@ Eq. 5/6 schedules; adjoint gradient).  This module adds the list builders,
 the dense-matrix helpers (FCI by numpy.linalg.eigh, Trotter-free energies by
 scipy.linalg.expm on the full space and by scipy.sparse.linalg.expm_multiply
 on the electron sector), the magnitude ordering of Section 2.3 with first-order
-amplitudes, the Trotter-error extrapolation of Section 3.2 and ctypes
+amplitudes, the Trotter-error extrapolation of Section 3.2, the FMO two-body
+assembly of Section 2.1 (Eq. 1, embedded fragment integrals) and ctypes
 marshalling.
 
 Parity pins: every function here is checked against something other than
-itself in ``tests/test_oracle_pins.py`` and ``tests/test_oracle_trotter.py``;
-none is "parity unpinned".
+itself in ``tests/test_oracle_pins.py``, ``tests/test_oracle_trotter.py`` and
+``tests/test_oracle_fmo.py``; none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -439,3 +440,52 @@ def trotter_free_energy_grad_sector(n_orb, h, eri, e_core, n_alpha, n_beta, ijab
         L = scipy.linalg.expm_frechet(A, Gk, compute_expm=False)
         g[k] = 2.0 * s @ (L @ e0)
     return E, g
+
+
+# ---------------------------------------------------------------------------
+# FMO two-body assembly (Section 2.1, Eq. 1)
+# ---------------------------------------------------------------------------
+def fmo_fragment_integrals(h, eri, frag_orbs, frag_nocc, members):
+    """Integrals of the fragment made of `members` (one monomer or two for a
+    dimer) in the mean field of the other fragments' closed-shell reference
+    determinants, written out element by element:
+        h'_pq = h_pq + sum_{j in env occ} [2 (pq|jj) - (pj|jq)]
+        (pq|rs)' = (pq|rs) restricted to the members' orbitals,
+    orbitals ordered [members' occupied..., members' virtual...].
+    Returns (h', eri', n_occ)."""
+    occ, vir = [], []
+    for f in members:
+        occ += list(frag_orbs[f][:frag_nocc[f]])
+        vir += list(frag_orbs[f][frag_nocc[f]:])
+    sel = occ + vir
+    env = []
+    for f in range(len(frag_orbs)):
+        if f not in members:
+            env += list(frag_orbs[f][:frag_nocc[f]])
+    m = len(sel)
+    hp = np.zeros((m, m))
+    for a, p in enumerate(sel):
+        for b, q in enumerate(sel):
+            v = h[p, q]
+            for j in env:
+                v += 2.0 * eri[p, q, j, j] - eri[p, j, j, q]
+            hp[a, b] = v
+    ep = np.zeros((m, m, m, m))
+    for a, p in enumerate(sel):
+        for b, q in enumerate(sel):
+            for c, r in enumerate(sel):
+                for d, s in enumerate(sel):
+                    ep[a, b, c, d] = eri[p, q, r, s]
+    return hp, ep, len(occ)
+
+
+def fmo2_energy(E_monomer, E_dimer, n_frag):
+    """Eq. 1: sum_{I<J} E_IJ - (N_f - 2) sum_I E_I, with E_monomer[I] and
+    E_dimer[(I, J)] (I < J)."""
+    total = 0.0
+    for i in range(n_frag):
+        for j in range(i + 1, n_frag):
+            total += E_dimer[(i, j)]
+    for i in range(n_frag):
+        total -= (n_frag - 2) * E_monomer[i]
+    return total

@@ -225,6 +225,60 @@ def pair_mixing(n_occ, n_virt, angle=math.pi / 4):
     return U
 
 
+def fmo_trimer(seed: int, coupling: float, n_frag: int = 3, n_orb_frag: int = 4,
+               n_occ_frag: int = 2, n_chol_frag: int = 5, n_chol_cross: int = 4):
+    """Integrals of a synthetic supersystem of n_frag fragments (the FMO
+    setting of the paper's Section 2.1), each with n_orb_frag localised
+    orbitals of which the n_occ_frag lowest are occupied.
+
+    Orbital order: fragment after fragment, occupied before virtual within a
+    fragment.  Draw order (one generator, seed):
+      (i)   for each fragment: h_pq (p < q within the fragment) ~ N(0, 1),
+            diagonal linspace(-2, -0.5, n_orb_frag);
+      (ii)  for each pair of orbitals of different fragments (p < q,
+            row-major): h_pq ~ N(0, 1) * coupling;
+      (iii) for each fragment, n_chol_frag vectors L_pq (p <= q within the
+            fragment) ~ N(0, 1) / sqrt(n_chol_frag);
+      (iv)  n_chol_cross vectors on all pairs p <= q ~ N(0, 1) /
+            sqrt(n_chol_cross) * coupling;
+      (pq|rs) = sum over all vectors of L_pq L_rs (8-fold symmetric, PSD).
+    coupling = 0 gives non-interacting fragments (block-diagonal integrals).
+    Returns dict(h, eri, frag_orbs, frag_nocc)."""
+    rng = Xoshiro256StarStar(seed)
+    n = n_frag * n_orb_frag
+    frag_orbs = [list(range(f * n_orb_frag, (f + 1) * n_orb_frag)) for f in range(n_frag)]
+    frag_of = [p // n_orb_frag for p in range(n)]
+    h = np.zeros((n, n))
+    for orbs in frag_orbs:
+        for a, p in enumerate(orbs):
+            for q in orbs[a + 1:]:
+                h[p, q] = h[q, p] = rng.normal()
+        for a, p in enumerate(orbs):
+            h[p, p] = -2.0 + 1.5 * a / max(1, n_orb_frag - 1)
+    for p in range(n):
+        for q in range(p + 1, n):
+            if frag_of[p] != frag_of[q]:
+                h[p, q] = h[q, p] = rng.normal() * coupling
+    vecs = []
+    for orbs in frag_orbs:
+        for _ in range(n_chol_frag):
+            L = np.zeros((n, n))
+            for a, p in enumerate(orbs):
+                for q in orbs[a:]:
+                    L[p, q] = L[q, p] = rng.normal() / math.sqrt(n_chol_frag)
+            vecs.append(L)
+    for _ in range(n_chol_cross):
+        L = np.zeros((n, n))
+        for p in range(n):
+            for q in range(p, n):
+                L[p, q] = L[q, p] = rng.normal() / math.sqrt(n_chol_cross) * coupling
+        vecs.append(L)
+    eri = np.zeros((n, n, n, n))
+    for L in vecs:
+        eri += np.einsum("pq,rs->pqrs", L, L)
+    return dict(h=h, eri=eri, frag_orbs=frag_orbs, frag_nocc=[n_occ_frag] * n_frag)
+
+
 def stream_fragments(n_req: int, seed: int = 7):
     """stream_requests() with each fragment's integrals attached
     (h, eri, e_core, n_alpha, n_beta)."""
