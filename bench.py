@@ -40,6 +40,9 @@ import numpy as np  # noqa: E402
 import synth  # noqa: E402
 
 METRIC = "UCCSD energy+grad evals/s (18q dimer fragment, batch 64)"
+METRIC_26Q = "UCCSD energy+grad evals/s (26q scale-up, one state)"
+WORKLOAD_26Q = ("26q/12e UCCSD K=2478 (seed 4, 20 Cholesky), theta ~N(0,0.02) (seeds 1004+b), "
+                "energy+adjoint gradient, M=1 first-order Trotter")
 WORKLOAD = ("18q/10e UCCSD K=560 (seed 2, 16 Cholesky), batch 64 theta ~N(0,0.05), "
             "energy+adjoint gradient, M=1 first-order Trotter")
 UNIT = "evals/s"
@@ -52,7 +55,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--batch", type=int, default=None,
+                    help="states per step (default 64 at 18 qubits, 1 at 26 qubits)")
+    ap.add_argument("--workload", default="18q", choices=["18q", "26q"],
+                    help="timed workload: the 18-qubit dimer batch (the headline) or the "
+                         "26-qubit scale-up")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--layout", default="full", choices=["full", "sector"],
                     help="state layout of the timed path (the sector layout is also timed "
@@ -68,7 +75,10 @@ def parse():
     ap.add_argument("--serving-fp64-requests", type=int, default=None,
                     help="requests of the one-at-a-time FP64 arm (default: the same stream "
                          "as the batched arm)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.batch is None:
+        args.batch = 64 if args.workload == "18q" else 1
+    return args
 
 
 def dist_env():
@@ -466,13 +476,14 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     prec = uc.FP32_STATE if args.precision == "fp32" else uc.FP64
     amp_bytes = 8 if prec == uc.FP32_STATE else 16
-    w = synth.workload("18q")
+    w = synth.workload(args.workload)
     B = args.batch
     layout = uc.LAYOUT_SECTOR if args.layout == "sector" else uc.LAYOUT_FULL
     ctx = uc.make_context(w["n_orb"], w["h"], w["eri"], w["e_core"], w["n_alpha"], w["n_beta"],
                           precision=prec, device=local, batch=B, layout=layout)
     K = ctx.K
-    th_host = np.stack([synth.theta_normal(K, 0.05, 1002 + b + 1000 * rank) for b in range(B)])
+    std, seed0 = (0.05, 1002) if args.workload == "18q" else (0.02, 1004)
+    th_host = np.stack([synth.theta_normal(K, std, seed0 + b + 1000 * rank) for b in range(B)])
     theta = torch.tensor(th_host, device=dev, dtype=torch.float64)
     E = torch.empty(B, device=dev, dtype=torch.float64)
     G = torch.empty(B, K, device=dev, dtype=torch.float64)
@@ -524,18 +535,20 @@ def run_ours(args):
 
     info = ctx.info()
     ijab = uc.build_uccsd_list(w["n_orb"], w["n_alpha"], w["n_beta"])
-    workload = f"18q_b{B}_{args.precision}"
+    workload = f"{args.workload}_b{B}_{args.precision}"
     dev_pk = device_peaks(torch.cuda.get_device_properties(dev).multi_processor_count,
                           ck.get("sm_max_mhz") or 2070.0)
     roof = roofline(prof, B, info, amp_bytes, ijab, prec == uc.FP32_STATE, workload, dev_pk)
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "18q" else METRIC_26Q, "value": value, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec == uc.FP32_STATE else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD,
-                   "state": "complex64 + FP64 reductions" if prec else "complex128",
+        "config": {"workload": WORKLOAD if args.workload == "18q" else WORKLOAD_26Q,
+                   "state": ("real amplitudes as FP32 hi + lo (8 bytes), FP64 reductions"
+                             if prec else "complex128"),
                    "layout": args.layout + (" (2^n vector per slot)" if args.layout == "full"
                                             else " (electron-sector array per slot)"),
                    "l2": "flushed between timed steps (256 MB write)",
@@ -546,6 +559,10 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": ck,
     }
+    if args.workload != "18q":
+        # the oracle takes about 15 minutes per 26-qubit evaluation on the host
+        # cores, and the other measurements are 18-qubit ones
+        args.no_cpu_baseline = args.no_small = args.no_scaleup = args.no_serving = True
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()

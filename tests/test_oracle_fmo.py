@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import synth
+from tests._fmo import dimer_theta
 
 
 def _hf_energy(h, eri, occ):
@@ -42,23 +43,6 @@ def test_embedded_reference_energy_splits_exactly(oracle_mod, coupling):
         assert abs(e_frag + _hf_energy(h, eri, env) - e_tot) < 1e-10
 
 
-def _dimer_theta(ex_i, th_i, ex_j, th_j, ex_d, nocc, nvir):
-    """Amplitudes of a dimer's excitation list from its monomers' (spin
-    orbitals remapped from [occ, virt] of a monomer to [occ I, occ J,
-    virt I, virt J] of the dimer); cross-fragment rows get zero."""
-    def remap(q, frag):
-        if q < 0:
-            return q
-        p, s = q >> 1, q & 1
-        new = (frag * nocc + p) if p < nocc else (2 * nocc + frag * nvir + (p - nocc))
-        return 2 * new + s
-    table = {}
-    for frag, (ex, th) in enumerate(((ex_i, th_i), (ex_j, th_j))):
-        for row, t in zip(ex.tolist(), th):
-            table[tuple(remap(q, frag) for q in row)] = t
-    return np.array([table.get(tuple(r), 0.0) for r in ex_d.tolist()])
-
-
 def test_non_interacting_fragments_are_additive(oracle_mod):
     t = synth.fmo_trimer(32, 0.0)
     h, eri, fo, fn = t["h"], t["eri"], t["frag_orbs"], t["frag_nocc"]
@@ -73,7 +57,7 @@ def test_non_interacting_fragments_are_additive(oracle_mod):
     for i, j in itertools.combinations(range(3), 2):
         hp, ep, nocc = oracle_mod.fmo_fragment_integrals(h, eri, fo, fn, (i, j))
         ex_d = oracle_mod.excitations(hp.shape[0], nocc, nocc)
-        th = _dimer_theta(exs[i], thetas[i], exs[j], thetas[j], ex_d, fn[i], len(fo[i]) - fn[i])
+        th = dimer_theta(exs[i], thetas[i], exs[j], thetas[j], ex_d, fn[i], len(fo[i]) - fn[i])
         dim[(i, j)] = oracle_mod.energy_grad(hp.shape[0], hp, ep, 0.0, nocc, nocc, ex_d, th,
                                              grad=False)[0]
         assert abs(dim[(i, j)] - mono[i] - mono[j]) < 1e-10
