@@ -1492,6 +1492,15 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     build_schedule(K, trotter_order, n_slices, &c->op_k, &c->op_scale);
     const size_t A = c->prec ? 8 : 16;
     c->fwd = plan_sweep(n, c->n_alpha, c->n_beta, A, 1, kSweepBudget, exc, c->op_k);
+    // A forward whose whole sector fits one tile would run one CTA per state
+    // (64 of 152 SMs at a batch of 64) on a chain of issue-bound factors; at
+    // half the tile budget each state spreads over two tiles (two SMs) at the
+    // price of a few runs handing the state on (18 qubits: forward 0.44 ->
+    // 0.41 ms).  Plans of several runs already have many tiles per run (26
+    // qubits: 512) and keep the full budget.
+    if (c->fwd.runs.size() == 1 && c->fwd.max_tiles == 1 &&
+        size_t(c->hsec.Da) * size_t(c->hsec.Db) >= 4096)
+        c->fwd = plan_sweep(n, c->n_alpha, c->n_beta, A, 1, kSweepBudget / 2, exc, c->op_k);
     c->adj = plan_sweep(n, c->n_alpha, c->n_beta, A, 2, kSweepBudget, exc, c->op_k);
     for (const SweepPlan *pl : {&c->fwd, &c->adj})
         for (const CRunDev &r : pl->runs)
