@@ -423,6 +423,11 @@ uccsd_status uccsd_opt_history(uccsd_ctx *ctx, double *E, int cap, int *n_out);
  *               cap derived from it, should the GPU's timer stall) it gives
  *               up, records that, and returns.  The work behind it then runs
  *               anyway; uccsd_gate_status tells the caller to discard it.
+ * While gates wait, the thread that releases them must not make a call
+ * that waits for the device (cudaDeviceSynchronize, cudaFree, cudaFreeHost,
+ * a pinned allocation, a synchronous copy): it would wait for the gates it
+ * is to release, until their time limit.  The flag must stay allocated
+ * until the gate has finished.
  * One gate per context at a time: UCCSD_ERR_STATE while the previous one is
  * still waiting.  Errors: UCCSD_ERR_ARG for a null flag or stream or a
  * limit out of range, UCCSD_ERR_CUDA if the launch fails. */

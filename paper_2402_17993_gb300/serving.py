@@ -20,8 +20,8 @@ qubits, each with its own integrals) and share one GPU:
   its latency is arrival -> last step done;
 * preparation off the serving thread: the host work of an admission (the
   Jordan-Wigner compile and tables, the sweep plans, the graph capture and
-  the enqueue of the solve) runs on a pool of worker threads, each on the
-  fragment's own context and stream.  A context belongs to one thread at a
+  the enqueue of the solve) runs on a pool of worker threads (8 by default),
+  each on the fragment's own context and stream.  A context belongs to one thread at a
   time: the pool hands it to a worker, the worker hands the prepared
   fragment to the serving thread, and the serving thread returns the
   context to the pool only after it has read the results (the library's
@@ -45,7 +45,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import FP32_STATE, FP64, Context, build_uccsd_list
+from . import FP32_STATE, FP64, Context, UCCSDError, build_uccsd_list
 from .vqe import LBFGS
 
 
@@ -199,10 +199,16 @@ class _DevSlot:
         self.gate_flag[0] = 1
 
     def check_gate(self):
-        """Raise if the gate gave up before its release (the solve then ran
-        early and its timing is void)."""
-        if self.gate_flag is not None:
-            self.ctx.gate_status(wait=True)
+        """False if the gate gave up before its release: the solve then ran
+        early (its result is the same, its latency is void)."""
+        if self.gate_flag is None:
+            return True
+        try:
+            return self.ctx.gate_status(wait=True)
+        except UCCSDError as exc:
+            if exc.code != 5:  # anything but the gate's own time limit
+                raise
+            return False
 
     def result(self, keep_theta):
         energies = [float(e) for e in self.ctx.opt_history(self.steps)]
@@ -217,7 +223,7 @@ class FragmentServer:
     use_graphs = False gives the plain one-request-at-a-time form."""
 
     def __init__(self, precision=FP32_STATE, device=0, hbm_budget=8 << 30, max_active=48,
-                 n_streams=None, steps=40, use_graphs=True, prep_workers=4, lookahead=0):
+                 n_streams=None, steps=40, use_graphs=True, prep_workers=8, lookahead=0):
         import torch
         self.precision = precision
         self.device = device
@@ -227,6 +233,18 @@ class FragmentServer:
         self.use_graphs = use_graphs
         n_streams = max_active if n_streams is None else n_streams
         self.streams = _distinct_streams(device, n_streams)
+        # Streams beyond the device's hardware work queues share queues and
+        # serialise falsely (the default is 8 queues: the closed-loop stream
+        # runs at about 11K instead of 38K evaluations/s with 32 streams).
+        # The queue count is read when CUDA initialises, so the process sets
+        # CUDA_DEVICE_MAX_CONNECTIONS before that (bench.py sets 32).
+        import os
+        import warnings
+        conn = int(os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"))
+        if conn < min(len(self.streams), 32):
+            warnings.warn(f"CUDA_DEVICE_MAX_CONNECTIONS={conn} hardware queues for "
+                          f"{len(self.streams)} fragment streams: set it (to 32) before CUDA "
+                          "initialises, or fragments on shared queues serialise", RuntimeWarning)
         self.pool = {}
         self._pool_lock = threading.Lock()
         # pair lists held for each shape class seen (one shared copy per class)
@@ -327,6 +345,15 @@ class FragmentServer:
         active: list[_DevSlot] = []
         preparing = []  # (future, request, reserved bytes, arrival time)
         gated = []      # (arrival time, gate flag) not yet released, in arrival order
+        release_lag = 0.0   # longest delay between an arrival and its gate's release
+        gates_gave_up = 0
+        # Gate flags, pinned once before the loop: while gates wait on the
+        # device, the serving thread must make no call that waits for the
+        # device (a pinned allocation may), or it waits for the gates that
+        # only it can release, until their time limit.
+        n_flags = self.max_active + 1
+        flag_buf = torch.zeros(n_flags, dtype=torch.int32).pin_memory() if rate and self.lookahead else None
+        free_flags = list(range(n_flags))
         free_streams = list(self.streams)
         results: list[Result] = []
         used = peak_used = sum(self.shared.values())
@@ -351,8 +378,10 @@ class FragmentServer:
                 used += need + extra
                 peak_used = max(peak_used, used)
                 flag = None
-                if arrive[pending] > now:
-                    flag = torch.zeros(1, dtype=torch.int32).pin_memory()
+                if arrive[pending] > now and flag_buf is not None:
+                    fi = free_flags.pop()
+                    flag = flag_buf[fi:fi + 1]
+                    flag[0] = 0
                     gated.append((arrive[pending], flag))
                 if self._exec is not None:
                     fut = self._exec.submit(self._prepare, q, before, st, t0, flag)
@@ -366,7 +395,9 @@ class FragmentServer:
             # release the gates of the requests that have arrived
             now = time.perf_counter() - t0
             while gated and gated[0][0] <= now:
-                gated.pop(0)[1][0] = 1
+                t_arr, flag = gated.pop(0)
+                flag[0] = 1
+                release_lag = max(release_lag, now - t_arr)
                 progressed = True
             still_prep = []
             for fut, q, need, t_arr in preparing:
@@ -385,7 +416,10 @@ class FragmentServer:
             for s in active:
                 if s.done.query():
                     t_done = time.perf_counter() - t0
-                    s.check_gate()
+                    if not s.check_gate():
+                        gates_gave_up += 1
+                    if s.gate_flag is not None:
+                        free_flags.append((s.gate_flag.data_ptr() - flag_buf.data_ptr()) // 4)
                     energies, theta = s.result(keep_theta)
                     results.append(Result(s.req.r, 2 * s.req.n_orb, s.t_arrive, s.t_admit,
                                           t_done, energies[-1], energies, theta))
@@ -406,6 +440,9 @@ class FragmentServer:
         makespan = time.perf_counter() - t0
         stats = self._stats(results, n_evals, makespan, [], peak_used, peak_dev)
         stats["lookahead"] = self.lookahead if rate else 0
+        if stats["lookahead"]:
+            stats["max_gate_release_lag_ms"] = 1e3 * release_lag
+            stats["gates_gave_up"] = gates_gave_up
         # time average of the number of admitted, unfinished fragments
         stats["mean_active"] = (sum(r.t_done - r.t_admit for r in results) / makespan
                                 if makespan > 0 else 0.0)

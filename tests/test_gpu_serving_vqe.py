@@ -253,6 +253,7 @@ def test_gated_lookahead_gives_the_same_solves(uc):
     srv.lookahead = 6
     gated, stats = srv.run(reqs, rate=400.0, keep_theta=True)
     assert stats["lookahead"] == 6 and stats["requests"] == 12
+    assert stats["gates_gave_up"] == 0
     for a, b in zip(plain, gated):
         assert a.r == b.r and a.energies == b.energies and np.array_equal(a.theta, b.theta)
         assert b.t_done >= b.t_arrive
