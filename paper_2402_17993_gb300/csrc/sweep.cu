@@ -701,12 +701,13 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
 // critical path is the barrier, two shared-memory loads per pair, the
 // rotation and the stores.
 // ---------------------------------------------------------------------------
-// Pairs per thread held in registers, loaded two factors ahead (measured on
-// 18 qubits, batch 64, FP32: forward 8 against 3, 4 or 6; adjoint 2 against
-// 3 or 4).
+// Pairs per thread held in registers, loaded two factors ahead.  Measured on
+// 18 qubits, batch 64, FP32, two tiles per state: forward 2 slots 0.379 ms
+// against 1: 0.613, 3: 0.447, 4: 0.453, 6: 0.398, 8: 0.410; adjoint 2
+// against 3 or 4.
 template <typename R>
 struct ListPre {
-    static constexpr int kFwd = sizeof(R) == 4 ? 8 : 4;
+    static constexpr int kFwd = sizeof(R) == 4 ? 2 : 4;
     static constexpr int kAdj = 2;
 };
 
