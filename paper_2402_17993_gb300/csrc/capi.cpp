@@ -34,6 +34,7 @@ template <typename R>
 struct HamTables {
     std::vector<MixT<R>> mix;
     std::vector<MixO<R>> mixo, d2ao, d2bo;
+    std::vector<R> d2bs;
     std::vector<SglT<R>> s1a, s1b;
     std::vector<DblT<R>> d2a, d2b;
     std::vector<R> spec;
@@ -136,6 +137,24 @@ bool make_tables(const CompiledH &H, int n_orb, HamTables<R> *T, std::string *er
                         O.j = D.j;
                     }
     }
+    // beta doubles by (occupied pair, empty pair) index with the part of the
+    // Jordan-Wigner sign that depends on the excitation alone: the group's
+    // beta mask is M = L(o1) ^ L(o2) ^ L(v1) ^ L(v2) without the flipped
+    // bits (L(v) = bits below v), and the target occupies o1 and o2, so the
+    // source's parity under it is popc(target & M) - bit o1 of M - bit o2
+    // of M; the H-apply forms the first term from per-lane prefix parities.
+    T->d2bs.assign(size_t(std::max(np, 1)) * std::max(np, 1), R(0));
+    for (int o1 = 0; o1 < n_orb; ++o1)
+        for (int o2 = o1 + 1; o2 < n_orb; ++o2)
+            for (int v1 = 0; v1 < n_orb; ++v1)
+                for (int v2 = v1 + 1; v2 < n_orb; ++v2) {
+                    if (v1 == o1 || v1 == o2 || v2 == o1 || v2 == o2) continue;
+                    const uint32_t M = ((1u << o1) - 1u) ^ ((1u << o2) - 1u) ^ ((1u << v1) - 1u) ^
+                                       ((1u << v2) - 1u);
+                    const R w = T->d2bo[((size_t(o1) * n_orb + o2) * n_orb + v1) * n_orb + v2].w;
+                    T->d2bs[size_t(pair_idx(o1, o2)) * np + pair_idx(v1, v2)] =
+                        (((M >> o1) ^ (M >> o2)) & 1u) ? -w : w;
+                }
     return true;
 }
 
@@ -294,6 +313,7 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     for (size_t i = 0; i < T.s1b.size(); ++i) c->spec_s1b[i] = T.s1b[i].spec;
     MixT<R> *mx;
     MixO<R> *mo, *oa, *ob;
+    R *bs;
     SglT<R> *sa, *sb;
     DblT<R> *da, *db;
     R *sp;
@@ -303,6 +323,7 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     if ((st = upload(c, t + "mixo", T.mixo, &mo))) return st;
     if ((st = upload(c, t + "d2ao", T.d2ao, &oa))) return st;
     if ((st = upload(c, t + "d2bo", T.d2bo, &ob))) return st;
+    if ((st = upload(c, t + "d2bs", T.d2bs, &bs))) return st;
     if ((st = upload(c, t + "s1a", T.s1a, &sa))) return st;
     if ((st = upload(c, t + "s1b", T.s1b, &sb))) return st;
     if ((st = upload(c, t + "d2a", T.d2a, &da))) return st;
@@ -314,6 +335,7 @@ uccsd_status upload_ham(uccsd_ctx *c, DevHam<R> *dh, const char *tag) {
     dh->mixo = mo;
     dh->d2ao = oa;
     dh->d2bo = ob;
+    dh->d2bs = bs;
     dh->s1a = sa;
     dh->s1b = sb;
     dh->d2a = da;
@@ -419,13 +441,30 @@ uccsd_status upload_spectator_tables(uccsd_ctx *c, DevHam<R> *dh, const char *ta
             }
         }
     }
+    // beta-qubit part of the diagonal's fixed-point form per column (beta
+    // orbital j is qubit 2j + 1)
+    std::vector<long long> dc(std::max<size_t>(Db, 1), 0);
+    const int n = c->n;
+    for (size_t col = 0; col < Db; ++col) {
+        long long q = 0;
+        for (uint32_t w = bstr[col]; w; w &= w - 1u) {
+            const int r = 2 * __builtin_ctz(w) + 1;
+            q += c->diag_qa[r];
+            for (uint32_t w2 = w & (w - 1u); w2; w2 &= w2 - 1u)
+                q += c->diag_qb[size_t(r) * n + 2 * __builtin_ctz(w2) + 1];
+        }
+        dc[col] = q;
+    }
     std::string t(tag);
     R *pa_, *pb_;
+    long long *dc_;
     uccsd_status st;
     if ((st = upload(c, t + "bspec_a", ta, &pa_))) return st;
     if ((st = upload(c, t + "bspec_b", tb, &pb_))) return st;
+    if ((st = upload(c, t + "diag_col", dc, &dc_))) return st;
     dh->bspec_a = pa_;
     dh->bspec_b = pb_;
+    dh->diag_col = dc_;
     return UCCSD_OK;
 }
 
@@ -453,6 +492,7 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
         const int Db = int(bstr_h.size());
         const int ns = c->n_beta * (no - c->n_beta);
         std::vector<uint32_t> tab(size_t(2) * std::max(ns, 1) * std::max(Db, 1), 0u);
+        std::vector<uint32_t> mix(size_t(std::max(ns, 1)) * std::max(Db, 1), 0u);
         for (int col = 0; col < Db; ++col) {
             const uint32_t sb = bstr_h[col];
             int k = 0;
@@ -464,15 +504,25 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
                     const size_t at = 2 * (size_t(k) * Db + col);
                     const int lo = std::min(j, bb), hi = std::max(j, bb);
                     tab[at] = rank_h[yb] | (uint32_t(j * no + bb) << 16);
-                    tab[at + 1] = yb | (uint32_t(pair_idx(lo, hi)) << 16) | (uint32_t(bb > j) << 24);
+                    // the column's part of the single's sign: parities of the
+                    // occupied beta orbitals below j and below b, and b > j
+                    const uint32_t cs = uint32_t(__builtin_popcount(sb & ((1u << j) - 1u)) +
+                                                 __builtin_popcount(sb & ((1u << bb) - 1u)) + (bb > j)) & 1u;
+                    tab[at + 1] = cs | (uint32_t(2 * pair_idx(lo, hi) + (bb > j)) << 16);
+                    // occupied beta orbitals strictly between j and b
+                    const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+                    const uint32_t pi = uint32_t(__builtin_popcount(sb & between) & 1);
+                    mix[size_t(k) * Db + col] = rank_h[yb] | (uint32_t(j * no + bb + no * no * pi) << 16);
                     ++k;
                 }
             }
         }
-        uint32_t *p4;
+        uint32_t *p4, *pm;
         uccsd_status st = upload(c, "bsing", tab, &p4);
         if (st) return st;
+        if ((st = upload(c, "bmix", mix, &pm))) return st;
         c->hsec.bsing = reinterpret_cast<const uint2 *>(p4);
+        c->hsec.bmix = pm;
         c->hsec.n_bs = ns;
         // alpha singles per H-apply phase: up to 4 while their staged source
         // rows take at most 64 KiB (FP32) or 24 KiB (FP64) of shared memory.

@@ -129,12 +129,22 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
 constexpr int kRowThreads = 256;
 
 // Dynamic shared memory of the H-apply: one source row, the beta string
-// ranks, then (8-byte aligned) the per-row alpha-spectator sums.
+// ranks, then (16-byte aligned) the row's beta-single values.
 template <typename R>
 __host__ __device__ inline size_t happly_aspec_offset(int Db, int n_orb) {
     const size_t o = sizeof(V2<R>) * (size_t)Db + sizeof(uint16_t) * ((size_t)1 << n_orb);
-    return (o + 7) & ~(size_t)7;
+    return (o + 15) & ~(size_t)15;
 }
+
+// Row part of a beta single j -> b (pair group pb, source side sel), entry
+// 2 pb + sel: the table value plus the alpha-spectator sum of the row, and
+// the row's part of the Jordan-Wigner sign (bit 31: the parities of the
+// row's occupied alpha orbitals up to j and up to b).
+template <typename R>
+struct alignas(2 * sizeof(R) > 8 ? 16 : 8) RowB {
+    R v;
+    uint32_t s;
+};
 
 // One alpha single excitation of an H-apply row: source alpha string,
 // source row offset, p | q << 8 (p occupied, q empty in the target).
@@ -143,12 +153,16 @@ struct ASgl {
 };
 
 // Shared-memory layout after the aspec block (offsets 16-byte aligned):
-// the row's alpha singles, its alpha doubles, then for a group of G alpha
-// singles their source rows, their rows of the ordered mixed table and
-// their alpha-only values.
+// the row's alpha singles, its alpha doubles, then for a phase of G alpha
+// singles their source rows ([column][G]), their rows of the ordered mixed
+// table with the row's signs folded in ([j * n_orb + b][G], then the same
+// negated) and their alpha-only values; last, while the CTA stays within
+// kHappBbStage bytes, a copy of the signed beta-double table (dbt = 0: the
+// kernel reads it from global memory).
 struct HappLayout {
-    size_t asl, adl, srcg, mrow, asing, total;
+    size_t asl, adl, srcg, mrow, asing, dbt, total;
 };
+constexpr size_t kHappBbStage = 32 * 1024;
 template <typename R>
 __host__ __device__ inline HappLayout happly_layout(int Db, int n_orb, int n_alpha, int G) {
     auto up = [](size_t o) { return (o + 15) & ~(size_t)15; };
@@ -156,13 +170,29 @@ __host__ __device__ inline HappLayout happly_layout(int Db, int n_orb, int n_alp
     const size_t nas = (size_t)n_alpha * nva;
     const size_t nad = (size_t)(n_alpha * (n_alpha - 1) / 2) * (nva * (nva - 1) / 2);
     HappLayout L;
-    L.asl = up(happly_aspec_offset<R>(Db, n_orb) + sizeof(R) * (size_t)n_orb * (n_orb - 1));
+    L.asl = up(happly_aspec_offset<R>(Db, n_orb) + sizeof(RowB<R>) * (size_t)n_orb * (n_orb - 1));
     L.adl = up(L.asl + sizeof(ASgl) * nas);
     L.srcg = up(L.adl + sizeof(ADbl<R>) * nad);
     L.mrow = up(L.srcg + sizeof(V2<R>) * (size_t)G * Db);
-    L.asing = up(L.mrow + sizeof(MixO<R>) * (size_t)G * n_orb * n_orb);
+    L.asing = up(L.mrow + sizeof(R) * (size_t)2 * G * n_orb * n_orb);
     L.total = L.asing + sizeof(R) * (size_t)G;
+    const size_t np = (size_t)n_orb * (n_orb - 1) / 2;
+    const size_t bb = up(L.total);
+    L.dbt = 0;
+    if (bb + sizeof(R) * np * np <= kHappBbStage) {
+        L.dbt = bb;
+        L.total = bb + sizeof(R) * np * np;
+    }
     return L;
+}
+
+// Bit v = parity of the bits 0 .. v of x (16-bit strings).
+__device__ __forceinline__ uint32_t prefix_parity(uint32_t x) {
+    x ^= x << 1;
+    x ^= x << 2;
+    x ^= x << 4;
+    x ^= x << 8;
+    return x;
 }
 
 __device__ __forceinline__ int pair_index(int p, int q) {  // p < q
@@ -182,6 +212,137 @@ __device__ __forceinline__ double with_sign(double x, uint32_t s) {
 }
 
 
+// N consecutive values of T from shared memory in 16-byte (or one 8-byte)
+// loads; p is aligned to the vector's size.
+template <typename T, int N>
+__device__ __forceinline__ void lds_vec(const T *p, T (&v)[N]) {
+    constexpr int B = int(sizeof(T)) * N;
+    if constexpr (B >= 16) {
+        int4 w[B / 16];
+#pragma unroll
+        for (int k = 0; k < B / 16; ++k) w[k] = reinterpret_cast<const int4 *>(p)[k];
+        __builtin_memcpy(&v[0], &w[0], B);
+    } else if constexpr (B == 8) {
+        const int2 w = *reinterpret_cast<const int2 *>(p);
+        __builtin_memcpy(&v[0], &w, 8);
+    } else {
+        v[0] = p[0];
+    }
+}
+
+// The alpha singles p -> q of row R, AG per phase (source rows R ^ {p, q}):
+// the alpha-only pair group of each single on the lane's own column, and
+// the mixed groups (alpha pair, beta pair) through the lane's beta single
+// excitations j -> b.
+//
+// Sign of a mixed contribution.  The group's Jordan-Wigner mask is the
+// interval mask of its flipped qubits 2p, 2q (alpha) and 2j + 1, 2b + 1
+// (beta): the XOR of the bit masks below each, without the flipped bits.
+// Over beta orbitals that is (A_pq ^ B_jb) minus {j, b}, with A_pq =
+// L(p) ^ L(q), B_jb = L(j) ^ L(b) and L(v) the bits below v.  The source
+// beta string equals the column's string s_c except at j (occupied in s_c)
+// and b (empty), so the source's parity under the mask splits into
+//   popc(s_c & A_pq)                       column x alpha single,
+//   bit j of A_pq, and the alpha part      alpha single x (j, b),
+//   s_c's occupied orbitals strictly between j and b   column x beta single.
+// The middle term is folded into the staged table, the last one selects the
+// table's negated half (HSector::bmix), and the first flips the single's
+// partial sum once.  Sign flips are exact, so every partial sum equals,
+// bit for bit, the one formed with a sign per term.
+template <typename R, int EPT, int AG>
+__device__ __forceinline__ void alpha_phases(const V2<R> *__restrict__ st, const DevHam<R> &H,
+                                             const HSector &hs, const ASgl *asl, V2<R> *srcg,
+                                             R *tw, R *asing, const int (&cix)[EPT],
+                                             const uint32_t (&sc)[EPT], V2<R> (&acc)[EPT],
+                                             V2<R> (&comp)[EPT]) {
+    const int n_orb = H.n_orb;
+    const int nas = hs.n_alpha * (n_orb - hs.n_alpha);
+    const int nn = n_orb * n_orb;
+    for (int g0 = 0; g0 < nas; g0 += AG) {
+        const int gn = min(AG, nas - g0);
+        __syncthreads();  // the previous phase's rows are consumed
+        for (int t = threadIdx.x; t < hs.Db * AG; t += blockDim.x) {
+            const int c = t / AG, g = t % AG;
+            V2<R> v = V2<R>{(R)0, (R)0};
+            if (g < gn) v = st[asl[g0 + g].xoff + hs.boff[hs.bstr[c]]];
+            srcg[t] = v;
+        }
+        for (int t = threadIdx.x; t < nn * AG; t += blockDim.x) {
+            const int jb = t / AG, g = t % AG;
+            R w = (R)0;
+            if (g < gn) {
+                const ASgl a = asl[g0 + g];
+                const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
+                const MixO<R> M = H.mixo[(size_t)(p * n_orb + q) * nn + jb];
+                const uint32_t apq = ((1u << p) - 1u) ^ ((1u << q) - 1u);
+                const uint32_t par = (uint32_t)__popc(a.s & M.j & 0xFFFFu) ^ (apq >> (jb / n_orb));
+                w = with_sign(M.w, par << 31);
+            }
+            tw[t] = w;
+            tw[nn * AG + t] = with_sign(w, 0x80000000u);
+        }
+        if (threadIdx.x < gn) {
+            // the alpha-only group value's alpha part: the same for every column
+            const ASgl a = asl[g0 + threadIdx.x];
+            const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
+            const int asel = q > p;
+            const SglT<R> &S = H.s1a[pair_index(min(p, q), max(p, q))];
+            R va = S.lut[asel];
+            if (S.spec >= 0)
+                for (uint32_t w = a.s & ~(1u << q); w; w &= w - 1u)
+                    va += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + (asel ? 2 : 1)];
+            asing[threadIdx.x] = va;
+        }
+        __syncthreads();
+        uint32_t apq[AG];
+#pragma unroll
+        for (int g = 0; g < AG; ++g) {
+            const uint32_t pq = g < gn ? asl[g0 + g].pq : 0u;
+            apq[g] = ((1u << (pq & 0xFFu)) - 1u) ^ ((1u << (pq >> 8)) - 1u);
+        }
+#pragma unroll
+        for (int i = 0; i < EPT; ++i) {
+            if (cix[i] < 0) continue;
+            const uint32_t cb_str = sc[i];
+            // one table entry and one source entry per beta single serve the
+            // phase's AG alpha singles: a plain partial sum per alpha single,
+            // added with compensation
+            V2<R> seg[AG];
+#pragma unroll
+            for (int g = 0; g < AG; ++g) seg[g] = V2<R>{(R)0, (R)0};
+            const uint32_t *bm = hs.bmix + cix[i];
+#pragma unroll 2
+            for (int t = 0; t < hs.n_bs; ++t) {
+                const uint32_t e = __ldg(bm + (size_t)t * hs.Db);
+                R w[AG];
+                V2<R> y[AG];
+                lds_vec(tw + (e >> 16) * AG, w);
+                lds_vec(srcg + (e & 0xFFFFu) * AG, y);
+#pragma unroll
+                for (int g = 0; g < AG; ++g) {
+                    seg[g].x += w[g] * y[g].x;
+                    seg[g].y += w[g] * y[g].y;
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < AG; ++g) {
+                if (g < gn) {
+                    const ASgl a = asl[g0 + g];
+                    const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
+                    const int pa = pair_index(min(p, q), max(p, q));
+                    const int asel = q > p;
+                    // alpha-only pair group: same column (beta-spectator sum per column)
+                    R val = asing[g] + __ldg(H.bspec_a + ((size_t)pa * 2 + asel) * hs.Db + cix[i]);
+                    val = with_sign(val, jw_sign(a.s | (cb_str << 16), H.s1a[pa].j));
+                    accumulate<R>(acc[i], comp[i], val, srcg[(size_t)cix[i] * AG + g]);
+                    accumulate<R>(acc[i], comp[i], (__popc(cb_str & apq[g]) & 1) ? (R)-1 : (R)1,
+                                  seg[g]);
+                }
+            }
+        }
+    }
+}
+
 template <typename R, int EPT>
 __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__restrict__ psi,
                                                              V2<R> *__restrict__ sig, size_t N,
@@ -191,16 +352,18 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *src = reinterpret_cast<V2<R> *>(smem_raw);                  // one source row
     uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
-    // alpha-spectator part of each beta single's value for this row, [pair][sel]
-    R *aspec = reinterpret_cast<R *>(smem_raw + happly_aspec_offset<R>(hs.Db, H.n_orb));
+    // row part of each beta single, [pair][sel]
+    RowB<R> *rowb = reinterpret_cast<RowB<R> *>(smem_raw + happly_aspec_offset<R>(hs.Db, H.n_orb));
     const HappLayout lay = happly_layout<R>(hs.Db, H.n_orb, hs.n_alpha, hs.ag);
     ASgl *asl = reinterpret_cast<ASgl *>(smem_raw + lay.asl);
     ADbl<R> *adl = reinterpret_cast<ADbl<R> *>(smem_raw + lay.adl);
     V2<R> *srcg = reinterpret_cast<V2<R> *>(smem_raw + lay.srcg);
-    MixO<R> *mrowg = reinterpret_cast<MixO<R> *>(smem_raw + lay.mrow);
+    R *tw = reinterpret_cast<R *>(smem_raw + lay.mrow);
     R *asing = reinterpret_cast<R *>(smem_raw + lay.asing);
     __shared__ double red[32];
     __shared__ int nb4[16 * 5];
+    __shared__ long long xrow[16];  // diagonal: row's alpha-beta pair sums per beta orbital
+    __shared__ long long qrow;      // diagonal: constant plus the row's alpha part
     const int b = blockIdx.y;
     const int row = blockIdx.x / hs.ncb;
     const int cb = blockIdx.x - row * hs.ncb;
@@ -210,6 +373,8 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
     const V2<R> *st = psi + (size_t)b * N;
     for (int t = threadIdx.x; t < (1 << n_orb); t += blockDim.x) brk[t] = hs.brank[t];
     for (int t = threadIdx.x; t < 16 * 5; t += blockDim.x) nb4[t] = hs.binom[t];
+    // parity of the row's occupied alpha orbitals up to v, bit v
+    const uint32_t pa = prefix_parity(sR);
     for (int t = threadIdx.x; t < 2 * H.n_pairs; t += blockDim.x) {
         const SglT<R> &S = H.s1b[t >> 1];
         R val = (R)0;
@@ -218,7 +383,20 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             for (uint32_t w = sR; w; w &= w - 1u)
                 val += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + pat];
         }
-        aspec[t] = val;
+        int hi = 1;
+        while ((hi + 1) * hi / 2 <= (t >> 1)) ++hi;
+        const int lo = (t >> 1) - hi * (hi - 1) / 2;
+        RowB<R> rb;
+        rb.v = S.lut[t & 1] + val;
+        rb.s = ((pa >> lo) ^ (pa >> hi)) << 31;
+        rowb[t] = rb;
+    }
+    const int np = H.n_pairs;
+    const R *dbt = H.d2bs;
+    if (lay.dbt) {
+        R *d = reinterpret_cast<R *>(smem_raw + lay.dbt);
+        for (int t = threadIdx.x; t < np * np; t += blockDim.x) d[t] = __ldg(H.d2bs + t);
+        dbt = d;
     }
     {
         const uint32_t xR = hs.aoff[sR];
@@ -273,6 +451,28 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             }
         }
     }
+    if (H.has_diag) {
+        // alpha orbital i is qubit 2i, beta orbital j qubit 2j + 1
+        const int t = blockDim.x > 96 ? (int)threadIdx.x - 64 : (int)threadIdx.x;
+        if (t >= 0 && t < n_orb) {
+            const int r = 2 * t + 1;
+            long long v = 0;
+            for (uint32_t w = sR; w; w &= w - 1u) {
+                const int a = 2 * (__ffs(w) - 1);
+                v += H.diag_qb[(size_t)min(a, r) * H.n + max(a, r)];
+            }
+            xrow[t] = v;
+        } else if (t == n_orb) {
+            long long v = H.diag_q0;
+            for (uint32_t w = sR; w; w &= w - 1u) {
+                const int a = 2 * (__ffs(w) - 1);
+                v += H.diag_qa[a];
+                for (uint32_t w2 = w & (w - 1u); w2; w2 &= w2 - 1u)
+                    v += H.diag_qb[(size_t)a * H.n + 2 * (__ffs(w2) - 1)];
+            }
+            qrow = v;
+        }
+    }
     __syncthreads();
 
     int cix[EPT];
@@ -295,35 +495,29 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         if (cix[i] < 0) continue;
         const uint32_t cb_str = sc[i];
         if (H.has_diag) {
-            long long q = H.diag_q0;
-            uint32_t o1 = hs.aspread[sR] | hs.bspread[cb_str];
-            const int n = H.n;
-            while (o1) {
-                const int a = __ffs(o1) - 1;
-                o1 &= o1 - 1u;
-                q += H.diag_qa[a];
-                uint32_t o2 = o1;
-                while (o2) {
-                    const int r = __ffs(o2) - 1;
-                    o2 &= o2 - 1u;
-                    q += H.diag_qb[a * n + r];
-                }
-            }
+            // the occupation form over all occupied qubits: the row's part,
+            // the column's beta part and the alpha-beta pairs (exact integers)
+            long long q = qrow + __ldg(H.diag_col + cix[i]);
+            for (uint32_t w = cb_str; w; w &= w - 1u) q += xrow[__ffs(w) - 1];
             accumulate<R>(acc[i], comp[i], (R)q * (R)H.diag_unit, own[i]);
         }
-        // beta singles (precomputed per column: source rank, pair group,
-        // source side, beta-spectator sum)
+        // Jordan-Wigner signs of the beta-only groups from prefix parities:
+        // for a beta excitation the group's mask over alpha orbitals is the
+        // XOR of "up to v" masks and over beta orbitals the XOR of "below v"
+        // masks, v over its orbitals, without the flipped bits; so its sign
+        // is the XOR of bit v of pa ^ pb over those orbitals and a term of
+        // the excitation alone (in the tables)
+        const uint32_t pab = pa ^ prefix_parity(cb_str << 1);
+        // beta singles (precomputed per column: source rank, row-table
+        // entry, column sign, beta-spectator sum)
         {
             const uint2 *bsc = hs.bsing + cix[i];
             const R *bsp = H.bspec_b + cix[i];
             for (int t = 0; t < hs.n_bs; ++t) {
                 const uint2 e = __ldg(bsc + (size_t)t * hs.Db);
-                const int pb = (int)((e.y >> 16) & 0xFFu);
-                const int sel = (int)(e.y >> 24);
-                const SglT<R> &S = H.s1b[pb];
-                R val = S.lut[sel] + aspec[2 * pb + sel];
-                val += __ldg(bsp + (size_t)t * hs.Db);
-                val = with_sign(val, jw_sign(sR | (e.y << 16), S.j));
+                const RowB<R> rb = rowb[e.y >> 16];
+                R val = rb.v + __ldg(bsp + (size_t)t * hs.Db);
+                val = with_sign(val, rb.s ^ (e.y << 31));
                 accumulate<R>(acc[i], comp[i], val, src[e.x & 0xFFFFu]);
             }
         }
@@ -332,19 +526,18 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
             const int j1 = __ffs(o1) - 1;
             for (uint32_t o2 = o1 & (o1 - 1u); o2; o2 &= o2 - 1u) {
                 const int j2 = __ffs(o2) - 1;
-                const MixO<R> *Dj = H.d2bo + (size_t)(j1 * n_orb + j2) * n_orb * n_orb;
+                const R *Dj = dbt + (size_t)pair_index(j1, j2) * np;
                 const uint32_t yj = cb_str ^ (1u << j1) ^ (1u << j2);
+                const uint32_t s12 = (pab >> j1) ^ (pab >> j2);
                 V2<R> seg = V2<R>{(R)0, (R)0};  // plain partial per occupied pair
                 for (uint32_t v1 = vir; v1; v1 &= v1 - 1u) {
                     const int b1 = __ffs(v1) - 1;
-                    const MixO<R> *Db1 = Dj + b1 * n_orb;
                     const uint32_t y1 = yj ^ (1u << b1);
+                    const uint32_t s1 = s12 ^ (pab >> b1);
                     for (uint32_t v2 = v1 & (v1 - 1u); v2; v2 &= v2 - 1u) {
                         const int b2 = __ffs(v2) - 1;
-                        const MixO<R> D = Db1[b2];
-                        const uint32_t yb = y1 ^ (1u << b2);
-                        const R val = with_sign(D.w, jw_sign(sR | (yb << 16), D.j));
-                        const V2<R> y = src[brk[yb]];
+                        const R val = with_sign(Dj[pair_index(b1, b2)], (s1 ^ (pab >> b2)) << 31);
+                        const V2<R> y = src[brk[y1 ^ (1u << b2)]];
                         seg.x += val * y.x;
                         seg.y += val * y.y;
                     }
@@ -354,79 +547,11 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
         }
     }
 
-    // ---- alpha singles, G per phase: source rows R ^ {p, q} ----
-    const int nas = hs.n_alpha * nva, G = hs.ag;
-    const int nn = n_orb * n_orb;
-    for (int g0 = 0; g0 < nas; g0 += G) {
-        const int gn = min(G, nas - g0);
-        __syncthreads();  // the previous group's rows are consumed
-        for (int g = 0; g < gn; ++g) {
-            const ASgl a = asl[g0 + g];
-            V2<R> *dst = srcg + (size_t)g * hs.Db;
-            for (int c = threadIdx.x; c < hs.Db; c += blockDim.x)
-                dst[c] = st[a.xoff + hs.boff[hs.bstr[c]]];
-            const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
-            const MixO<R> *Mrow = H.mixo + (size_t)(p * n_orb + q) * nn;
-            for (int t = threadIdx.x; t < nn; t += blockDim.x) mrowg[g * nn + t] = Mrow[t];
-        }
-        if (threadIdx.x < gn) {
-            // the alpha-only group value's alpha part: the same for every column
-            const ASgl a = asl[g0 + threadIdx.x];
-            const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
-            const int asel = q > p;
-            const SglT<R> &S = H.s1a[pair_index(min(p, q), max(p, q))];
-            R va = S.lut[asel];
-            if (S.spec >= 0)
-                for (uint32_t w = a.s & ~(1u << q); w; w &= w - 1u)
-                    va += H.spec[(size_t)(S.spec + 2 * (__ffs(w) - 1)) * 4 + (asel ? 2 : 1)];
-            asing[threadIdx.x] = va;
-        }
-        __syncthreads();
-        uint32_t sg[4];
-#pragma unroll
-        for (int g = 0; g < 4; ++g) sg[g] = g < gn ? asl[g0 + g].s : 0u;
-#pragma unroll
-        for (int i = 0; i < EPT; ++i) {
-            if (cix[i] < 0) continue;
-            const uint32_t cb_str = sc[i];
-            // mixed groups through the lane's beta single excitations
-            // (precomputed per column: source rank, table index, source
-            // string), one table entry for the G singles of the phase: a
-            // plain partial sum per alpha single, added with compensation
-            V2<R> seg[4];
-#pragma unroll
-            for (int g = 0; g < 4; ++g) seg[g] = V2<R>{(R)0, (R)0};
-            const uint2 *bs = hs.bsing + cix[i];
-#pragma unroll 2
-            for (int t = 0; t < hs.n_bs; ++t) {
-                const uint2 e = __ldg(bs + (size_t)t * hs.Db);
-                const uint32_t jb = e.x >> 16, rk = e.x & 0xFFFFu, yb16 = e.y << 16;
-#pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    if (g < gn) {
-                        const MixO<R> M = mrowg[g * nn + jb];
-                        const R w = with_sign(M.w, jw_sign(sg[g] | yb16, M.j));
-                        const V2<R> y = srcg[(size_t)g * hs.Db + rk];
-                        seg[g].x += w * y.x;
-                        seg[g].y += w * y.y;
-                    }
-                }
-            }
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                if (g < gn) {
-                    const ASgl a = asl[g0 + g];
-                    const int p = (int)(a.pq & 0xFFu), q = (int)(a.pq >> 8);
-                    const int pa = pair_index(min(p, q), max(p, q));
-                    const int asel = q > p;
-                    // alpha-only pair group: same column (beta-spectator sum per column)
-                    R val = asing[g] + __ldg(H.bspec_a + ((size_t)pa * 2 + asel) * hs.Db + cix[i]);
-                    val = with_sign(val, jw_sign(a.s | (cb_str << 16), H.s1a[pa].j));
-                    accumulate<R>(acc[i], comp[i], val, srcg[(size_t)g * hs.Db + cix[i]]);
-                    accumulate<R>(acc[i], comp[i], (R)1, seg[g]);
-                }
-            }
-        }
+    // ---- alpha singles, hs.ag per phase: source rows R ^ {p, q} ----
+    switch (hs.ag) {
+        case 4: alpha_phases<R, EPT, 4>(st, H, hs, asl, srcg, tw, asing, cix, sc, acc, comp); break;
+        case 2: alpha_phases<R, EPT, 2>(st, H, hs, asl, srcg, tw, asing, cix, sc, acc, comp); break;
+        default: alpha_phases<R, EPT, 1>(st, H, hs, asl, srcg, tw, asing, cix, sc, acc, comp); break;
     }
 
     // ---- alpha doubles: source amplitude of the same column ----

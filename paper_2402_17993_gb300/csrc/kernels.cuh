@@ -19,6 +19,10 @@ struct DevHam {
     // the source occupying v1, v2 and the group's Jordan-Wigner mask
     const MixO<R> *d2ao = nullptr;
     const MixO<R> *d2bo = nullptr;
+    // beta doubles by pair index: entry pair(o1, o2) * n_pairs + pair(v1, v2)
+    // (o1 < o2 occupied, v1 < v2 empty in the target), the value times the
+    // excitation's own part of the Jordan-Wigner sign
+    const R *d2bs = nullptr;
     const SglT<R> *s1a = nullptr;  // [n_pairs] alpha singles
     const SglT<R> *s1b = nullptr;  // [n_pairs] beta singles
     const DblT<R> *d2a = nullptr;  // [n_quads] alpha doubles
@@ -38,6 +42,10 @@ struct DevHam {
     //   d(x) - shift = q0 + sum_{q in occ(x)} qa[q] + sum_{q<r in occ(x)} qb[q*n + r]
     const long long *diag_qa = nullptr; // n
     const long long *diag_qb = nullptr; // n*n (q < r)
+    // The part of that form over the beta qubits of each column (Db
+    // entries, the reference's beta strings); the H-apply adds the alpha
+    // part and the alpha-beta pairs per row.
+    const long long *diag_col = nullptr;
     long long diag_q0 = 0;
     double diag_unit = 0.0;
     int has_diag = 0;
@@ -65,9 +73,16 @@ struct HSector {
     // Beta single excitations of every column, [s][Db] with s over the
     // column's occupied j (ascending) then virtual b (ascending):
     // x = rank of the source string yb = bstr ^ {j, b} | (j * n_orb + b) << 16,
-    // y = yb | pair_index(min(j, b), max(j, b)) << 16 | (b > j) << 24.
+    // y = c | (2 * pair_index(min(j, b), max(j, b)) + (b > j)) << 16 with c
+    // the column's part of the Jordan-Wigner sign: the parity of the
+    // column's occupied orbitals below j, plus those below b, plus (b > j).
     // n_bs = n_beta * (n_orb - n_beta) per column.
     const uint2 *bsing = nullptr;
+    // The same excitations for the mixed groups, [s][Db]: rank of the source
+    // string | (j * n_orb + b + n_orb^2 * pi) << 16, pi the parity of the
+    // column's occupied beta orbitals strictly between j and b (selects the
+    // negated half of the H-apply's staged mixed table).
+    const uint32_t *bmix = nullptr;
     int n_bs = 0;
     int ag = 1;  // alpha singles staged per phase of the H-apply (1..4)
     int n_alpha = 0, n_beta = 0;
