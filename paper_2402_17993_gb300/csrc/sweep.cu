@@ -188,6 +188,14 @@ __device__ __forceinline__ void build_sides(const PairSet &p, const TileView &v,
     }
 }
 
+// x with its sign bit flipped when bit 31 of neg is set.
+__device__ __forceinline__ float flip_sign(float x, uint32_t neg) {
+    return __int_as_float(__float_as_int(x) ^ (int)(neg & 0x80000000u));
+}
+__device__ __forceinline__ double flip_sign(double x, uint32_t neg) {
+    return __hiloint2double(__double2hiint(x) ^ (int)(neg & 0x80000000u), __double2loint(x));
+}
+
 // Stage the run's factor descriptors and (small tiles) the combinatorial
 // table prefixes into shared memory at `base`; returns the table view the
 // CTA uses.  Callers synchronise before use.
@@ -227,15 +235,30 @@ template <typename R>
 __device__ __forceinline__ SweepArgs stage_run(const CRunDev &run, const SweepArgs &sa,
                                                const COpDev *ops, const V2<R> *csb,
                                                unsigned char *base, COpDev **sops, V2<R> **scs,
-                                               const int2 *cls_pl = nullptr, int2 **spl = nullptr) {
+                                               const int2 *cls_pl = nullptr, int2 **spl = nullptr,
+                                               bool signed_sin = false, uint32_t rest = 0u) {
     const int nops = run.op_end - run.op_begin;
     COpDev *so = reinterpret_cast<COpDev *>(base);
     const uint32_t *gsrc = reinterpret_cast<const uint32_t *>(ops + run.op_begin);
     uint32_t *gdst = reinterpret_cast<uint32_t *>(so);
-    for (int t = threadIdx.x; t < nops * 8; t += blockDim.x) gdst[t] = gsrc[t];
+    // signed_sin: the sine carries the factor's sign and the tile's rest
+    // parity (the list sweeps' rotation constants, one load per factor), and
+    // so does bit 31 of the staged op_s0 (word 7 of a descriptor)
+    for (int t = threadIdx.x; t < nops * 8; t += blockDim.x) {
+        uint32_t w = gsrc[t];
+        if (signed_sin && (t & 7) == 7)
+            w ^= (uint32_t)(__popc(rest & gsrc[t - 1]) & 1) << 31;  // word 6: par_rest
+        gdst[t] = w;
+    }
     V2<R> *c = reinterpret_cast<V2<R> *>(so + nops);
-    for (int t = threadIdx.x; t < nops; t += blockDim.x)
-        c[t] = csb[ops[run.op_begin + t].op_s0 & 0x7FFFFFFFu];
+    for (int t = threadIdx.x; t < nops; t += blockDim.x) {
+        const COpDev &op = ops[run.op_begin + t];
+        V2<R> v = csb[op.op_s0 & 0x7FFFFFFFu];
+        if (signed_sin)
+            v.y = flip_sign(v.y, (op.op_s0 ^ ((uint32_t)(__popc(rest & op.par_rest) & 1) << 31)) &
+                                     0x80000000u);
+        c[t] = v;
+    }
     *sops = so;
     *scs = c;
     int2 *pl = reinterpret_cast<int2 *>(c + nops);
@@ -273,13 +296,6 @@ __device__ __forceinline__ void split_index(int j, int Vb, float inv, int *ja, i
     *jb = j - q * Vb;
 }
 
-// x with its sign bit flipped when bit 31 of neg is set.
-__device__ __forceinline__ float flip_sign(float x, uint32_t neg) {
-    return __int_as_float(__float_as_int(x) ^ (int)(neg & 0x80000000u));
-}
-__device__ __forceinline__ double flip_sign(double x, uint32_t neg) {
-    return __hiloint2double(__double2hiint(x) ^ (int)(neg & 0x80000000u), __double2loint(x));
-}
 
 // Walk over the pair set j = ja * Vb + jb in steps of THREADS: the step in
 // (ja, jb) coordinates is (sq, sr) with THREADS = sq * Vb + sr.
@@ -745,10 +761,10 @@ __device__ __forceinline__ void forward_list_step(int o, int nops, V2<R> *tile, 
     if (t == 0 && o + kListAhead < nops) prefetch_list_l2(pairs, spl[o + kListAhead]);
     if (o + 2 < nops) fetch_pairs<KP>(nxt, pairs, spl[o + 2], t, THREADS);
     const int2 pl = spl[o];
-    const COpDev &op = sops[o];
-    const V2<R> csv = scs[o];
-    const uint32_t rneg = (uint32_t)(__popc(rest & op.par_rest) & 1) << 31;
-    const R ct = csv.x, st = flip_sign(csv.y, (op.op_s0 & 0x80000000u) ^ rneg);
+    const V2<R> csv = scs[o];  // signed sine (stage_run)
+    const R ct = csv.x, st = csv.y;
+    (void)sops;
+    (void)rest;
     // the prefetched pairs in chunks of two: loads of a chunk before its stores
 #pragma unroll
     for (int k0 = 0; k0 < KP; k0 += 2) {
@@ -803,7 +819,8 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
     int2 *spl;
     const SweepArgs la = stage_run<R>(run, sa, ops, cs + (size_t)b * n_ops,
                                       reinterpret_cast<unsigned char *>(tile + tile_alloc(run.max_entries)),
-                                      &sops, &scs, sa.op_pl + run.pl_base + (size_t)cls * nops, &spl);
+                                      &sops, &scs, sa.op_pl + run.pl_base + (size_t)cls * nops, &spl,
+                                      true, v.rest);
     if (threadIdx.x < kTileScratch)  // padding pairs rotate these zeros
         tile[tile_scratch(run.max_entries) + threadIdx.x] = V2<R>{(R)0, (R)0};
     __syncthreads();
@@ -882,10 +899,8 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
     if (t == 0 && o - kListAhead >= 0) prefetch_list_l2(pairs, spl[o - kListAhead]);
     if (o - 2 >= 0) fetch_pairs<KP>(nxt, pairs, spl[o - 2], t, THREADS);
     const int2 pl = spl[o];
-    const COpDev &op = sops[o];
-    const V2<R> csv = scs[o];
-    const uint32_t rneg = (uint32_t)(__popc(rest & op.par_rest) & 1) << 31;
-    const R ct = csv.x, st = flip_sign(csv.y, (op.op_s0 & 0x80000000u) ^ rneg);
+    const V2<R> csv = scs[o];  // signed sine (stage_run)
+    const R ct = csv.x, st = csv.y;
     Part<R> part = part_zero<R>();
     auto one = [&](uint2 q, V2<R> &fa, V2<R> &fb, V2<R> &la0, V2<R> &lb0) {
         const uint32_t e = q.x, e2 = q.y;
@@ -937,9 +952,11 @@ __device__ __forceinline__ void adjoint_list_step(int o, int nops, V2<R> *tp, V2
     // the warp partial (FP64, or FP32 hi + lo for the FP32 state) goes to
     // the factor's (tile, warp) slot; the reduction sums the slots in a
     // fixed order in FP64
+    const uint32_t w = sops[o].op_s0;  // sign bit with the rest parity (stage_run)
     pend.part = part;
-    pend.dst = gp + (size_t)(op.op_s0 & 0x7FFFFFFFu) * tile_stride + warp;
-    pend.neg = (op.op_s0 ^ rneg) & 0x80000000u;
+    pend.dst = gp + (size_t)(w & 0x7FFFFFFFu) * tile_stride + warp;
+    pend.neg = w & 0x80000000u;
+    (void)rest;
     __syncthreads();
 }
 
@@ -969,7 +986,8 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     int2 *spl;
     const SweepArgs la = stage_run<R>(run, sa, ops, cs + (size_t)b * n_ops,
                                       reinterpret_cast<unsigned char *>(tl + tile_alloc(run.max_entries)),
-                                      &sops, &scs, sa.op_pl + run.pl_base + (size_t)cls * nops, &spl);
+                                      &sops, &scs, sa.op_pl + run.pl_base + (size_t)cls * nops, &spl,
+                                      true, v.rest);
     if (threadIdx.x < kTileScratch) {  // padding pairs rotate these zeros
         tp[tile_scratch(run.max_entries) + threadIdx.x] = V2<R>{(R)0, (R)0};
         tl[tile_scratch(run.max_entries) + threadIdx.x] = V2<R>{(R)0, (R)0};
