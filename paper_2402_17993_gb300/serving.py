@@ -169,7 +169,8 @@ class _DevSlot:
     """A fragment whose whole solve is enqueued on its stream at admission:
     `steps` replays of one captured graph (evaluation + device L-BFGS step)."""
 
-    def __init__(self, req, ctx, stream, t_admit, steps, gate_flag=None, gate_timeout_s=5.0):
+    def __init__(self, req, ctx, stream, t_admit, steps, gate_flag=None, gate_timeout_s=5.0,
+                 buf=None):
         import torch
         self.req = req
         self.ctx = ctx
@@ -178,12 +179,17 @@ class _DevSlot:
         self.t_admit = t_admit
         self.steps = steps
         self.gate_flag = gate_flag
+        self.buf = buf
         dev = torch.device("cuda", ctx.device)
         k = max(self.K, 1)
         ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=steps)
         # everything of this fragment is ordered on its own stream
         with torch.cuda.stream(stream):
-            buf = torch.zeros(2 * k + 1, dtype=torch.float64, device=dev)  # theta | grad | E
+            if buf is None:
+                buf = torch.zeros(2 * k + 1, dtype=torch.float64, device=dev)  # theta | grad | E
+            else:  # a buffer the serving thread allocated: theta starts at zero
+                buf = buf[: 2 * k + 1]
+                buf.zero_()
             self.th_dev, self.g_dev, self.E_dev = buf[:k], buf[k:2 * k], buf[2 * k:]
             ctx.capture_vqe_step(self.th_dev, self.E_dev, self.g_dev, stream)
             if gate_flag is not None:
@@ -286,7 +292,7 @@ class FragmentServer:
         with self._pool_lock:
             self.pool.setdefault((req.n_orb, req.n_alpha, req.n_beta), []).append(ctx)
 
-    def _prepare(self, q, used, stream, t0, gate_flag=None):
+    def _prepare(self, q, used, stream, t0, gate_flag=None, buf=None):
         """Host work of one admission (on a worker thread or the serving
         thread): the context's set-up on the fragment's stream, then the
         capture of its evaluation and optimiser step and the enqueue of the
@@ -294,7 +300,7 @@ class FragmentServer:
         import torch
         torch.cuda.set_device(self.device)
         ctx = self._context(q, used, stream)
-        slot = _DevSlot(q, ctx, stream, time.perf_counter() - t0, self.steps, gate_flag)
+        slot = _DevSlot(q, ctx, stream, time.perf_counter() - t0, self.steps, gate_flag, buf=buf)
         slot.dev_bytes = ctx.info()["device_bytes"]
         return slot
 
@@ -354,6 +360,17 @@ class FragmentServer:
         n_flags = self.max_active + 1
         flag_buf = torch.zeros(n_flags, dtype=torch.int32).pin_memory() if rate and self.lookahead else None
         free_flags = list(range(n_flags))
+        # For the same reason the solves' device buffers (theta | grad | E) are
+        # allocated here: a device allocation on a preparing worker thread
+        # waits for the device while holding the interpreter lock, which the
+        # serving thread then cannot take to release the gates.
+        slot_bufs = []
+        if flag_buf is not None:
+            kmax = max(max(1, len(build_uccsd_list(q.n_orb, q.n_alpha, q.n_beta))) for q in reqs)
+            dev = torch.device("cuda", self.device)
+            slot_bufs = [torch.zeros(2 * kmax + 1, dtype=torch.float64, device=dev)
+                         for _ in range(self.max_active)]
+            torch.cuda.synchronize(dev)
         free_streams = list(self.streams)
         results: list[Result] = []
         used = peak_used = sum(self.shared.values())
@@ -383,10 +400,11 @@ class FragmentServer:
                     flag = flag_buf[fi:fi + 1]
                     flag[0] = 0
                     gated.append((arrive[pending], flag))
+                sbuf = slot_bufs.pop() if slot_bufs else None
                 if self._exec is not None:
-                    fut = self._exec.submit(self._prepare, q, before, st, t0, flag)
+                    fut = self._exec.submit(self._prepare, q, before, st, t0, flag, sbuf)
                 else:
-                    fut = _Done(self._prepare(q, before, st, t0, flag))
+                    fut = _Done(self._prepare(q, before, st, t0, flag, sbuf))
                 preparing.append((fut, q, need, arrive[pending]))
                 pending += 1
                 progressed = True
@@ -421,6 +439,8 @@ class FragmentServer:
                     if s.gate_flag is not None:
                         free_flags.append((s.gate_flag.data_ptr() - flag_buf.data_ptr()) // 4)
                     energies, theta = s.result(keep_theta)
+                    if s.buf is not None:  # free again once its results are read
+                        slot_bufs.append(s.buf)
                     results.append(Result(s.req.r, 2 * s.req.n_orb, s.t_arrive, s.t_admit,
                                           t_done, energies[-1], energies, theta))
                     n_evals += s.steps
