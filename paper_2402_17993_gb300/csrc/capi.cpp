@@ -1365,7 +1365,7 @@ void uccsd_destroy(uccsd_ctx *c) {
         cudaEventSynchronize(c->gate_ev);
         cudaEventDestroy(c->gate_ev);
     }
-    if (c->gate_status) cudaFreeHost(c->gate_status);
+    uccsd::gate_status_give(c->gate_status);  // back to the process's pool
     delete c;
 }
 

@@ -21,6 +21,13 @@ inline constexpr int kHL = 0;  // unused by the row layout
 inline constexpr size_t kSweepBudget = 200 * 1024;
 }  // namespace uccsd
 
+namespace uccsd {
+// Gate status words (gate.cu): a word of a pinned pool allocated once per
+// process, and its return.
+uint32_t *gate_status_take();
+void gate_status_give(uint32_t *w);
+}  // namespace uccsd
+
 struct uccsd_ctx {
     int device = 0;
     int prec = 0;  // 0 FP64, 1 FP32 state
@@ -109,7 +116,7 @@ struct uccsd_ctx {
 
     // gate of the serving loop (uccsd_gate_enqueue): its status word in
     // mapped pinned memory (1 released, 2 gave up), the event after the gate
-    uint32_t *gate_status = nullptr;
+    uint32_t *gate_status = nullptr;  // a word of the process's pool (gate.cu)
     cudaEvent_t gate_ev = nullptr;
     bool gate_pending = false;
 

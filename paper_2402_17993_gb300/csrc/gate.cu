@@ -15,11 +15,51 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "../../include/uccsd.h"
 #include "ctx.hpp"
 
 namespace uccsd {
+
+// Status words of the gates, from one pinned, mapped block allocated at the
+// first gate of the process.  A pinned allocation waits for the device, and
+// while gates wait for flags that are released later, such a wait (on any
+// host thread) holds up the thread that would release them; so no gate
+// allocates after the first.
+namespace {
+constexpr int kGateStatusWords = 4096;
+std::mutex g_gate_mu;
+uint32_t *g_gate_words = nullptr;
+std::vector<int> *g_gate_free = nullptr;  // never destroyed (no CUDA calls at exit)
+}  // namespace
+
+uint32_t *gate_status_take() {
+    std::lock_guard<std::mutex> lk(g_gate_mu);
+    if (!g_gate_words) {
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(uint32_t) * kGateStatusWords,
+                          cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_gate_words = static_cast<uint32_t *>(p);
+        g_gate_free = new std::vector<int>();
+        for (int i = kGateStatusWords - 1; i >= 0; --i) g_gate_free->push_back(i);
+    }
+    if (g_gate_free->empty()) return nullptr;
+    const int i = g_gate_free->back();
+    g_gate_free->pop_back();
+    return g_gate_words + i;
+}
+
+void gate_status_give(uint32_t *w) {
+    if (!w) return;
+    std::lock_guard<std::mutex> lk(g_gate_mu);
+    g_gate_free->push_back(int(w - g_gate_words));
+}
+
 namespace {
 
 // Poll interval of the gate (ns, approximate: __nanosleep sleeps up to
@@ -75,9 +115,12 @@ uccsd_status uccsd_gate_enqueue(uccsd_ctx *c, const uint32_t *flag, uint32_t tar
     }
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess && !c->gate_status) {
-        void *p = nullptr;
-        e = cudaHostAlloc(&p, sizeof(uint32_t), cudaHostAllocMapped);
-        if (e == cudaSuccess) c->gate_status = static_cast<uint32_t *>(p);
+        c->gate_status = uccsd::gate_status_take();
+        if (!c->gate_status) {
+            c->err = "uccsd_gate_enqueue: no gate status word left (pinned allocation failed or "
+                     "4096 contexts hold gates)";
+            return UCCSD_ERR_CUDA;
+        }
     }
     if (e == cudaSuccess && !c->gate_ev) e = cudaEventCreateWithFlags(&c->gate_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
