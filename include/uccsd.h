@@ -331,6 +331,19 @@ uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *e
 uccsd_status uccsd_plan_pairs(int n_orb, int n_alpha, int n_beta, const int32_t *ijab, int K,
                               int amp_bytes, int nvec, int32_t *out, int cap, int *n_out);
 
+/* Host-only check hook (no device use): the order in which the FP32
+ * H-apply (Eq. 2, one column of beta strings per thread) takes each
+ * column's beta single excitations in its mixed alpha-beta groups.  The
+ * C(n_orb, n_beta) columns are the beta strings in ascending order; a
+ * column's ns = n_beta (n_orb - n_beta) singles j -> b in natural order are
+ * j occupied ascending, then b empty ascending.  out[t * C(n_orb, n_beta) +
+ * column] = the natural index of the single taken at slot t.  Every order
+ * gives the same contributions; this one is chosen per group of eight
+ * columns against shared-memory bank conflicts.  Writes min(count, cap)
+ * entries and *n_out = count; UCCSD_ERR_ARG for sizes outside
+ * 1 <= n_orb <= 15, 0 <= n_beta <= n_orb. */
+uccsd_status uccsd_happly_mixed_order(int n_orb, int n_beta, int32_t *out, int cap, int *n_out);
+
 /* Host-only: the compiled Jordan-Wigner Pauli terms of Eq. 2 in the
  * X^x Z^z form: H = sum_t coef[t] X^{xmask[t]} Z^{zmask[t]}, where
  * X^x Z^z |y> = (-1)^{popcount(y & z)} |y ^ x>.  Writes min(count, cap)

@@ -39,6 +39,7 @@ EXPORTS = [
     "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
     "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
     "uccsd_energy_grad_batched", "uccsd_plan_pairs", "uccsd_gate_enqueue", "uccsd_gate_status",
+    "uccsd_happly_mixed_order",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -127,6 +128,7 @@ def lib():
         L.uccsd_trotter_extrapolate.argtypes = [ip, ctypes.POINTER(ctypes.c_int), f64p, f64p]
         L.uccsd_plan_pairs.argtypes = [ip, ip, ip, i32p, ip, ip, ip, i32p, ip,
                                        ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_happly_mixed_order.argtypes = [ip, ip, i32p, ip, ctypes.POINTER(ctypes.c_int)]
         L.uccsd_gate_enqueue.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp]
         L.uccsd_gate_status.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
         _lib = L
@@ -177,6 +179,23 @@ def plan_pairs(n_orb, n_alpha, n_beta, ijab, amp_bytes=8, nvec=1):
     if st:
         raise UCCSDError(st, "plan_pairs")
     return out
+
+
+def happly_mixed_order(n_orb, n_beta):
+    """Host-only: the slot order of every column's beta singles in the FP32
+    H-apply's mixed groups, shape (n_singles, C(n_orb, n_beta)); entry
+    [t, column] = the natural index of the single taken at slot t
+    (uccsd_happly_mixed_order)."""
+    n = ctypes.c_int(0)
+    st = lib().uccsd_happly_mixed_order(n_orb, n_beta, None, 0, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "happly_mixed_order")
+    out = np.zeros(n.value, dtype=np.int32)
+    st = lib().uccsd_happly_mixed_order(n_orb, n_beta, _i32p(out), n.value, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "happly_mixed_order")
+    from math import comb
+    return out.reshape(n_beta * (n_orb - n_beta), comb(n_orb, n_beta))
 
 
 def hamiltonian_stats(n_orb, h, eri, e_core=0.0):

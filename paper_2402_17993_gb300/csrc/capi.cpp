@@ -468,6 +468,17 @@ uccsd_status upload_spectator_tables(uccsd_ctx *c, DevHam<R> *dh, const char *ta
     return UCCSD_OK;
 }
 
+// happly_mixed_order per (n_orb, n_beta), computed once per process.
+const std::vector<uint8_t> &mixed_order(int n_orb, int n_beta) {
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, std::vector<uint8_t>> *cache =
+        new std::map<std::pair<int, int>, std::vector<uint8_t>>();
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache->find({n_orb, n_beta});
+    if (it == cache->end()) it = cache->emplace(std::make_pair(n_orb, n_beta), happly_mixed_order(n_orb, n_beta)).first;
+    return it->second;
+}
+
 uccsd_status set_row_layout(uccsd_ctx *c) {
     const int no = c->n_orb;
     const size_t base = (size_t(1) << no) - 1;
@@ -516,6 +527,16 @@ uccsd_status set_row_layout(uccsd_ctx *c) {
                     ++k;
                 }
             }
+        }
+        if (c->prec && happly_cols_per_thread(c->hsec) == 1) {
+            // FP32 at one column per thread: the mixed groups take each
+            // column's singles in the order that spreads a wavefront's
+            // 16-byte loads over the bank groups
+            const std::vector<uint8_t> &ord = mixed_order(no, c->n_beta);
+            std::vector<uint32_t> nat(mix);
+            for (size_t t = 0; t < size_t(ns); ++t)
+                for (size_t col = 0; col < size_t(Db); ++col)
+                    mix[t * Db + col] = nat[size_t(ord[t * Db + col]) * Db + col];
         }
         uint32_t *p4, *pm;
         uccsd_status st = upload(c, "bsing", tab, &p4);
@@ -1994,6 +2015,17 @@ uccsd_status uccsd_hamiltonian_stats(int n_orb, const double *h, const double *e
     if (!compile_hamiltonian(n_orb, h, eri, e_core, &H, &err)) return UCCSD_ERR_ARG;
     if (n_groups) *n_groups = int(H.groups.size()) + (H.has_diag ? 1 : 0);
     if (n_terms) *n_terms = H.n_terms;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_happly_mixed_order(int n_orb, int n_beta, int32_t *out, int cap, int *n_out) {
+    if (n_orb < 1 || n_orb > 15 || n_beta < 0 || n_beta > n_orb || cap < 0 || !n_out ||
+        (cap > 0 && !out))
+        return UCCSD_ERR_ARG;
+    const std::vector<uint8_t> &ord = mixed_order(n_orb, n_beta);
+    const size_t w = std::min(size_t(cap), ord.size());
+    for (size_t i = 0; i < w; ++i) out[i] = ord[i];
+    *n_out = int(ord.size());
     return UCCSD_OK;
 }
 

@@ -126,8 +126,6 @@ __global__ void cs_kernel(const double *__restrict__ theta, int K, const int32_t
 // sigma_x) and sum |psi_x|^2 feed the energy; sigma outside the sector is
 // never written (it stays zero).
 // ---------------------------------------------------------------------------
-constexpr int kRowThreads = 256;
-
 // Dynamic shared memory of the H-apply: one source row, the beta string
 // ranks, then (16-byte aligned) the row's beta-single values.
 template <typename R>
@@ -858,8 +856,8 @@ cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int 
                           const DevHam<R> &H, const HSector &hs, double *Epart, int flags) {
     (void)LH;
     dim3 grid(hs.Da * hs.ncb, cfg.B);
-    const int threads = std::min(kRowThreads, std::max(32, ((hs.colblock + 31) / 32) * 32));
-    const int ept = (hs.colblock + threads - 1) / threads;
+    const int threads = happly_threads(hs);
+    const int ept = happly_cols_per_thread(hs);
     const size_t smem = happly_smem<R>(hs, H.n_orb);
     const V2<R> *p = static_cast<const V2<R> *>(psi);
     V2<R> *s = static_cast<V2<R> *>(sig);

@@ -208,6 +208,20 @@ cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles
 template <typename R>
 size_t happly_smem(const HSector &hs, int n_orb);
 
+// Threads of an H-apply CTA (a column block, one or more columns per
+// thread) and the columns each thread takes.  At one column per thread the
+// FP32 kernel stages the alpha singles' source rows in 16-byte chunks and
+// reads the mixed groups' beta singles in the order of happly_mixed_order.
+constexpr int kRowThreads = 256;
+inline int happly_threads(const HSector &hs) {
+    const int t = ((hs.colblock + 31) / 32) * 32;
+    return t < 32 ? 32 : t > kRowThreads ? kRowThreads : t;
+}
+inline int happly_cols_per_thread(const HSector &hs) {
+    const int t = happly_threads(hs);
+    return (hs.colblock + t - 1) / t;
+}
+
 // Fixed-step L-BFGS update of theta (K doubles, device) from the gradient g
 // and energy E of the evaluation at theta; state holds 2 m K + m + 3 K
 // doubles, meta 4 ints (zeroed to start); E is recorded in E_hist[step].

@@ -460,4 +460,152 @@ void build_comb_tables(std::vector<uint16_t> *combos, std::vector<uint16_t> *ran
     }
 }
 
+namespace {
+// Minimum-cost perfect matching of rows to columns of an n x n cost matrix
+// (row-major) by successive shortest augmenting paths: Dijkstra over the
+// alternating paths on reduced costs C - u(row) - v(column), which the
+// potential update keeps non-negative, and zero on matched edges.  Returns
+// the column of each row.
+std::vector<int> min_cost_assignment(int n, const std::vector<int> &C) {
+    const long long kInf = 1LL << 60;
+    std::vector<long long> u(n), v(n, 0), dist(n), drow(n);
+    std::vector<int> row_to(n, -1), col_to(n, -1), via(n);
+    std::vector<char> done(n);
+    for (int i = 0; i < n; ++i) u[i] = *std::min_element(C.begin() + size_t(i) * n, C.begin() + size_t(i + 1) * n);
+    for (int s = 0; s < n; ++s) {
+        std::fill(done.begin(), done.end(), 0);
+        std::fill(drow.begin(), drow.end(), kInf);
+        drow[s] = 0;
+        for (int j = 0; j < n; ++j) {
+            dist[j] = C[size_t(s) * n + j] - u[s] - v[j];
+            via[j] = s;
+        }
+        int jf = -1;
+        for (;;) {
+            int j = -1;
+            for (int k = 0; k < n; ++k)
+                if (!done[k] && (j < 0 || dist[k] < dist[j])) j = k;
+            done[j] = 1;
+            if (col_to[j] < 0) {
+                jf = j;
+                break;
+            }
+            const int i = col_to[j];  // through its matched row (reduced cost 0)
+            drow[i] = dist[j];
+            for (int k = 0; k < n; ++k) {
+                if (done[k]) continue;
+                const long long d = dist[j] + C[size_t(i) * n + k] - u[i] - v[k];
+                if (d < dist[k]) {
+                    dist[k] = d;
+                    via[k] = i;
+                }
+            }
+        }
+        const long long D = dist[jf];
+        for (int i = 0; i < n; ++i)
+            if (drow[i] < kInf) u[i] += D - drow[i];
+        for (int j = 0; j < n; ++j)
+            if (done[j]) v[j] -= D - dist[j];
+        // flip the path: column jf to the row it was reached from, that row's
+        // old column to the row before it, back to row s
+        for (int j = jf;;) {
+            const int i = via[j];
+            const int old = row_to[i];
+            row_to[i] = j;
+            col_to[j] = i;
+            if (i == s) break;
+            j = old;
+        }
+    }
+    return row_to;
+}
+
+// Shared-memory wavefronts of one slot of the mixed loop for the lanes of
+// an aligned group of eight columns: its 16-byte loads of the table item and
+// of the source chunk each take as many wavefronts as the largest number of
+// distinct items (sources) in one of the eight 16-byte bank groups.
+int slot_wavefronts(const uint32_t *item, const uint32_t *src, int m) {
+    int cnt_i[8] = {0}, cnt_s[8] = {0}, wi = 0, ws = 0;
+    for (int a = 0; a < m; ++a) {
+        bool seen_i = false, seen_s = false;
+        for (int b = 0; b < a; ++b) {
+            seen_i |= item[b] == item[a];
+            seen_s |= src[b] == src[a];
+        }
+        if (!seen_i) wi = std::max(wi, ++cnt_i[item[a] & 7u]);
+        if (!seen_s) ws = std::max(ws, ++cnt_s[src[a] & 7u]);
+    }
+    return wi + 2 * ws;  // the source item is two 16-byte chunks
+}
+}  // namespace
+
+#ifndef UCCSD_MIXED_ORDER_ROUNDS
+#define UCCSD_MIXED_ORDER_ROUNDS 8
+#endif
+constexpr int kMixedOrderRounds = UCCSD_MIXED_ORDER_ROUNDS;
+
+std::vector<uint8_t> happly_mixed_order(int n_orb, int n_beta) {
+    std::vector<uint32_t> bstr, rank(size_t(1) << n_orb, 0u);
+    for (uint32_t s = 0; s < (1u << n_orb); ++s)
+        if (popc(s) == n_beta) {
+            rank[s] = uint32_t(bstr.size());
+            bstr.push_back(s);
+        }
+    const int Db = int(bstr.size());
+    const int ns = n_beta * (n_orb - n_beta);
+    std::vector<uint8_t> order(size_t(ns) * Db);
+    for (int t = 0; t < ns; ++t)
+        for (int c = 0; c < Db; ++c) order[size_t(t) * Db + c] = uint8_t(t);
+    if (ns < 2) return order;
+    // natural entries of each column: table item and source rank of its
+    // k-th single j -> b (j occupied ascending, then b empty ascending)
+    std::vector<uint32_t> item(size_t(Db) * ns), src(size_t(Db) * ns);
+    for (int c = 0; c < Db; ++c) {
+        const uint32_t sb = bstr[c];
+        int k = 0;
+        for (int j = 0; j < n_orb; ++j) {
+            if (!((sb >> j) & 1u)) continue;
+            for (int b = 0; b < n_orb; ++b) {
+                if ((sb >> b) & 1u) continue;
+                const int lo = std::min(j, b), hi = std::max(j, b);
+                const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
+                const uint32_t pi = uint32_t(popc(sb & between) & 1);
+                item[size_t(c) * ns + k] = uint32_t(j * n_orb + b) + uint32_t(n_orb * n_orb) * pi;
+                src[size_t(c) * ns + k] = rank[sb ^ (1u << j) ^ (1u << b)];
+                ++k;
+            }
+        }
+    }
+    std::vector<int> cost(size_t(ns) * ns);
+    uint32_t ti[8], ts[8];
+    for (int q0 = 0; q0 < Db; q0 += 8) {
+        const int m = std::min(8, Db - q0);
+        // coordinate descent: each column's singles re-assigned to the slots
+        // by an exact minimum-cost assignment against the other columns of
+        // the group (never worse than its current order; an equal-cost
+        // assignment is taken too, which lets later columns move), a fixed
+        // number of rounds
+        for (int round = 0; round < kMixedOrderRounds; ++round) {
+            for (int a = 0; a < m; ++a) {
+                const int c = q0 + a;
+                for (int t = 0; t < ns; ++t) {
+                    for (int b = 0; b < m; ++b) {
+                        const int k = order[size_t(t) * Db + q0 + b];
+                        ti[b] = item[size_t(q0 + b) * ns + k];
+                        ts[b] = src[size_t(q0 + b) * ns + k];
+                    }
+                    for (int k = 0; k < ns; ++k) {
+                        ti[a] = item[size_t(c) * ns + k];
+                        ts[a] = src[size_t(c) * ns + k];
+                        cost[size_t(k) * ns + t] = slot_wavefronts(ti, ts, m);
+                    }
+                }
+                const std::vector<int> slot = min_cost_assignment(ns, cost);
+                for (int k = 0; k < ns; ++k) order[size_t(slot[k]) * Db + c] = uint8_t(k);
+            }
+        }
+    }
+    return order;
+}
+
 }  // namespace uccsd

@@ -109,6 +109,17 @@ struct ExpandedPair {
 std::vector<ExpandedPair> expand_pair_lists(int n_qubits, int n_alpha, int n_beta,
                                             const SweepPlan &plan, const PairLists &L);
 
+// Order of every column's beta single excitations in the FP32 H-apply's
+// mixed groups (one column per thread, staged source rows in 16-byte
+// chunks).  Column c's k-th single j -> b in natural order (j occupied
+// ascending, then b empty ascending) is taken at slot t when
+// order[t * Db + c] == k; Db = C(n_orb, n_beta) columns in ascending string
+// order.  Per aligned group of eight columns (the lanes of one wavefront of
+// 16-byte shared-memory loads) the slots are chosen to minimise the bank
+// conflicts of the loads of the staged mixed table and source rows; any
+// order gives the same contributions, summed in that order.
+std::vector<uint8_t> happly_mixed_order(int n_orb, int n_beta);
+
 // Combinatorial tables for bit strings of m <= kCombMax bits: for each m,
 // the 2^m strings sorted by (popcount, value) at combos[2^m - 1 ...], the
 // rank of each string among those of equal popcount at rank[2^m - 1 + s],
