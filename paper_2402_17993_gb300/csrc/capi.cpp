@@ -468,6 +468,78 @@ uccsd_status upload_spectator_tables(uccsd_ctx *c, DevHam<R> *dh, const char *ta
     return UCCSD_OK;
 }
 
+// Whether state addressing tables are the sector order's (where the plans'
+// entry maps apply).
+bool sector_order(const uccsd_ctx *c, const uint32_t *aoff, const uint32_t *boff) {
+    return aoff && aoff == c->sec_aoff && boff == c->sec_boff;
+}
+
+// Entry maps of a sweep plan: the sector index (sector addressing: alpha
+// rank x C(n_orb, n_beta) + beta rank) of every entry e = ia * Db + ib of
+// every tile of every run, as the kernels' tile view orders them (tile
+// strings of each popcount in ascending order, spread to orbital strings,
+// the tile's rest bits added); run r's tiles at max_entries entries each
+// from runs[r].emap_base.  No map (all emap_base = -1) when it would hold
+// more than kMaxMapEntries entries.
+constexpr size_t kMaxMapEntries = size_t(4) << 20;
+uccsd_status build_entry_map(uccsd_ctx *c, SweepPlan *pl, const std::string &name,
+                             const uint32_t **out) {
+    *out = nullptr;
+    size_t total = 0;
+    for (CRunDev &r : pl->runs) {
+        r.emap_base = -1;
+        total += size_t(r.n_tiles) * size_t(r.max_entries);
+    }
+    if (total == 0 || total > kMaxMapEntries) return UCCSD_OK;
+    const int no = c->n_orb, n = 2 * no;
+    std::vector<uint32_t> rank(size_t(1) << no);
+    std::vector<int> cnt(no + 2, 0);
+    for (uint32_t sv = 0; sv < (1u << no); ++sv) rank[sv] = uint32_t(cnt[__builtin_popcount(sv)]++);
+    const uint32_t dbs = uint32_t(binom_int(no, c->n_beta));
+    uint32_t amask = 0;
+    for (int q = 0; q < n; q += 2) amask |= 1u << q;
+    auto strings = [](int L, int k) {  // L-bit strings of popcount k, ascending
+        std::vector<uint32_t> v;
+        for (uint32_t s = 0; s < (1u << L); ++s)
+            if (__builtin_popcount(s) == k) v.push_back(s);
+        return v;
+    };
+    std::vector<uint32_t> map(total, 0u);
+    size_t base = 0;
+    for (CRunDev &r : pl->runs) {
+        r.emap_base = int32_t(base);
+        const uint32_t *spa = pl->spread.data() + r.spread_off;
+        const uint32_t *spb = spa + (size_t(1) << r.La);
+        for (int bx = 0; bx < r.n_tiles; ++bx) {
+            uint32_t rest = 0;  // bit k of bx at the k-th set bit of rmask
+            int k = 0;
+            for (uint32_t m = r.rmask; m; m &= m - 1u, ++k)
+                if ((uint32_t(bx) >> k) & 1u) rest |= m & (~m + 1u);
+            const int a = c->n_alpha - __builtin_popcount(rest & amask);
+            const int b = c->n_beta - __builtin_popcount(rest & ~amask);
+            if (a < 0 || a > r.La || b < 0 || b > r.Lb) continue;
+            uint32_t ra = 0, rb = 0;
+            for (uint32_t m = rest; m; m &= m - 1u) {
+                const int q = __builtin_ctz(m);
+                if (q & 1) rb |= 1u << (q >> 1);
+                else ra |= 1u << (q >> 1);
+            }
+            const std::vector<uint32_t> sa = strings(r.La, a), sb = strings(r.Lb, b);
+            uint32_t *m = map.data() + base + size_t(bx) * size_t(r.max_entries);
+            for (size_t ia = 0; ia < sa.size(); ++ia) {
+                const uint32_t xa = rank[ra | spa[sa[ia]]] * dbs;
+                for (size_t ib = 0; ib < sb.size(); ++ib) m[ia * sb.size() + ib] = xa + rank[rb | spb[sb[ib]]];
+            }
+        }
+        base += size_t(r.n_tiles) * size_t(r.max_entries);
+    }
+    uint32_t *p;
+    uccsd_status st = upload(c, name, map, &p);
+    if (st) return st;
+    *out = p;
+    return UCCSD_OK;
+}
+
 // happly_mixed_order per (n_orb, n_beta), computed once per process.
 const std::vector<uint8_t> &mixed_order(int n_orb, int n_beta) {
     static std::mutex mu;
@@ -788,6 +860,8 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
             out.aoff = c->fwd_args.aoff;
             out.boff = c->fwd_args.boff;
         }
+        in.emap = sector_order(c, in.aoff, in.boff) ? c->fwd_emap : nullptr;
+        out.emap = sector_order(c, out.aoff, out.boff) ? c->fwd_emap : nullptr;
         if ((e = launch_forward_sweep<R>(fcfg, psi_in, c->fwd.runs[r], fops, cs, in, r == 0 ? 1 : 0,
                                          c->hf_addr, out)) != cudaSuccess)
             return cuda_fail(c, e, "forward kernel");
@@ -854,6 +928,8 @@ uccsd_status run_eval(uccsd_ctx *c, int B, const double *theta, int on_dev, doub
                     out.boff = in.boff;
                 }
             }
+            in.emap = sector_order(c, in.aoff, in.boff) ? c->adj_emap : nullptr;
+            out.emap = sector_order(c, out.aoff, out.boff) ? c->adj_emap : nullptr;
             if ((e = launch_adjoint_sweep<R>(acfg, phi_in, lam_in, c->adj.runs[r], aops, cs, in,
                                              gpart, n_tiles_a(c), out)) != cudaSuccess)
                 return cuda_fail(c, e, "adjoint kernel");
@@ -1614,6 +1690,8 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->adj_args.spread = p4;
     if ((st = attach_lists(c, &c->fwd, &c->fwd_args, 0))) return st;
     if ((st = attach_lists(c, &c->adj, &c->adj_args, 1))) return st;
+    if ((st = build_entry_map(c, &c->fwd, "fwd_emap", &c->fwd_emap))) return st;
+    if ((st = build_entry_map(c, &c->adj, "adj_emap", &c->adj_emap))) return st;
     // gradient partial slots: the pair-list adjoint writes one per (tile, warp)
     {
         const bool lists = c->adj_args.pairs != nullptr;

@@ -95,6 +95,7 @@ struct CRunDev {
     int32_t max_entries; // largest compact tile over the run's CTAs
     int32_t max_da, max_db;  // largest C(La, a), C(Lb, b) over the run's CTAs
     int32_t pl_base;     // precomputed pair lists: first (offset, count) entry of the run, or -1
+    int32_t emap_base;   // entry maps: first entry of the run's tiles (max_entries each), or -1
 };
 
 // One factor exp(angle * G) of the schedule in the string spaces of its

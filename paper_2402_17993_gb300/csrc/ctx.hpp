@@ -72,6 +72,10 @@ struct uccsd_ctx {
     std::vector<double> op_scale;
     uccsd::SweepPlan fwd, adj;
     uccsd::SweepArgs fwd_args, adj_args;
+    // entry maps of the forward and adjoint plans (null when too large):
+    // set as SweepArgs / SweepOut::emap where a run reads or writes vectors
+    // in the sector order
+    const uint32_t *fwd_emap = nullptr, *adj_emap = nullptr;
     // Pair lists of the forward and adjoint plans: device copies shared with
     // every context of the same plan (not counted in `bytes`), and their hashes
     std::shared_ptr<void> lists_held[2];

@@ -118,6 +118,10 @@ struct SweepArgs {
     const uint2 *pairs = nullptr;
     uint32_t amask = 0;                  // alpha qubits (even positions)
     int n_alpha = 0, n_beta = 0;
+    // the plan's entry maps (sector index of each tile entry, from
+    // CRunDev::emap_base) when the vectors read are in the sector order
+    // (aoff / boff the sector addressing), else null: the tables above
+    const uint32_t *emap = nullptr;
 };
 
 // Where a sweep run leaves its vectors after its factors (the forward: the
@@ -129,6 +133,7 @@ struct SweepOut {
     void *phi = nullptr, *lam = nullptr;
     size_t N = 0;
     const uint32_t *aoff = nullptr, *boff = nullptr;
+    const uint32_t *emap = nullptr;  // as SweepArgs::emap, for the vectors written
 };
 
 // psi, cfg.N and sa.aoff / sa.boff address the state the run reads (unused

@@ -154,6 +154,7 @@ SweepPlan plan_sweep(int n_qubits, int n_alpha, int n_beta, size_t amp_bytes, in
             ++e;
         }
         CRunDev r{};
+        r.emap_base = -1;
         r.pl_base = -1;
         r.tmask = U;
         r.rmask = all & ~U;

@@ -122,27 +122,60 @@ __device__ __forceinline__ uint32_t entry_index(const TileView &v, int e) {
     return entry_index_at(v, e, v.aoff, v.boff);
 }
 
+// This CTA's tile entries in a plan's entry map (their sector indices, one
+// coalesced load each instead of the rank and spread table chain), or null.
+__device__ __forceinline__ const uint32_t *tile_map(const uint32_t *emap, const CRunDev &run) {
+    return (emap && run.emap_base >= 0)
+               ? emap + (size_t)run.emap_base + (size_t)blockIdx.x * (size_t)run.max_entries
+               : nullptr;
+}
+
 // Write a forward tile's entries to where the next run (or the caller, after
 // the last run) reads the state.
 template <typename R, int THREADS>
 __device__ __forceinline__ void store_forward_tile(const TileView &v, int D, const V2<R> *tile,
-                                                   const SweepOut &out) {
+                                                   const SweepOut &out, const CRunDev &run) {
     V2<R> *op = static_cast<V2<R> *>(out.phi) + (size_t)blockIdx.y * out.N;
-    for (int e = threadIdx.x; e < D; e += THREADS) op[entry_index_at(v, e, out.aoff, out.boff)] = tile[e];
+    if (const uint32_t *em = tile_map(out.emap, run)) {
+        for (int e = threadIdx.x; e < D; e += THREADS) op[__ldg(em + e)] = tile[e];
+    } else {
+        for (int e = threadIdx.x; e < D; e += THREADS) op[entry_index_at(v, e, out.aoff, out.boff)] = tile[e];
+    }
 }
 
 // Write an adjoint tile's phi and lambda entries to where the next run reads
 // them (nothing after the last run).
 template <typename R, int THREADS>
 __device__ __forceinline__ void store_adjoint_tile(const TileView &v, int D, const V2<R> *tp,
-                                                   const V2<R> *tl, const SweepOut &out) {
+                                                   const V2<R> *tl, const SweepOut &out,
+                                                   const CRunDev &run) {
     if (!out.phi) return;
     V2<R> *op = static_cast<V2<R> *>(out.phi) + (size_t)blockIdx.y * out.N;
     V2<R> *ol = static_cast<V2<R> *>(out.lam) + (size_t)blockIdx.y * out.N;
+    const uint32_t *em = tile_map(out.emap, run);
     for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index_at(v, e, out.aoff, out.boff);
+        const uint32_t x = em ? __ldg(em + e) : entry_index_at(v, e, out.aoff, out.boff);
         op[x] = tp[e];
         ol[x] = tl[e];
+    }
+}
+
+// Read the tile's entries of the vectors at st (and sl) into tp (and tl).
+template <typename R, int THREADS>
+__device__ __forceinline__ void load_tile(const TileView &v, int D, const uint32_t *em,
+                                          const V2<R> *st, V2<R> *tp, const V2<R> *sl, V2<R> *tl) {
+    if (em) {
+        for (int e = threadIdx.x; e < D; e += THREADS) {
+            const uint32_t x = __ldg(em + e);
+            tp[e] = st[x];
+            if (sl) tl[e] = sl[x];
+        }
+    } else {
+        for (int e = threadIdx.x; e < D; e += THREADS) {
+            const uint32_t x = entry_index(v, e);
+            tp[e] = st[x];
+            if (sl) tl[e] = sl[x];
+        }
     }
 }
 
@@ -514,16 +547,11 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
     V2<R> *st = psi + (size_t)b * N;
     const int D = v.Da * v.Db;
     const int nops = run.op_end - run.op_begin;
-    for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index(v, e);
-        V2<R> val;
-        if (init_hf) {
-            val.x = (R)(x == hf ? 1 : 0);
-            val.y = (R)0;
-        } else {
-            val = st[x];
-        }
-        tile[e] = val;
+    if (init_hf) {
+        for (int e = threadIdx.x; e < D; e += THREADS)
+            tile[e] = V2<R>{(R)(entry_index(v, e) == hf ? 1 : 0), (R)0};
+    } else {
+        load_tile<R, THREADS>(v, D, tile_map(la.emap, run), st, tile, nullptr, nullptr);
     }
     if (builder && nops > 0)
         build_factor<R, RL::kBuildLanes>(run, la, v, sops[0], scs[0], lists, &hdr[0], bl);
@@ -576,7 +604,7 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
         }
         __syncthreads();
     }
-    store_forward_tile<R, THREADS>(v, D, tile, out);
+    store_forward_tile<R, THREADS>(v, D, tile, out, run);
 }
 
 // Adjoint sweep of one run over one tile, factors in reverse: the compute
@@ -617,11 +645,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     const bool builder = (int)threadIdx.x >= RL::kCompute;
     const int bl = (int)threadIdx.x - RL::kCompute;  // builder lane
     const int nops = run.op_end - run.op_begin;
-    for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index(v, e);
-        tp[e] = sp[x];
-        tl[e] = sl[x];
-    }
+    load_tile<R, THREADS>(v, D, tile_map(la.emap, run), sp, tp, sl, tl);
     if (builder && nops > 0)
         build_factor<R, RL::kBuildLanes>(run, la, v, sops[nops - 1], scs[nops - 1], lists, &hdr[0], bl);
     __syncthreads();
@@ -707,7 +731,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
         __syncthreads();
     }
     if (builder && bl < 32 && nops > 0) flush_partial(it - 1, 0);
-    store_adjoint_tile<R, THREADS>(v, D, tp, tl, out);
+    store_adjoint_tile<R, THREADS>(v, D, tp, tl, out, run);
 }
 
 // ---------------------------------------------------------------------------
@@ -827,16 +851,11 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
     make_view(run, la, &v);
     V2<R> *st = psi + (size_t)b * N;
     const int D = v.Da * v.Db;
-    for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index(v, e);
-        V2<R> val;
-        if (init_hf) {
-            val.x = (R)(x == hf ? 1 : 0);
-            val.y = (R)0;
-        } else {
-            val = st[x];
-        }
-        tile[e] = val;
+    if (init_hf) {
+        for (int e = threadIdx.x; e < D; e += THREADS)
+            tile[e] = V2<R>{(R)(entry_index(v, e) == hf ? 1 : 0), (R)0};
+    } else {
+        load_tile<R, THREADS>(v, D, tile_map(la.emap, run), st, tile, nullptr, nullptr);
     }
     if (threadIdx.x < kListAhead && (int)threadIdx.x < nops) prefetch_list_l2(sa.pairs, spl[threadIdx.x]);
     uint2 p0[KP], p1[KP], p2[KP];
@@ -850,7 +869,7 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
         if (o + 2 < nops)
             forward_list_step<R, THREADS, KP>(o + 2, nops, tile, sops, scs, spl, sa.pairs, v.rest, p2, p1);
     }
-    store_forward_tile<R, THREADS>(v, D, tile, out);
+    store_forward_tile<R, THREADS>(v, D, tile, out, run);
 }
 
 // A thread's gradient partial of one factor waiting for its warp sum: the
@@ -997,11 +1016,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     const int D = v.Da * v.Db;
     V2<R> *sp = phi + (size_t)b * N;
     V2<R> *sl = lam + (size_t)b * N;
-    for (int e = threadIdx.x; e < D; e += THREADS) {
-        const uint32_t x = entry_index(v, e);
-        tp[e] = sp[x];
-        tl[e] = sl[x];
-    }
+    load_tile<R, THREADS>(v, D, tile_map(la.emap, run), sp, tp, sl, tl);
     // gradient partials of this slot and tile: gp[op_index * tile_stride + warp]
     double *gp = gpart + (size_t)b * n_ops * tile_stride + (size_t)blockIdx.x * W;
     if (threadIdx.x < kListAhead && (int)threadIdx.x < nops)
@@ -1023,7 +1038,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
                                               p2, p1, gp, tile_stride, pend);
     }
     flush_pending<R>(pend);
-    store_adjoint_tile<R, THREADS>(v, D, tp, tl, out);
+    store_adjoint_tile<R, THREADS>(v, D, tp, tl, out, run);
 }
 
 // Trotter-free ansatz (Eq. 3): w = scale * sum_k coef_k G_k u over the
