@@ -11,6 +11,7 @@
 
 #include "amp.cuh"
 #include "kernels.cuh"
+#include "pdl.cuh"
 
 namespace uccsd {
 namespace {
@@ -372,6 +373,7 @@ __global__ void __launch_bounds__(kRowThreads) happly_kernel(const V2<R> *__rest
                                                              DevHam<R> H, HSector hs,
                                                              double *__restrict__ Epart,
                                                              int flags) {
+    pdl_wait();  // psi is the previous kernel's output
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *src = reinterpret_cast<V2<R> *>(smem_raw);                  // one source row
     uint16_t *brk = reinterpret_cast<uint16_t *>(src + hs.Db);          // beta string ranks
@@ -661,6 +663,7 @@ __global__ void __launch_bounds__(kThreads) reduce_kernel(const double *__restri
                                                           double shift, int rayleigh,
                                                           double *__restrict__ E,
                                                           double *__restrict__ grad) {
+    pdl_wait();  // the partials are the previous kernels' output
     __shared__ double s_nrm;
     const int b = blockIdx.y;
     energy_sums(Epart, n_tiles_h, b, shift, rayleigh, E, &s_nrm);
@@ -861,14 +864,15 @@ cudaError_t launch_happly(const LaunchCfg &cfg, const void *psi, void *sig, int 
     const size_t smem = happly_smem<R>(hs, H.n_orb);
     const V2<R> *p = static_cast<const V2<R> *>(psi);
     V2<R> *s = static_cast<V2<R> *>(sig);
+    cudaError_t e = cudaSuccess;
     switch (ept <= 1 ? 1 : ept <= 2 ? 2 : ept <= 4 ? 4 : ept <= 8 ? 8 : 0) {
-        case 1: happly_kernel<R, 1><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
-        case 2: happly_kernel<R, 2><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
-        case 4: happly_kernel<R, 4><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
-        case 8: happly_kernel<R, 8><<<grid, threads, smem, cfg.stream>>>(p, s, cfg.N, H, hs, Epart, flags); break;
+        case 1: e = launch_pdl(happly_kernel<R, 1>, grid, dim3(threads), smem, cfg.stream, p, s, cfg.N, H, hs, Epart, flags); break;
+        case 2: e = launch_pdl(happly_kernel<R, 2>, grid, dim3(threads), smem, cfg.stream, p, s, cfg.N, H, hs, Epart, flags); break;
+        case 4: e = launch_pdl(happly_kernel<R, 4>, grid, dim3(threads), smem, cfg.stream, p, s, cfg.N, H, hs, Epart, flags); break;
+        case 8: e = launch_pdl(happly_kernel<R, 8>, grid, dim3(threads), smem, cfg.stream, p, s, cfg.N, H, hs, Epart, flags); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles_h,
@@ -878,10 +882,10 @@ cudaError_t launch_reduce(const LaunchCfg &cfg, const double *Epart, int n_tiles
                           int rayleigh, double *E, double *grad) {
     if (grad && tile_stride <= kReduceSerialMax) {
         dim3 grid(std::max(1, (K + kThreads - 1) / kThreads), cfg.B);
-        reduce_serial_kernel<<<grid, kThreads, 0, cfg.stream>>>(Epart, n_tiles_h, gpart, tile_stride,
-                                                                op_tiles, cfg.n_ops, K, k_ptr, k_ops,
-                                                                op_scale, shift, rayleigh, E, grad);
-        return cudaGetLastError();
+        const cudaError_t e = launch_pdl(reduce_serial_kernel, grid, dim3(kThreads), 0, cfg.stream, Epart,
+                                         n_tiles_h, gpart, tile_stride, op_tiles, cfg.n_ops, K, k_ptr,
+                                         k_ops, op_scale, shift, rayleigh, E, grad);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     int gx = grad ? std::max(1, std::min(64, (K + 7) / 8)) : 1;
     dim3 grid(gx, cfg.B);

@@ -15,6 +15,7 @@
 
 #include "amp.cuh"
 #include "kernels.cuh"
+#include "pdl.cuh"
 #include "plan.hpp"
 
 namespace uccsd {
@@ -830,6 +831,7 @@ __global__ void __launch_bounds__(THREADS) forward_list_kernel(
     V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
     const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf,
     SweepOut out) {
+    pdl_wait();  // the state and the cos/sin values are earlier kernels' output
     constexpr int KP = ListPre<R>::kFwd;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V2<R> *tile = reinterpret_cast<V2<R> *>(smem_raw);
@@ -984,6 +986,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_list_kernel(
     V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
     double *__restrict__ gpart, int tile_stride, SweepOut out) {
+    pdl_wait();  // phi, lambda and the partial slots belong to earlier kernels first
     constexpr int KP = ListPre<R>::kAdj;
     constexpr int W = THREADS / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1280,14 +1283,15 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
                                          run.op_end - run.op_begin, max(run.La, run.Lb));
     V2<R> *p = static_cast<V2<R> *>(psi);
     const V2<R> *c = static_cast<const V2<R> *>(cs);
+    cudaError_t e = cudaSuccess;
     if (run.pl_base >= 0 && sa.pairs) {
         if (run.max_entries >= kLargeTile)
-            forward_list_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
+            e = launch_pdl(forward_list_kernel<R, kSweepThreadsLarge>, grid, dim3(kSweepThreadsLarge), smem, cfg.stream,
+                           p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
         else
-            forward_list_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-                p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
-        return cudaGetLastError();
+            e = launch_pdl(forward_list_kernel<R, kSweepThreadsSmall>, grid, dim3(kSweepThreadsSmall), smem, cfg.stream,
+                           p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (run.max_entries >= kLargeTile)
         forward_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
@@ -1308,14 +1312,15 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
     V2<R> *f = static_cast<V2<R> *>(phi);
     V2<R> *l = static_cast<V2<R> *>(lam);
     const V2<R> *c = static_cast<const V2<R> *>(cs);
+    cudaError_t e = cudaSuccess;
     if (run.pl_base >= 0 && sa.pairs) {
         if (run.max_entries >= kLargeTile)
-            adjoint_list_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
+            e = launch_pdl(adjoint_list_kernel<R, kSweepThreadsLarge>, grid, dim3(kSweepThreadsLarge), smem, cfg.stream,
+                           f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
         else
-            adjoint_list_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-                f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
-        return cudaGetLastError();
+            e = launch_pdl(adjoint_list_kernel<R, kSweepThreadsSmall>, grid, dim3(kSweepThreadsSmall), smem, cfg.stream,
+                           f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (run.max_entries >= kLargeTile)
         adjoint_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
