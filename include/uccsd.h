@@ -454,6 +454,22 @@ uccsd_status uccsd_gate_enqueue(uccsd_ctx *ctx, const uint32_t *flag, uint32_t t
  * UCCSD_ERR_STATE without a gate. */
 uccsd_status uccsd_gate_status(uccsd_ctx *ctx, int wait, int *released);
 
+/* Stream bookkeeping for callers that enqueue work while gates hold the
+ * device (the serving loop's preparing threads).  A launch can wait in the
+ * driver while a hardware queue is full of work held by a gate; these calls
+ * are plain C calls, so a caller's language runtime may let the thread that
+ * releases the gates run meanwhile.
+ * uccsd_stream_mark records the context's completion marker (an event) on
+ * `stream`: it completes when the work enqueued on `stream` before it has.
+ * uccsd_mark_done sets *done to 1 once the last recorded marker has
+ * completed, else 0 (no wait); UCCSD_ERR_STATE before any mark.
+ * uccsd_zero_async enqueues the zeroing of `bytes` bytes of device memory
+ * at `ptr` on `stream`.  Errors: UCCSD_ERR_ARG for null arguments,
+ * UCCSD_ERR_CUDA if CUDA refuses the call. */
+uccsd_status uccsd_stream_mark(uccsd_ctx *ctx, void *stream);
+uccsd_status uccsd_mark_done(uccsd_ctx *ctx, int *done);
+uccsd_status uccsd_zero_async(uccsd_ctx *ctx, void *ptr, size_t bytes, void *stream);
+
 /* ---- Trotter-schedule helpers (Section 2.3 ordering; Section 3.2 extrapolation) ---- */
 
 /* First-order (Moller-Plesset) amplitude of every excitation of the context's

@@ -39,7 +39,7 @@ EXPORTS = [
     "uccsd_set_layout", "uccsd_pauli_terms_scbk", "uccsd_opt_init", "uccsd_opt_step",
     "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
     "uccsd_energy_grad_batched", "uccsd_plan_pairs", "uccsd_gate_enqueue", "uccsd_gate_status",
-    "uccsd_happly_mixed_order",
+    "uccsd_happly_mixed_order", "uccsd_stream_mark", "uccsd_mark_done", "uccsd_zero_async",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -129,6 +129,9 @@ def lib():
         L.uccsd_plan_pairs.argtypes = [ip, ip, ip, i32p, ip, ip, ip, i32p, ip,
                                        ctypes.POINTER(ctypes.c_int)]
         L.uccsd_happly_mixed_order.argtypes = [ip, ip, i32p, ip, ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_stream_mark.argtypes = [vp, vp]
+        L.uccsd_mark_done.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_zero_async.argtypes = [vp, vp, ctypes.c_size_t, vp]
         L.uccsd_gate_enqueue.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_uint64, vp]
         L.uccsd_gate_status.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int)]
         _lib = L
@@ -466,6 +469,24 @@ class Context:
         self._check(self._L.uccsd_gate_enqueue(self._c, ctypes.c_void_p(flag.data_ptr()),
                                                int(target), int(timeout_s * 1e9),
                                                _stream_ptr(stream)), "gate_enqueue")
+
+    def mark(self, stream):
+        """Record the context's completion marker on `stream`
+        (uccsd_stream_mark): mark_done() is True once the work enqueued
+        there before it is done."""
+        self._check(self._L.uccsd_stream_mark(self._c, _stream_ptr(stream)), "stream_mark")
+
+    def mark_done(self):
+        d = ctypes.c_int(0)
+        self._check(self._L.uccsd_mark_done(self._c, ctypes.byref(d)), "mark_done")
+        return bool(d.value)
+
+    def zero_async(self, t, stream):
+        """Zero the CUDA tensor t (contiguous) in order on `stream`
+        (uccsd_zero_async)."""
+        self._check(self._L.uccsd_zero_async(self._c, ctypes.c_void_p(t.data_ptr()),
+                                             t.numel() * t.element_size(), _stream_ptr(stream)),
+                    "zero_async")
 
     def gate_status(self, wait=True):
         """True once the gate was released, False while it waits; raises

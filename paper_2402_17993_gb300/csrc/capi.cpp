@@ -474,6 +474,51 @@ bool sector_order(const uccsd_ctx *c, const uint32_t *aoff, const uint32_t *boff
     return aoff && aoff == c->sec_aoff && boff == c->sec_boff;
 }
 
+// Optimiser records in one pinned, mapped block allocated at the first
+// uccsd_opt_init of the process: the optimiser kernel writes a context's
+// meta words and energy history there, and uccsd_opt_history reads them from
+// host memory after the context's stream is done, without a copy on any
+// stream (a copy could queue behind other streams' work on a shared hardware
+// queue, such as solves held by gates, and wait for it).
+constexpr int kOptRecDoubles = 1024;  // 2 doubles of meta ints, then up to 1022 energies
+constexpr int kOptRecs = 1024;
+std::mutex g_opt_mu;
+double *g_opt_block = nullptr;
+std::vector<int> *g_opt_free = nullptr;  // never destroyed (no CUDA calls at exit)
+
+double *opt_rec_take() {
+    std::lock_guard<std::mutex> lk(g_opt_mu);
+    if (!g_opt_block) {
+        if (g_opt_free) return nullptr;  // the allocation failed once
+        g_opt_free = new std::vector<int>();
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(double) * kOptRecDoubles * kOptRecs,
+                          cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_opt_block = static_cast<double *>(p);
+        for (int i = kOptRecs - 1; i >= 0; --i) g_opt_free->push_back(i);
+    }
+    if (g_opt_free->empty()) return nullptr;
+    const int i = g_opt_free->back();
+    g_opt_free->pop_back();
+    return g_opt_block + size_t(i) * kOptRecDoubles;
+}
+
+void opt_rec_give(double *r) {
+    if (!r) return;
+    std::lock_guard<std::mutex> lk(g_opt_mu);
+    g_opt_free->push_back(int((r - g_opt_block) / kOptRecDoubles));
+}
+
+int *opt_meta_ptr(uccsd_ctx *c) {
+    return c->opt_rec_dev ? reinterpret_cast<int *>(c->opt_rec_dev) : opt_meta_ptr(c);
+}
+double *opt_hist_ptr(uccsd_ctx *c) {
+    return c->opt_rec_dev ? c->opt_rec_dev + 2 : opt_hist_ptr(c);
+}
+
 // Entry maps of a sweep plan: the sector index (sector addressing: alpha
 // rank x C(n_orb, n_beta) + beta rank) of every entry e = ia * Db + ib of
 // every tile of every run, as the kernels' tile view orders them (tile
@@ -1430,6 +1475,7 @@ uccsd_status uccsd_create(uccsd_ctx **out, int device, uccsd_prec prec, size_t h
         cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         if (c->join_ev) cudaEventDestroy(c->join_ev);
+    if (c->mark_ev) cudaEventDestroy(c->mark_ev);
         if (c->fork_ev) cudaEventDestroy(c->fork_ev);
         if (c->aux) cudaStreamDestroy(c->aux);
         if (c->stage_ev) cudaEventDestroy(c->stage_ev);
@@ -1463,6 +1509,7 @@ void uccsd_destroy(uccsd_ctx *c) {
         cudaEventDestroy(c->gate_ev);
     }
     uccsd::gate_status_give(c->gate_status);  // back to the process's pool
+    opt_rec_give(c->opt_rec);  // the device is idle after the frees above
     delete c;
 }
 
@@ -1816,8 +1863,8 @@ uccsd_status capture_graph(uccsd_ctx *c, int B, const double *theta, double *E, 
         cudaError_t eo = launch_lbfgs(s, c->K, c->opt_m, c->opt_max_step, c->opt_first,
                                       const_cast<double *>(theta), E, grad,
                                       static_cast<double *>(dptr(c, "opt_state")),
-                                      static_cast<int *>(dptr(c, "opt_meta")),
-                                      static_cast<double *>(dptr(c, "opt_hist")), c->opt_steps);
+                                      opt_meta_ptr(c),
+                                      opt_hist_ptr(c), c->opt_steps);
         if (eo != cudaSuccess) st = fail(c, UCCSD_ERR_CUDA, "optimiser kernel in capture");
         else ++c->launches;
     }
@@ -2035,11 +2082,28 @@ uccsd_status uccsd_opt_init(uccsd_ctx *c, int memory, double max_step, double fi
     uccsd_status st;
     if ((st = dalloc(c, "opt_state", sizeof(double) * (2 * size_t(memory) * K + memory + 3 * K), &p)))
         return st;
-    if ((st = dalloc(c, "opt_meta", 4 * sizeof(int), &p))) return st;
-    if ((e = cudaMemsetAsync(p, 0, 4 * sizeof(int), c->setup)) != cudaSuccess) return cuda_fail(c, e, "memset");
-    if ((st = dalloc(c, "opt_hist", sizeof(double) * max_steps, &p))) return st;
-    if ((e = cudaMemsetAsync(p, 0, sizeof(double) * max_steps, c->setup)) != cudaSuccess)
-        return cuda_fail(c, e, "memset");
+    if (!c->opt_rec && max_steps <= kOptRecDoubles - 2) {
+        if ((c->opt_rec = opt_rec_take()) &&
+            cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->opt_rec_dev), c->opt_rec, 0) != cudaSuccess) {
+            cudaGetLastError();
+            opt_rec_give(c->opt_rec);
+            c->opt_rec = c->opt_rec_dev = nullptr;
+        }
+    }
+    if (c->opt_rec && max_steps > kOptRecDoubles - 2) {  // longer than a record: device buffers
+        opt_rec_give(c->opt_rec);
+        c->opt_rec = c->opt_rec_dev = nullptr;
+    }
+    if (c->opt_rec) {
+        p = c->opt_rec_dev;
+    } else {
+        if ((st = dalloc(c, "opt_meta", 4 * sizeof(int), &p))) return st;
+        if ((e = cudaMemsetAsync(p, 0, 4 * sizeof(int), c->setup)) != cudaSuccess) return cuda_fail(c, e, "memset");
+        if ((st = dalloc(c, "opt_hist", sizeof(double) * max_steps, &p))) return st;
+    }
+    // zeroed in stream order (a record's meta words and history at once)
+    const size_t zb = c->opt_rec ? sizeof(double) * (2 + size_t(max_steps)) : sizeof(double) * max_steps;
+    if ((e = cudaMemsetAsync(p, 0, zb, c->setup)) != cudaSuccess) return cuda_fail(c, e, "memset");
     if ((e = setup_sync(c)) != cudaSuccess) return cuda_fail(c, e, "memset");
     c->opt_m = memory;
     c->opt_steps = max_steps;
@@ -2057,8 +2121,8 @@ uccsd_status uccsd_opt_step(uccsd_ctx *c, double *theta, const double *E, const 
     if (!E) return fail(c, UCCSD_ERR_ARG, "null E");
     cudaError_t e = launch_lbfgs(static_cast<cudaStream_t>(stream), c->K, c->opt_m, c->opt_max_step,
                                  c->opt_first, theta, E, grad, static_cast<double *>(dptr(c, "opt_state")),
-                                 static_cast<int *>(dptr(c, "opt_meta")),
-                                 static_cast<double *>(dptr(c, "opt_hist")), c->opt_steps);
+                                 opt_meta_ptr(c),
+                                 opt_hist_ptr(c), c->opt_steps);
     if (e != cudaSuccess) return cuda_fail(c, e, "optimiser kernel");
     ++c->launches;
     c->last_stream = static_cast<cudaStream_t>(stream);
@@ -2070,6 +2134,16 @@ uccsd_status uccsd_opt_history(uccsd_ctx *c, double *E, int cap, int *n_out) {
     if (c->opt_m == 0) return fail(c, UCCSD_ERR_STATE, "uccsd_opt_init must come first");
     cudaError_t e = cudaSetDevice(c->device);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->last_stream);
+    if (e == cudaSuccess && c->opt_rec) {
+        // the record in host memory: complete once the stream is done
+        const volatile int *m = reinterpret_cast<const volatile int *>(c->opt_rec);
+        const int done = m[3];
+        const int n = std::min(done, c->opt_steps);
+        const volatile double *h = c->opt_rec + 2;
+        for (int i = 0; i < std::min(n, cap); ++i) E[i] = h[i];
+        *n_out = std::max(n, 0);
+        return UCCSD_OK;
+    }
     int meta[4] = {0, 0, 0, 0};
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(meta, dptr(c, "opt_meta"), sizeof(meta), cudaMemcpyDeviceToHost, c->setup);

@@ -117,11 +117,17 @@ struct uccsd_ctx {
     // device optimiser (fixed-step L-BFGS)
     int opt_m = 0, opt_steps = 0;
     double opt_max_step = 0.0, opt_first = 0.0;
+    // its record (4 meta ints, then the energy history) in the process's
+    // mapped pinned pool (capi.cpp), or null: device buffers opt_meta and
+    // opt_hist; opt_rec_dev is the record's device address
+    double *opt_rec = nullptr, *opt_rec_dev = nullptr;
 
     // gate of the serving loop (uccsd_gate_enqueue): its status word in
     // mapped pinned memory (1 released, 2 gave up), the event after the gate
     uint32_t *gate_status = nullptr;  // a word of the process's pool (gate.cu)
     cudaEvent_t gate_ev = nullptr;
+    cudaEvent_t mark_ev = nullptr;  // uccsd_stream_mark
+    bool marked = false;
     bool gate_pending = false;
 
     // captured evaluation graph

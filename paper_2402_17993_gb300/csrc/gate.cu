@@ -180,4 +180,44 @@ uccsd_status uccsd_gate_status(uccsd_ctx *c, int wait, int *released) {
     return UCCSD_ERR_TIMEOUT;
 }
 
+uccsd_status uccsd_stream_mark(uccsd_ctx *c, void *stream) {
+    if (!c || !stream) return UCCSD_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess && !c->mark_ev) e = cudaEventCreateWithFlags(&c->mark_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->mark_ev, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        c->err = std::string("uccsd_stream_mark: ") + cudaGetErrorString(e);
+        return UCCSD_ERR_CUDA;
+    }
+    c->marked = true;
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_mark_done(uccsd_ctx *c, int *done) {
+    if (!c || !done) return UCCSD_ERR_ARG;
+    if (!c->marked) {
+        c->err = "uccsd_mark_done: no mark recorded";
+        return UCCSD_ERR_STATE;
+    }
+    const cudaError_t e = cudaEventQuery(c->mark_ev);
+    if (e == cudaSuccess || e == cudaErrorNotReady) {
+        if (e == cudaErrorNotReady) cudaGetLastError();
+        *done = e == cudaSuccess;
+        return UCCSD_OK;
+    }
+    c->err = std::string("uccsd_mark_done: ") + cudaGetErrorString(e);
+    return UCCSD_ERR_CUDA;
+}
+
+uccsd_status uccsd_zero_async(uccsd_ctx *c, void *ptr, size_t bytes, void *stream) {
+    if (!c || !ptr) return UCCSD_ERR_ARG;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, bytes, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        c->err = std::string("uccsd_zero_async: ") + cudaGetErrorString(e);
+        return UCCSD_ERR_CUDA;
+    }
+    return UCCSD_OK;
+}
+
 }  // extern "C"

@@ -165,6 +165,17 @@ class _Slot:
         return E
 
 
+class _Mark:
+    """Completion of a fragment's enqueued solve (the context's stream mark),
+    queried without waiting."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    def query(self):
+        return self.ctx.mark_done()
+
+
 class _DevSlot:
     """A fragment whose whole solve is enqueued on its stream at admission:
     `steps` replays of one captured graph (evaluation + device L-BFGS step)."""
@@ -183,23 +194,24 @@ class _DevSlot:
         dev = torch.device("cuda", ctx.device)
         k = max(self.K, 1)
         ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=steps)
-        # everything of this fragment is ordered on its own stream
-        with torch.cuda.stream(stream):
-            if buf is None:
-                buf = torch.zeros(2 * k + 1, dtype=torch.float64, device=dev)  # theta | grad | E
-            else:  # a buffer the serving thread allocated: theta starts at zero
-                buf = buf[: 2 * k + 1]
-                buf.zero_()
-            self.th_dev, self.g_dev, self.E_dev = buf[:k], buf[k:2 * k], buf[2 * k:]
-            ctx.capture_vqe_step(self.th_dev, self.E_dev, self.g_dev, stream)
-            if gate_flag is not None:
-                # prepared ahead of its arrival: the solve waits on the device
-                # until the serving thread releases the flag
-                ctx.gate(gate_flag, 1, gate_timeout_s, stream)
-            for _ in range(steps):
-                ctx.replay(stream)  # evaluation + device L-BFGS step
-            self.done = torch.cuda.Event()
-            self.done.record(stream)
+        # Everything of this fragment is ordered on its own stream, and every
+        # enqueue goes through the library: a launch may wait in the driver
+        # while a hardware queue is full of solves held by gates, and a plain
+        # C call lets the serving thread run meanwhile to release them.
+        if buf is None:
+            buf = torch.empty(2 * k + 1, dtype=torch.float64, device=dev)  # theta | grad | E
+        buf = buf[: 2 * k + 1]
+        ctx.zero_async(buf, stream)  # theta starts at zero
+        self.th_dev, self.g_dev, self.E_dev = buf[:k], buf[k:2 * k], buf[2 * k:]
+        ctx.capture_vqe_step(self.th_dev, self.E_dev, self.g_dev, stream)
+        if gate_flag is not None:
+            # prepared ahead of its arrival: the solve waits on the device
+            # until the serving thread releases the flag
+            ctx.gate(gate_flag, 1, gate_timeout_s, stream)
+        for _ in range(steps):
+            ctx.replay(stream)  # evaluation + device L-BFGS step
+        ctx.mark(stream)
+        self.done = _Mark(ctx)
 
     def release(self):
         self.gate_flag[0] = 1
