@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(THREADS) forward_sweep_kernel(
     V2<R> *__restrict__ psi, size_t N, CRunDev run, const COpDev *__restrict__ ops,
     const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa, int init_hf, uint32_t hf,
     SweepOut out) {
+    pdl_wait();  // the state and the cos/sin values are earlier kernels' output
     using RL = Roles<THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ OpHdr<R> hdr[2];
@@ -617,6 +618,7 @@ __global__ void __launch_bounds__(THREADS) adjoint_sweep_kernel(
     V2<R> *__restrict__ phi, V2<R> *__restrict__ lam, size_t N, CRunDev run,
     const COpDev *__restrict__ ops, const V2<R> *__restrict__ cs, int n_ops, SweepArgs sa,
     double *__restrict__ gpart, int tile_stride, SweepOut out) {
+    pdl_wait();  // phi, lambda and the partial slots belong to earlier kernels first
     using RL = Roles<THREADS>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ OpHdr<R> hdr[2];
@@ -1294,12 +1296,12 @@ cudaError_t launch_forward_sweep(const LaunchCfg &cfg, void *psi, const CRunDev 
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (run.max_entries >= kLargeTile)
-        forward_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
+        e = launch_pdl(forward_sweep_kernel<R, kSweepThreadsLarge>, grid, dim3(kSweepThreadsLarge), smem, cfg.stream,
+                       p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
     else
-        forward_sweep_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-            p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
-    return cudaGetLastError();
+        e = launch_pdl(forward_sweep_kernel<R, kSweepThreadsSmall>, grid, dim3(kSweepThreadsSmall), smem, cfg.stream,
+                       p, cfg.N, run, ops, c, cfg.n_ops, sa, init_hf, hf, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename R>
@@ -1323,12 +1325,12 @@ cudaError_t launch_adjoint_sweep(const LaunchCfg &cfg, void *phi, void *lam, con
         return e != cudaSuccess ? e : cudaGetLastError();
     }
     if (run.max_entries >= kLargeTile)
-        adjoint_sweep_kernel<R, kSweepThreadsLarge><<<grid, kSweepThreadsLarge, smem, cfg.stream>>>(
-            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
+        e = launch_pdl(adjoint_sweep_kernel<R, kSweepThreadsLarge>, grid, dim3(kSweepThreadsLarge), smem, cfg.stream,
+                       f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
     else
-        adjoint_sweep_kernel<R, kSweepThreadsSmall><<<grid, kSweepThreadsSmall, smem, cfg.stream>>>(
-            f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
-    return cudaGetLastError();
+        e = launch_pdl(adjoint_sweep_kernel<R, kSweepThreadsSmall>, grid, dim3(kSweepThreadsSmall), smem, cfg.stream,
+                       f, l, cfg.N, run, ops, c, cfg.n_ops, sa, gpart, tile_stride, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename R>
