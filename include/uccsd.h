@@ -344,6 +344,22 @@ uccsd_status uccsd_plan_pairs(int n_orb, int n_alpha, int n_beta, const int32_t 
  * 1 <= n_orb <= 15, 0 <= n_beta <= n_orb. */
 uccsd_status uccsd_happly_mixed_order(int n_orb, int n_beta, int32_t *out, int cap, int *n_out);
 
+/* Host-only check hook (no device use): the entry maps of the sweep plan
+ * (Eq. 5, first order, one slice; the forward's plan for nvec = 1, the
+ * adjoint's for nvec = 2, amplitudes of amp_bytes bytes), by which the
+ * sweeps read and write their tiles in the sector order.  One row of 5
+ * int32 per entry of every tile of every run that holds sector entries:
+ *   run, tile, entry  the run, its tile (CTA) and the tile entry
+ *   index             the map's sector index of the entry: rank of its alpha
+ *                     string x C(n_orb, n_beta) + rank of its beta string,
+ *                     strings ranked in ascending order within a popcount
+ *   det               the entry's determinant (bit q = occupation of spin
+ *                     orbital q), decoded independently of the map
+ * Writes min(count, cap) rows and *n_out = count.  UCCSD_ERR_ARG for an
+ * invalid list or arguments, or a plan of more than 2^26 map entries. */
+uccsd_status uccsd_plan_entry_map(int n_orb, int n_alpha, int n_beta, const int32_t *ijab, int K,
+                                  int amp_bytes, int nvec, int32_t *out, int cap, int *n_out);
+
 /* Host-only: the compiled Jordan-Wigner Pauli terms of Eq. 2 in the
  * X^x Z^z form: H = sum_t coef[t] X^{xmask[t]} Z^{zmask[t]}, where
  * X^x Z^z |y> = (-1)^{popcount(y & z)} |y ^ x>.  Writes min(count, cap)

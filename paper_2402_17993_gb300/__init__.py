@@ -40,6 +40,7 @@ EXPORTS = [
     "uccsd_opt_history", "uccsd_set_setup_stream", "uccsd_capture_vqe_step",
     "uccsd_energy_grad_batched", "uccsd_plan_pairs", "uccsd_gate_enqueue", "uccsd_gate_status",
     "uccsd_happly_mixed_order", "uccsd_stream_mark", "uccsd_mark_done", "uccsd_zero_async",
+    "uccsd_plan_entry_map",
 ]
 
 FAMILIES = ["cs", "forward", "happly", "adjoint", "reduce"]
@@ -129,6 +130,8 @@ def lib():
         L.uccsd_plan_pairs.argtypes = [ip, ip, ip, i32p, ip, ip, ip, i32p, ip,
                                        ctypes.POINTER(ctypes.c_int)]
         L.uccsd_happly_mixed_order.argtypes = [ip, ip, i32p, ip, ctypes.POINTER(ctypes.c_int)]
+        L.uccsd_plan_entry_map.argtypes = [ip, ip, ip, i32p, ip, ip, ip, i32p, ip,
+                                           ctypes.POINTER(ctypes.c_int)]
         L.uccsd_stream_mark.argtypes = [vp, vp]
         L.uccsd_mark_done.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.uccsd_zero_async.argtypes = [vp, vp, ctypes.c_size_t, vp]
@@ -181,6 +184,23 @@ def plan_pairs(n_orb, n_alpha, n_beta, ijab, amp_bytes=8, nvec=1):
                                 nvec, _i32p(out), n.value, ctypes.byref(n))
     if st:
         raise UCCSDError(st, "plan_pairs")
+    return out
+
+
+def plan_entry_map(n_orb, n_alpha, n_beta, ijab, amp_bytes=8, nvec=1):
+    """Host-only: the sweep plan's entry maps, one row (run, tile, entry,
+    sector index, determinant) per tile entry (uccsd_plan_entry_map)."""
+    ijab = np.ascontiguousarray(ijab, dtype=np.int32).reshape(-1, 4)
+    n = ctypes.c_int(0)
+    st = lib().uccsd_plan_entry_map(n_orb, n_alpha, n_beta, _i32p(ijab), ijab.shape[0], amp_bytes,
+                                    nvec, None, 0, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "plan_entry_map")
+    out = np.zeros((n.value, 5), dtype=np.int32)
+    st = lib().uccsd_plan_entry_map(n_orb, n_alpha, n_beta, _i32p(ijab), ijab.shape[0], amp_bytes,
+                                    nvec, _i32p(out), n.value, ctypes.byref(n))
+    if st:
+        raise UCCSDError(st, "plan_entry_map")
     return out
 
 

@@ -519,18 +519,14 @@ double *opt_hist_ptr(uccsd_ctx *c) {
     return c->opt_rec_dev ? c->opt_rec_dev + 2 : opt_hist_ptr(c);
 }
 
-// Entry maps of a sweep plan: the sector index (sector addressing: alpha
-// rank x C(n_orb, n_beta) + beta rank) of every entry e = ia * Db + ib of
-// every tile of every run, as the kernels' tile view orders them (tile
-// strings of each popcount in ascending order, spread to orbital strings,
-// the tile's rest bits added); run r's tiles at max_entries entries each
-// from runs[r].emap_base.  No map (all emap_base = -1) when it would hold
+// The entry maps of a sweep plan (build_entry_map, plan.cpp) on the device.
+// No map (all emap_base = -1) when it would hold
 // more than kMaxMapEntries entries (2 GB), or take more than half of a
 // context's HBM budget (the state vectors come later).  26 qubits: 1.2 GB
 // for both plans, evaluation 27.9 -> 26.3 ms.
 constexpr size_t kMaxMapEntries = size_t(512) << 20;
-uccsd_status build_entry_map(uccsd_ctx *c, SweepPlan *pl, const std::string &name,
-                             const uint32_t **out) {
+uccsd_status attach_entry_map(uccsd_ctx *c, SweepPlan *pl, const std::string &name,
+                              const uint32_t **out) {
     *out = nullptr;
     size_t total = 0;
     for (CRunDev &r : pl->runs) {
@@ -539,51 +535,13 @@ uccsd_status build_entry_map(uccsd_ctx *c, SweepPlan *pl, const std::string &nam
     }
     if (total == 0 || total > kMaxMapEntries) return UCCSD_OK;
     if (c->budget && c->bytes + sizeof(uint32_t) * total > c->budget / 2) return UCCSD_OK;
-    const int no = c->n_orb, n = 2 * no;
-    std::vector<uint32_t> rank(size_t(1) << no);
-    std::vector<int> cnt(no + 2, 0);
-    for (uint32_t sv = 0; sv < (1u << no); ++sv) rank[sv] = uint32_t(cnt[__builtin_popcount(sv)]++);
-    const uint32_t dbs = uint32_t(binom_int(no, c->n_beta));
-    uint32_t amask = 0;
-    for (int q = 0; q < n; q += 2) amask |= 1u << q;
-    auto strings = [](int L, int k) {  // L-bit strings of popcount k, ascending
-        std::vector<uint32_t> v;
-        for (uint32_t s = 0; s < (1u << L); ++s)
-            if (__builtin_popcount(s) == k) v.push_back(s);
-        return v;
-    };
-    std::vector<uint32_t> map(total, 0u);
-    size_t base = 0;
-    for (CRunDev &r : pl->runs) {
-        r.emap_base = int32_t(base);
-        const uint32_t *spa = pl->spread.data() + r.spread_off;
-        const uint32_t *spb = spa + (size_t(1) << r.La);
-        for (int bx = 0; bx < r.n_tiles; ++bx) {
-            uint32_t rest = 0;  // bit k of bx at the k-th set bit of rmask
-            int k = 0;
-            for (uint32_t m = r.rmask; m; m &= m - 1u, ++k)
-                if ((uint32_t(bx) >> k) & 1u) rest |= m & (~m + 1u);
-            const int a = c->n_alpha - __builtin_popcount(rest & amask);
-            const int b = c->n_beta - __builtin_popcount(rest & ~amask);
-            if (a < 0 || a > r.La || b < 0 || b > r.Lb) continue;
-            uint32_t ra = 0, rb = 0;
-            for (uint32_t m = rest; m; m &= m - 1u) {
-                const int q = __builtin_ctz(m);
-                if (q & 1) rb |= 1u << (q >> 1);
-                else ra |= 1u << (q >> 1);
-            }
-            const std::vector<uint32_t> sa = strings(r.La, a), sb = strings(r.Lb, b);
-            uint32_t *m = map.data() + base + size_t(bx) * size_t(r.max_entries);
-            for (size_t ia = 0; ia < sa.size(); ++ia) {
-                const uint32_t xa = rank[ra | spa[sa[ia]]] * dbs;
-                for (size_t ib = 0; ib < sb.size(); ++ib) m[ia * sb.size() + ib] = xa + rank[rb | spb[sb[ib]]];
-            }
-        }
-        base += size_t(r.n_tiles) * size_t(r.max_entries);
-    }
+    const std::vector<uint32_t> map = build_entry_map(c->n, c->n_alpha, c->n_beta, pl);
     uint32_t *p;
     uccsd_status st = upload(c, name, map, &p);
-    if (st) return st;
+    if (st) {
+        for (CRunDev &r : pl->runs) r.emap_base = -1;
+        return st;
+    }
     *out = p;
     return UCCSD_OK;
 }
@@ -1740,8 +1698,8 @@ uccsd_status uccsd_set_excitations(uccsd_ctx *c, int K, const int32_t *ijab, int
     c->adj_args.spread = p4;
     if ((st = attach_lists(c, &c->fwd, &c->fwd_args, 0))) return st;
     if ((st = attach_lists(c, &c->adj, &c->adj_args, 1))) return st;
-    if ((st = build_entry_map(c, &c->fwd, "fwd_emap", &c->fwd_emap))) return st;
-    if ((st = build_entry_map(c, &c->adj, "adj_emap", &c->adj_emap))) return st;
+    if ((st = attach_entry_map(c, &c->fwd, "fwd_emap", &c->fwd_emap))) return st;
+    if ((st = attach_entry_map(c, &c->adj, "adj_emap", &c->adj_emap))) return st;
     // gradient partial slots: the pair-list adjoint writes one per (tile, warp)
     {
         const bool lists = c->adj_args.pairs != nullptr;
@@ -2181,6 +2139,54 @@ uccsd_status uccsd_happly_mixed_order(int n_orb, int n_beta, int32_t *out, int c
     const size_t w = std::min(size_t(cap), ord.size());
     for (size_t i = 0; i < w; ++i) out[i] = ord[i];
     *n_out = int(ord.size());
+    return UCCSD_OK;
+}
+
+uccsd_status uccsd_plan_entry_map(int n_orb, int n_alpha, int n_beta, const int32_t *ijab, int K,
+                                  int amp_bytes, int nvec, int32_t *out, int cap, int *n_out) {
+    if (n_orb < 1 || n_orb > 15 || n_alpha < 0 || n_beta < 0 || n_alpha > n_orb ||
+        n_beta > n_orb || K < 1 || !ijab || (amp_bytes != 8 && amp_bytes != 16) ||
+        (nvec != 1 && nvec != 2) || cap < 0 || !n_out || (cap > 0 && !out))
+        return UCCSD_ERR_ARG;
+    const int n = 2 * n_orb;
+    const uint64_t hf = hf_bits(n_alpha, n_beta);
+    std::vector<CompiledExc> exc(K);
+    for (int k = 0; k < K; ++k) {
+        const int32_t *r = ijab + 4 * k;
+        std::string err;
+        auto occ = [&](int q) { return q >= 0 && q < n && ((hf >> q) & 1u); };
+        auto vir = [&](int q) { return q >= 0 && q < n && !((hf >> q) & 1u); };
+        const bool ok = r[1] < 0 ? r[3] < 0 && occ(r[0]) && vir(r[2]) && ((r[0] & 1) == (r[2] & 1))
+                                 : occ(r[0]) && occ(r[1]) && vir(r[2]) && vir(r[3]) && r[0] != r[1] &&
+                                       r[2] != r[3] &&
+                                       ((r[0] & 1) + (r[1] & 1) == (r[2] & 1) + (r[3] & 1));
+        if (!ok || !compile_excitation(n, r, &exc[k], &err)) return UCCSD_ERR_ARG;
+    }
+    std::vector<int32_t> op_k;
+    std::vector<double> op_scale;
+    build_schedule(K, 1, 1, &op_k, &op_scale);
+    SweepPlan plan = plan_sweep(n, n_alpha, n_beta, size_t(amp_bytes), nvec, kSweepBudget, exc, op_k);
+    size_t total = 0;
+    for (const CRunDev &r : plan.runs) total += size_t(r.n_tiles) * size_t(r.max_entries);
+    if (total > (size_t(1) << 26)) return UCCSD_ERR_ARG;  // a check hook for small plans
+    const std::vector<uint32_t> map = build_entry_map(n, n_alpha, n_beta, &plan);
+    size_t rows = 0;
+    for (size_t ri = 0; ri < plan.runs.size(); ++ri) {
+        const CRunDev &r = plan.runs[ri];
+        for (int t = 0; t < r.n_tiles; ++t) {
+            const std::vector<uint32_t> dets = tile_entry_dets(n, n_alpha, n_beta, r, t);
+            for (size_t e = 0; e < dets.size(); ++e, ++rows) {
+                if (rows >= size_t(cap)) continue;
+                int32_t *row = out + 5 * rows;
+                row[0] = int32_t(ri);
+                row[1] = t;
+                row[2] = int32_t(e);
+                row[3] = int32_t(map[size_t(r.emap_base) + size_t(t) * size_t(r.max_entries) + e]);
+                row[4] = int32_t(dets[e]);
+            }
+        }
+    }
+    *n_out = int(rows);
     return UCCSD_OK;
 }
 

@@ -440,6 +440,67 @@ std::vector<ExpandedPair> expand_pair_lists(int n_qubits, int n_alpha, int n_bet
     return out;
 }
 
+std::vector<uint32_t> build_entry_map(int n_qubits, int n_alpha, int n_beta, SweepPlan *plan) {
+    size_t total = 0;
+    for (CRunDev &r : plan->runs) total += size_t(r.n_tiles) * size_t(r.max_entries);
+    const int no = n_qubits / 2;
+    std::vector<uint32_t> rank(size_t(1) << no);
+    std::vector<int> cnt(no + 2, 0);
+    for (uint32_t sv = 0; sv < (1u << no); ++sv) rank[sv] = uint32_t(cnt[popc(sv)]++);
+    const uint32_t dbs = uint32_t(cnt[n_beta]);  // C(n_orb, n_beta)
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
+    auto strings = [](int L, int k) {  // L-bit strings of popcount k, ascending
+        std::vector<uint32_t> v;
+        for (uint32_t s = 0; s < (1u << L); ++s)
+            if (popc(s) == k) v.push_back(s);
+        return v;
+    };
+    std::vector<uint32_t> map(total, 0u);
+    size_t base = 0;
+    for (CRunDev &r : plan->runs) {
+        r.emap_base = int32_t(base);
+        const uint32_t *spa = plan->spread.data() + r.spread_off;
+        const uint32_t *spb = spa + (size_t(1) << r.La);
+        for (int bx = 0; bx < r.n_tiles; ++bx) {
+            const uint32_t rest = deposit_bits(uint32_t(bx), r.rmask);
+            const int a = n_alpha - popc(rest & amask), b = n_beta - popc(rest & ~amask);
+            if (a < 0 || a > r.La || b < 0 || b > r.Lb) continue;
+            uint32_t ra = 0, rb = 0;  // orbital strings of the rest bits
+            for (uint32_t m = rest; m; m &= m - 1u) {
+                const int q = __builtin_ctz(m);
+                if (q & 1) rb |= 1u << (q >> 1);
+                else ra |= 1u << (q >> 1);
+            }
+            const std::vector<uint32_t> sa = strings(r.La, a), sb = strings(r.Lb, b);
+            uint32_t *m = map.data() + base + size_t(bx) * size_t(r.max_entries);
+            for (size_t ia = 0; ia < sa.size(); ++ia) {
+                const uint32_t xa = rank[ra | spa[sa[ia]]] * dbs;
+                for (size_t ib = 0; ib < sb.size(); ++ib) m[ia * sb.size() + ib] = xa + rank[rb | spb[sb[ib]]];
+            }
+        }
+        base += size_t(r.n_tiles) * size_t(r.max_entries);
+    }
+    return map;
+}
+
+std::vector<uint32_t> tile_entry_dets(int n_qubits, int n_alpha, int n_beta, const CRunDev &r,
+                                      int tile) {
+    uint32_t amask = 0;
+    for (int q = 0; q < n_qubits; q += 2) amask |= 1u << q;
+    const uint32_t rest = deposit_bits(uint32_t(tile), r.rmask);
+    const int a = n_alpha - popc(rest & amask), b = n_beta - popc(rest & ~amask);
+    std::vector<uint32_t> out;
+    if (a < 0 || a > r.La || b < 0 || b > r.Lb) return out;
+    const uint32_t Ta = r.tmask & amask, Tb = r.tmask & ~amask;
+    for (uint32_t s = 0; s < (1u << r.La); ++s) {
+        if (popc(s) != a) continue;
+        for (uint32_t t = 0; t < (1u << r.Lb); ++t)
+            if (popc(t) == b) out.push_back(rest | deposit_bits(s, Ta) | deposit_bits(t, Tb));
+    }
+    return out;
+}
+
 void build_comb_tables(std::vector<uint16_t> *combos, std::vector<uint16_t> *rank,
                        std::vector<int32_t> *offs) {
     combos->assign((size_t(1) << (kCombMax + 1)) - 1, 0);

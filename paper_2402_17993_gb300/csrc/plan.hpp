@@ -109,6 +109,18 @@ struct ExpandedPair {
 std::vector<ExpandedPair> expand_pair_lists(int n_qubits, int n_alpha, int n_beta,
                                             const SweepPlan &plan, const PairLists &L);
 
+// Entry maps of a plan: the sector index (alpha string rank x C(n_orb,
+// n_beta) + beta string rank, strings ranked in ascending order within
+// their popcount) of every entry e = ia * Db + ib of every tile of every run,
+// as the sweep kernels' tile view orders them; run r's tiles at max_entries
+// entries each from runs[r].emap_base (set here).  Unused slots are 0.
+std::vector<uint32_t> build_entry_map(int n_qubits, int n_alpha, int n_beta, SweepPlan *plan);
+// The determinants of tile `tile` of run r in entry order, decoded by
+// depositing the tile strings into the tile's qubit positions (a check of
+// the maps by another route); empty for a tile without sector entries.
+std::vector<uint32_t> tile_entry_dets(int n_qubits, int n_alpha, int n_beta, const CRunDev &r,
+                                      int tile);
+
 // Order of every column's beta single excitations in the FP32 H-apply's
 // mixed groups (one column per thread, staged source rows in 16-byte
 // chunks).  Column c's k-th single j -> b in natural order (j occupied
