@@ -524,14 +524,22 @@ def run_ours(args):
     th_pin = torch.tensor(th_host, dtype=torch.float64).pin_memory()
     E_pin = torch.empty(B, dtype=torch.float64).pin_memory()
     G_pin = torch.empty(B, K, dtype=torch.float64).pin_memory()
+    # each step from host buffers to host buffers, timed on the host (the call
+    # returns once the results are in E_pin and G_pin), with L2 evicted and the
+    # device idle before it as in the device-timed loop (not timed)
     barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e2e_s = 0.0
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
         ctx.energy_grad_ptr(B, th_pin.data_ptr(), E_pin.data_ptr(), G_pin.data_ptr(), False, stream)
+        e2e_s += time.perf_counter() - t0
     barrier()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(e2e_s * 1e3, world) * 1e-3
     e2e = {"value": world * B * args.steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": B * K * 8, "d2h_bytes_per_step": B * 8 + B * K * 8}
+           "h2d_bytes_per_step": B * K * 8, "d2h_bytes_per_step": B * 8 + B * K * 8,
+           "l2": "evicted before each step (not timed)"}
 
     info = ctx.info()
     ijab = uc.build_uccsd_list(w["n_orb"], w["n_alpha"], w["n_beta"])
