@@ -195,37 +195,6 @@ def test_captured_vqe_step_is_the_eager_step(uc):
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
-def test_long_history_moves_the_optimiser_and_drops_the_captured_step(uc):
-    # up to 1022 steps the history lives in a host record; asking for more
-    # moves it to device buffers, which discards a captured step (it would
-    # write to the old place); captured again, the long history is read back
-    import torch
-    w = synth.workload("12q")
-    ctx = uc.make_context(6, w["h"], w["eri"], 0.0, 3, 3, precision=uc.FP32_STATE)
-    K = ctx.K
-    s = torch.cuda.Stream()
-    th = torch.zeros(K, dtype=torch.float64, device="cuda")
-    E = torch.zeros(1, dtype=torch.float64, device="cuda")
-    G = torch.zeros(K, dtype=torch.float64, device="cuda")
-    ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=4)
-    ctx.capture_vqe_step(th, E, G, s)
-    for _ in range(4):
-        ctx.replay(s)
-    short = ctx.opt_history()
-    assert len(short) == 4
-    th.zero_()
-    torch.cuda.synchronize()  # the replays below run on s
-    ctx.opt_init(memory=10, max_step=0.2, first_scale=0.1, max_steps=2000)
-    with pytest.raises(uc.UCCSDError):
-        ctx.replay(s)  # the captured step was dropped
-    ctx.capture_vqe_step(th, E, G, s)
-    for _ in range(4):
-        ctx.replay(s)
-    long = ctx.opt_history()
-    assert np.array_equal(short, long)  # the same four steps from the same start
-    ctx.close()
-
-
 def test_contexts_prepared_on_many_threads_are_independent(uc):
     # distinct contexts on distinct host threads: set-up (Jordan-Wigner
     # compile, plans, shared pair lists), capture and evaluation run
