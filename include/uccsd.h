@@ -404,13 +404,8 @@ uccsd_status uccsd_energy_grad_trotter_free(uccsd_ctx *ctx, const double *theta,
  * Algorithm 7.4): memory m in [1, 32] pairs, steps capped at max_step in the
  * max-norm, the first step -first_scale * grad; pairs with s.y <= 1e-16
  * max(1, y.y) are not stored.  Allocates (2 m + 3) K + m doubles of state and
- * max_steps doubles of energy history and resets them.  Up to 1022 steps the
- * history and the step count live in a record of a pinned, mapped host
- * block shared by the process (allocated at its first call), which
- * uccsd_opt_history reads without a copy on any stream.  When the call moves
- * the optimiser's buffers, a graph captured by uccsd_capture_vqe_step is
- * discarded (capture it again).  Requires uccsd_set_excitations (which
- * discards the optimiser).  Errors:
+ * max_steps doubles of energy history and resets them.  Requires
+ * uccsd_set_excitations (which discards the optimiser).  Errors:
  * UCCSD_ERR_STATE, UCCSD_ERR_ARG for parameters out of range,
  * UCCSD_ERR_BUDGET / UCCSD_ERR_OOM. */
 uccsd_status uccsd_opt_init(uccsd_ctx *ctx, int memory, double max_step, double first_scale,
@@ -436,8 +431,7 @@ uccsd_status uccsd_capture_vqe_step(uccsd_ctx *ctx, double *theta_dev, double *E
 
 /* Energies recorded by uccsd_opt_step, in step order, to host E (min(steps,
  * cap) doubles); *n_out = steps recorded.  Synchronises the last stream the
- * optimiser ran on; with the history in a host record (see uccsd_opt_init)
- * it enqueues nothing, so it does not wait for other streams' work. */
+ * optimiser ran on. */
 uccsd_status uccsd_opt_history(uccsd_ctx *ctx, double *E, int cap, int *n_out);
 
 /* ---- Bounded device wait of the serving loop (no counterpart in the paper,

@@ -1815,7 +1815,6 @@ uccsd_status capture_graph(uccsd_ctx *c, int B, const double *theta, double *E, 
         cudaGraphDestroy(c->graph);
         c->graph = nullptr;
     }
-    c->graph_opt = false;
     e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
     const uint64_t l0 = c->launches;
@@ -1842,7 +1841,6 @@ uccsd_status capture_graph(uccsd_ctx *c, int B, const double *theta, double *E, 
     c->graph = g;
     e = cudaGraphInstantiate(&c->graph_exec, g, 0);
     if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-    c->graph_opt = opt_step;
     return UCCSD_OK;
 }
 }  // namespace
@@ -2043,8 +2041,6 @@ uccsd_status uccsd_opt_init(uccsd_ctx *c, int memory, double max_step, double fi
     const size_t K = size_t(std::max(c->K, 1));
     void *p;
     uccsd_status st;
-    const int *meta_before = opt_meta_ptr(c);
-    const double *state_before = static_cast<const double *>(dptr(c, "opt_state"));
     if ((st = dalloc(c, "opt_state", sizeof(double) * (2 * size_t(memory) * K + memory + 3 * K), &p)))
         return st;
     if (!c->opt_rec && max_steps <= kOptRecDoubles - 2) {
@@ -2069,16 +2065,6 @@ uccsd_status uccsd_opt_init(uccsd_ctx *c, int memory, double max_step, double fi
     // zeroed in stream order (a record's meta words and history at once)
     const size_t zb = c->opt_rec ? sizeof(double) * (2 + size_t(max_steps)) : sizeof(double) * max_steps;
     if ((e = cudaMemsetAsync(p, 0, zb, c->setup)) != cudaSuccess) return cuda_fail(c, e, "memset");
-    if (c->graph_exec && c->graph_opt &&
-        (opt_meta_ptr(c) != meta_before || dptr(c, "opt_state") != state_before)) {
-        // a captured optimiser step would write where the optimiser no longer
-        // keeps its state: it must be captured again
-        cudaGraphExecDestroy(c->graph_exec);
-        cudaGraphDestroy(c->graph);
-        c->graph_exec = nullptr;
-        c->graph = nullptr;
-        c->graph_opt = false;
-    }
     if ((e = setup_sync(c)) != cudaSuccess) return cuda_fail(c, e, "memset");
     c->opt_m = memory;
     c->opt_steps = max_steps;

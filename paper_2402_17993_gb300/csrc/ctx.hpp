@@ -121,7 +121,6 @@ struct uccsd_ctx {
     // mapped pinned pool (capi.cpp), or null: device buffers opt_meta and
     // opt_hist; opt_rec_dev is the record's device address
     double *opt_rec = nullptr, *opt_rec_dev = nullptr;
-    bool graph_opt = false;  // the captured graph holds the optimiser step
 
     // gate of the serving loop (uccsd_gate_enqueue): its status word in
     // mapped pinned memory (1 released, 2 gave up), the event after the gate
