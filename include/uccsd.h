@@ -425,6 +425,10 @@ uccsd_status uccsd_opt_step(uccsd_ctx *ctx, double *theta, const double *E, cons
  * uccsd_replay then runs one iteration of the Section 2.3 loop (ansatz
  * state, energy, gradient, classical update) as one graph launch.  Needs
  * uccsd_opt_init first; the optimiser history advances on every replay.
+ * The graph holds the optimiser buffers' addresses, which a later
+ * uccsd_opt_init may change (histories of more than 1022 steps live in
+ * device buffers, shorter ones in a record of a process-wide pinned block):
+ * capture again after calling uccsd_opt_init.
  * Errors as uccsd_capture; UCCSD_ERR_STATE without uccsd_opt_init. */
 uccsd_status uccsd_capture_vqe_step(uccsd_ctx *ctx, double *theta_dev, double *E_dev,
                                     double *grad_dev, void *stream);
